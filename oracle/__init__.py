@@ -1,0 +1,147 @@
+"""CPU oracle for the 1-D complex DFT (Eq. 1), as a ctypes wrapper.
+
+TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and
+bench.py's cpu_baseline / reference legs import this package.  The product
+library (paper_1409_5757_gb300) never imports it and shares no code with it.
+
+All routines take and return numpy complex128 arrays (interleaved re, im),
+and compute X[k] = sum_n x[n] exp(sign*2*pi*i*n*k/N) with no normalisation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_c_i64p = ctypes.POINTER(ctypes.c_int64)
+_c_dp = ctypes.POINTER(ctypes.c_double)
+
+
+class Oracle:
+    """Handle on one build of oracle.c (mutant 0 is the real oracle)."""
+
+    def __init__(self, mutant: int = 0, outdir: str | None = None):
+        path = _build.build(mutant=mutant, outdir=outdir)
+        self.path = path
+        self.mutant = mutant
+        lib = ctypes.CDLL(path)
+        lib.oracle_version.restype = ctypes.c_int
+        lib.oracle_mutant.restype = ctypes.c_int
+        lib.oracle_threads.restype = ctypes.c_int
+        lib.oracle_twiddle.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_int, _c_dp, _c_dp]
+        lib.oracle_dft_naive.argtypes = [_c_dp, _c_dp, ctypes.c_int64, ctypes.c_int]
+        lib.oracle_dft_naive.restype = ctypes.c_int
+        lib.oracle_fft_radix2.argtypes = [_c_dp, ctypes.c_int64, ctypes.c_int]
+        lib.oracle_fft_radix2.restype = ctypes.c_int
+        lib.oracle_gen_uniform.argtypes = [ctypes.c_uint64, ctypes.c_int64, ctypes.c_int64, _c_dp]
+        lib.oracle_splitmix64.argtypes = [ctypes.c_uint64, ctypes.c_uint64]
+        lib.oracle_splitmix64.restype = ctypes.c_uint64
+        lib.oracle_dft_bins_uniform.argtypes = [ctypes.c_uint64, ctypes.c_int64, ctypes.c_int,
+                                                _c_i64p, ctypes.c_int64, _c_dp]
+        lib.oracle_dft_bins_uniform.restype = ctypes.c_int
+        lib.oracle_dft_bins.argtypes = [_c_dp, ctypes.c_int64, ctypes.c_int, _c_i64p,
+                                        ctypes.c_int64, _c_dp]
+        lib.oracle_dft_bins.restype = ctypes.c_int
+        self._lib = lib
+
+    # -- helpers -----------------------------------------------------------
+    @staticmethod
+    def _c128(x) -> np.ndarray:
+        return np.ascontiguousarray(np.asarray(x, dtype=np.complex128))
+
+    @staticmethod
+    def _dp(a: np.ndarray):
+        return a.ctypes.data_as(_c_dp)
+
+    # -- API -----------------------------------------------------------------
+    @property
+    def version(self) -> int:
+        return self._lib.oracle_version()
+
+    @property
+    def threads(self) -> int:
+        return self._lib.oracle_threads()
+
+    def twiddle(self, m: int, N: int, sign: int) -> complex:
+        """exp(sign*2*pi*i*m/N) (long double, octant-reduced, rounded to double)."""
+        re, im = ctypes.c_double(), ctypes.c_double()
+        self._lib.oracle_twiddle(m, N, sign, ctypes.byref(re), ctypes.byref(im))
+        return complex(re.value, im.value)
+
+    def dft_naive(self, x, sign: int = -1) -> np.ndarray:
+        """Direct O(N^2) evaluation of Eq. 1."""
+        x = self._c128(x)
+        X = np.empty_like(x)
+        rc = self._lib.oracle_dft_naive(self._dp(x), self._dp(X), x.size, sign)
+        if rc:
+            raise ValueError(f"oracle_dft_naive failed ({rc})")
+        return X
+
+    def fft_radix2(self, x, sign: int = -1) -> np.ndarray:
+        """Iterative radix-2 Cooley-Tukey (Eqs. 4-6); returns a new array."""
+        X = self._c128(x).copy()
+        rc = self._lib.oracle_fft_radix2(self._dp(X), X.size, sign)
+        if rc:
+            raise ValueError(f"oracle_fft_radix2 failed ({rc})")
+        return X
+
+    def dft(self, x, sign: int = -1) -> np.ndarray:
+        """Naive DFT for N <= 4096, radix-2 FFT above (N a power of two)."""
+        x = self._c128(x)
+        if x.size <= 4096:
+            return self.dft_naive(x, sign)
+        return self.fft_radix2(x, sign)
+
+    def gen_uniform(self, seed: int, N: int, n0: int = 0) -> np.ndarray:
+        """The oracle's own SplitMix64 uniform[-1,1) re/im input, elements n0..n0+N-1."""
+        out = np.empty(N, dtype=np.complex128)
+        self._lib.oracle_gen_uniform(seed & (2**64 - 1), n0, N, self._dp(out))
+        return out
+
+    def splitmix64(self, seed: int, i: int) -> int:
+        return int(self._lib.oracle_splitmix64(seed & (2**64 - 1), i))
+
+    def dft_bins_uniform(self, seed: int, N: int, ks, sign: int = -1) -> np.ndarray:
+        """X[k] for the listed k with x = gen_uniform(seed, N) regenerated on the fly."""
+        ks = np.ascontiguousarray(np.asarray(ks, dtype=np.int64))
+        X = np.empty(ks.size, dtype=np.complex128)
+        rc = self._lib.oracle_dft_bins_uniform(seed & (2**64 - 1), N, sign,
+                                               ks.ctypes.data_as(_c_i64p), ks.size, self._dp(X))
+        if rc:
+            raise ValueError(f"oracle_dft_bins_uniform failed ({rc})")
+        return X
+
+    def dft_bins(self, x, ks, sign: int = -1) -> np.ndarray:
+        """X[k] for the listed k by the direct sum of Eq. 1 over an explicit x."""
+        x = self._c128(x)
+        ks = np.ascontiguousarray(np.asarray(ks, dtype=np.int64))
+        X = np.empty(ks.size, dtype=np.complex128)
+        rc = self._lib.oracle_dft_bins(self._dp(x), x.size, sign, ks.ctypes.data_as(_c_i64p),
+                                       ks.size, self._dp(X))
+        if rc:
+            raise ValueError(f"oracle_dft_bins failed ({rc})")
+        return X
+
+
+def rel_l2(F, Fe) -> float:
+    """Relative L2 error of Eq. 9 (Sec. 5.3), read with complex moduli:
+    sqrt(sum |F_k - Fe_k|^2) / sqrt(sum |Fe_k|^2)."""
+    F = np.asarray(F, dtype=np.complex128)
+    Fe = np.asarray(Fe, dtype=np.complex128)
+    num = np.sqrt(np.sum(np.abs(F - Fe) ** 2))
+    den = np.sqrt(np.sum(np.abs(Fe) ** 2))
+    return float(num / den) if den > 0 else float(num)
+
+
+_default: Oracle | None = None
+
+
+def get() -> Oracle:
+    """The real oracle (no planted mistake), built on first use."""
+    global _default
+    if _default is None:
+        _default = Oracle(0)
+    return _default

@@ -1,0 +1,293 @@
+"""Pins for the CPU oracle: facts fixed by the paper and by mathematics.
+
+Each pin takes an ``oracle.Oracle`` and raises AssertionError if the oracle
+disagrees with something that does not come from the oracle itself:
+closed forms of Eq. 1 (Sec. 1), multiple-precision brute force (mpmath),
+numpy's independent FFT, invariants of the DFT (Parseval, linearity, shift,
+round trip, conjugate symmetry), and the generator's published known-answer
+vector.  ``test_oracle_pins.py`` runs them on the real oracle;
+``test_oracle_mutants.py`` runs them on builds with a planted mistake and
+requires every mistake to fail at least one pin.
+"""
+from __future__ import annotations
+
+import os
+
+import mpmath
+import numpy as np
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def _mp_dft(x, sign, dps=40):
+    """Eq. 1 evaluated term by term in mpmath at `dps` digits."""
+    with mpmath.workdps(dps):
+        N = len(x)
+        xs = [mpmath.mpc(complex(v).real, complex(v).imag) for v in x]
+        out = []
+        for k in range(N):
+            acc = mpmath.mpc(0)
+            for n in range(N):
+                acc += xs[n] * mpmath.expjpi(sign * 2 * mpmath.mpf(n * k % N) / N)
+            out.append(complex(acc))
+    return np.array(out, dtype=np.complex128)
+
+
+def _rel(a, b):
+    a = np.asarray(a, np.complex128)
+    b = np.asarray(b, np.complex128)
+    d = np.linalg.norm(b)
+    return float(np.linalg.norm(a - b) / (d if d > 0 else 1.0))
+
+
+def _rng(seed):
+    return np.random.default_rng(seed)
+
+
+def _rand_c(n, seed):
+    g = _rng(seed)
+    return g.uniform(-1, 1, n) + 1j * g.uniform(-1, 1, n)
+
+
+# --------------------------------------------------------------------------
+# Naive DFT (Eq. 1 by direct summation)
+# --------------------------------------------------------------------------
+def pin_naive_impulse_at_zero(o):
+    """x = delta_0 gives X[k] = 1 for every k, exactly."""
+    for N in (1, 2, 3, 8, 64, 1000, 4096):
+        x = np.zeros(N, np.complex128)
+        x[0] = 1
+        for sign in (-1, 1):
+            X = o.dft_naive(x, sign)
+            assert np.array_equal(X, np.ones(N)), (N, sign)
+
+
+def pin_naive_shifted_impulse(o):
+    """x = delta_m gives X[k] = exp(sign*2*pi*i*m*k/N) (mpmath at 40 digits)."""
+    for N, m in ((8, 3), (12, 5), (64, 17), (1024, 333)):
+        x = np.zeros(N, np.complex128)
+        x[m] = 1
+        for sign in (-1, 1):
+            X = o.dft_naive(x, sign)
+            with mpmath.workdps(40):
+                ref = np.array([complex(mpmath.expjpi(sign * 2 * mpmath.mpf(m * k % N) / N))
+                                for k in range(N)])
+            assert np.max(np.abs(X - ref)) <= 2e-16, (N, m, sign, np.max(np.abs(X - ref)))
+
+
+def pin_naive_constant(o):
+    """x = c gives X = N*c at k = 0 and 0 elsewhere."""
+    c = 0.625 - 0.375j
+    for N in (7, 16, 256, 4096):
+        x = np.full(N, c, np.complex128)
+        for sign in (-1, 1):
+            X = o.dft_naive(x, sign)
+            assert abs(X[0] - N * c) <= 1e-13 * N, (N, sign)
+            assert np.max(np.abs(X[1:])) <= 1e-13 * N if N > 1 else True, (N, sign)
+
+
+def pin_naive_single_tone(o):
+    """x_n = exp(-sign*2*pi*i*f*n/N) gives N at k = f and 0 elsewhere."""
+    for N, f in ((16, 3), (100, 37), (2048, 999)):
+        for sign in (-1, 1):
+            with mpmath.workdps(30):
+                x = np.array([complex(mpmath.expjpi(-sign * 2 * mpmath.mpf(f * n % N) / N))
+                              for n in range(N)])
+            X = o.dft_naive(x, sign)
+            ref = np.zeros(N, np.complex128)
+            ref[f] = N
+            assert np.max(np.abs(X - ref)) <= 1e-12 * N, (N, f, sign)
+
+
+def pin_naive_brute_force(o):
+    """Random inputs, any N (not only powers of two), vs mpmath term-by-term sums."""
+    for i, N in enumerate((1, 2, 3, 5, 8, 12, 16, 31, 32)):
+        x = _rand_c(N, 100 + i)
+        for sign in (-1, 1):
+            assert _rel(o.dft_naive(x, sign), _mp_dft(x, sign)) <= 1e-15, (N, sign)
+
+
+def pin_naive_vs_numpy(o):
+    """Naive DFT vs numpy's pocketfft: fft for sign -1, N*ifft for sign +1."""
+    for e in range(0, 11):
+        N = 1 << e
+        x = _rand_c(N, 200 + e)
+        assert _rel(o.dft_naive(x, -1), np.fft.fft(x)) <= 1e-15 * max(e, 1), e
+        assert _rel(o.dft_naive(x, 1), N * np.fft.ifft(x)) <= 1e-15 * max(e, 1), e
+
+
+# --------------------------------------------------------------------------
+# Radix-2 FFT (Sec. 2.2, Eqs. 4-6)
+# --------------------------------------------------------------------------
+def pin_radix2_vs_naive(o):
+    """Radix-2 equals the direct sum for every N = 2^1 .. 2^12."""
+    for e in range(1, 13):
+        N = 1 << e
+        x = _rand_c(N, 300 + e)
+        for sign in (-1, 1):
+            assert _rel(o.fft_radix2(x, sign), o.dft_naive(x, sign)) <= 1e-15 * e, (e, sign)
+
+
+def pin_radix2_vs_numpy(o):
+    """Radix-2 vs numpy for N up to 2^18."""
+    for e in (1, 2, 3, 5, 9, 13, 16, 18):
+        N = 1 << e
+        x = _rand_c(N, 400 + e)
+        assert _rel(o.fft_radix2(x, -1), np.fft.fft(x)) <= 1e-15 * e, e
+        assert _rel(o.fft_radix2(x, 1), N * np.fft.ifft(x)) <= 1e-15 * e, e
+
+
+def pin_radix2_closed_forms(o):
+    """Impulse, shifted impulse, constant and tone at N = 2^16."""
+    N = 1 << 16
+    x = np.zeros(N, np.complex128)
+    x[0] = 1
+    assert np.max(np.abs(o.fft_radix2(x, -1) - 1)) <= 1e-15
+    x[:] = 0.5 + 0.25j
+    X = o.fft_radix2(x, -1)
+    assert abs(X[0] - N * (0.5 + 0.25j)) <= 1e-12 * N and np.max(np.abs(X[1:])) <= 1e-12 * N
+    m = 12345
+    x[:] = 0
+    x[m] = 1
+    k = np.arange(N)
+    with mpmath.workdps(30):
+        sel = [0, 1, 7, 4096, 33333, N - 1]
+        ref = np.array([complex(mpmath.expjpi(-2 * mpmath.mpf(m * kk % N) / N)) for kk in sel])
+    X = o.fft_radix2(x, -1)
+    assert np.max(np.abs(X[sel] - ref)) <= 1e-14
+    f = 4321
+    x = np.exp(2j * np.pi * ((f * k) % N) / N)
+    X = o.fft_radix2(x, -1)
+    ref = np.zeros(N, np.complex128)
+    ref[f] = N
+    assert np.max(np.abs(X - ref)) <= 1e-11 * N
+
+
+def pin_radix2_invariants(o):
+    """Parseval, linearity, shift theorem, round trip, real-input conjugate symmetry."""
+    N = 1 << 15
+    x = _rand_c(N, 500)
+    y = _rand_c(N, 501)
+    X = o.fft_radix2(x, -1)
+    Y = o.fft_radix2(y, -1)
+    # Parseval: sum |X|^2 = N sum |x|^2
+    assert abs(np.sum(np.abs(X) ** 2) - N * np.sum(np.abs(x) ** 2)) <= 1e-13 * N * np.sum(np.abs(x) ** 2)
+    # linearity
+    a, b = 0.75 - 0.5j, -1.25 + 2j
+    assert _rel(o.fft_radix2(a * x + b * y, -1), a * X + b * Y) <= 1e-14
+    # shift: x[n - m] -> X[k] * exp(-2*pi*i*m*k/N)
+    m = 1234
+    k = np.arange(N)
+    ramp = np.exp(-2j * np.pi * ((m * k) % N) / N)
+    assert _rel(o.fft_radix2(np.roll(x, m), -1), X * ramp) <= 1e-13
+    # round trip: F+(F-(x)) / N = x
+    assert _rel(o.fft_radix2(X, 1) / N, x) <= 1e-14
+    # real input: X[(N-k) mod N] = conj(X[k])  (Eq. 8 read with the index N-k)
+    r = x.real.copy()
+    R = o.fft_radix2(r, -1)
+    assert np.max(np.abs(R[(-k) % N] - np.conj(R))) <= 1e-12 * np.sqrt(N)
+    assert abs(R[0].imag) <= 1e-12 and abs(R[N // 2].imag) <= 1e-12
+
+
+# --------------------------------------------------------------------------
+# Twiddle factors
+# --------------------------------------------------------------------------
+def pin_twiddle_dyadic(o):
+    """exp(-2*pi*i*m/N) at the eight octant points is known in closed form."""
+    h = np.sqrt(0.5)
+    known = [1, h - 1j * h, -1j, -h - 1j * h, -1, -h + 1j * h, 1j, h + 1j * h]
+    for N in (8, 64, 1 << 20, 1 << 33):
+        for j in range(8):
+            w = o.twiddle(j * N // 8, N, -1)
+            assert abs(w - known[j]) <= 1.2e-16, (N, j, w)
+            w = o.twiddle(j * N // 8, N, 1)
+            assert abs(w - np.conj(known[j])) <= 1.2e-16, (N, j, w)
+
+
+def pin_twiddle_vs_mpmath(o):
+    """Random phases m/N vs mpmath at 40 digits, to about one ulp."""
+    g = _rng(7)
+    for _ in range(200):
+        e = int(g.integers(1, 34))
+        N = 1 << e
+        m = int(g.integers(0, N))
+        for sign in (-1, 1):
+            w = o.twiddle(m, N, sign)
+            with mpmath.workdps(40):
+                ref = complex(mpmath.expjpi(sign * 2 * mpmath.mpf(m) / N))
+            assert abs(w - ref) <= 2.3e-16, (m, N, sign)
+
+
+# --------------------------------------------------------------------------
+# Input generator (published SplitMix64 definition)
+# --------------------------------------------------------------------------
+def _kat():
+    vals = []
+    with open(os.path.join(GOLDEN, "splitmix64_kat.txt")) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            a, b = line.split()
+            if a == "seed":
+                seed = int(b)
+            else:
+                vals.append((int(a), int(b)))
+    return seed, vals
+
+
+def pin_rng_known_answer(o):
+    """SplitMix64 reproduces the generator's published known-answer vector."""
+    seed, vals = _kat()
+    for i, v in vals:
+        assert o.splitmix64(seed, i) == v, (i, o.splitmix64(seed, i), v)
+
+
+def pin_rng_uniform_mapping(o):
+    """u = top 53 bits * 2^-53 and value 2u - 1, from the known-answer outputs."""
+    seed, vals = _kat()
+    x = o.gen_uniform(seed, 3)
+    for i, v in vals[:6]:
+        n, c = divmod(i, 2)
+        if n < 3:
+            got = x[n].real if c == 0 else x[n].imag
+            assert got == 2.0 * ((v >> 11) * 2.0 ** -53) - 1.0, (i, got)
+    y = o.gen_uniform(5, 1 << 16)
+    assert np.all(np.abs(y.real) <= 1) and np.all(y.real < 1) and np.all(y.imag < 1)
+    assert abs(np.mean(y.real)) < 0.02 and abs(np.mean(y.imag)) < 0.02
+    assert abs(np.var(y.real) - 1 / 3) < 0.01
+    # windows are consistent: elements n0.. of the stream
+    z = o.gen_uniform(5, 100, n0=1000)
+    assert np.array_equal(z, y[1000:1100])
+
+
+# --------------------------------------------------------------------------
+# Sampled bins
+# --------------------------------------------------------------------------
+def pin_bins_vs_radix2(o):
+    """Direct sums at selected k equal the full transform's entries."""
+    for e in (4, 11, 14):
+        N = 1 << e
+        ks = np.array(sorted({0, 1, N // 2, N - 1, 5 % N, (N // 3) | 1}), np.int64)
+        x = o.gen_uniform(11, N)
+        for sign in (-1, 1):
+            full = np.fft.fft(x) if sign == -1 else N * np.fft.ifft(x)
+            scale = np.linalg.norm(full) / np.sqrt(N)
+            Xb = o.dft_bins_uniform(11, N, ks, sign)
+            assert np.max(np.abs(Xb - full[ks])) <= 1e-14 * scale * e, (e, sign)
+            Xe = o.dft_bins(x, ks, sign)
+            assert np.max(np.abs(Xe - full[ks])) <= 1e-14 * scale * e, (e, sign)
+
+
+def pin_bins_tone(o):
+    """A pure tone at f gives N at k = f and ~0 at other sampled bins."""
+    N = 1 << 16
+    f = 3001
+    n = np.arange(N)
+    x = np.exp(2j * np.pi * ((f * n) % N) / N)
+    X = o.dft_bins(x, [f, 0, 1, 777, N - 1], -1)
+    assert abs(X[0] - N) <= 1e-10 * N
+    assert np.max(np.abs(X[1:])) <= 1e-10 * N
+
+
+ALL_PINS = [v for k, v in sorted(globals().items()) if k.startswith("pin_")]
