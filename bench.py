@@ -1,0 +1,395 @@
+#!/usr/bin/env python3
+"""Throughput of the in-place 1-D complex DFT on GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload c2|c3|c1|c4]
+                    [--impl ours|reference]
+
+Default workload (the headline configuration): one step = a forward DFT
+(sign -1, Eq. 1) followed by the normalised inverse (sign +1, times 1/N) of
+N = 2^30 complex128 points in place (16 GiB), input uniform[-1,1) re/im plus
+64 seeded tones.  value = 5*N*log2(N) flop per transform x transforms / time
+(GFLOP/s, BASELINE metric), whole job.  The input (16 GiB) is larger than the
+129 MB L2, so no flush is needed between timed iterations.
+
+--impl reference times the CPU oracle (the FP64 radix-2 FFT, as it stands)
+on the host cores on a bounded sample of the same workload.
+
+Multi-GPU: the transform does not shard across GPUs in this build (one FFT
+per GPU); under torchrun every rank runs an independent replica ("replicas
+only") and value is the sum over ranks divided by the max time over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "5N·log2N GFLOP/s + HBM GB/s, in-place 1D FFT; FP32 vs FP64 at stated error"
+
+WORKLOADS = {
+    "c2": dict(log2n=30, dtype="c128", seed=2, tones=64, fwd_inv=True, gauss=False,
+               desc="complex128 N=2^30 in place, forward then normalised inverse; "
+                    "uniform[-1,1) re/im + 64 seeded tones"),
+    "c3": dict(log2n=33, dtype="c128", seed=3, tones=0, fwd_inv=False, gauss=False,
+               desc="complex128 N=2^33 (128 GiB) in place, one transform per step "
+                    "(forward / normalised inverse alternating); uniform[-1,1) re/im"),
+    "c1": dict(log2n=20, dtype="c128", seed=1, tones=0, fwd_inv=False, gauss=False,
+               desc="complex128 N=2^20 in place, one transform per step; uniform[-1,1) re/im"),
+    "c4": dict(log2n=31, dtype="c64", seed=4, tones=0, fwd_inv=False, gauss=True,
+               desc="complex64 N=2^31 in place, one transform per step; Gaussian(0,1) re/im"),
+}
+DTYPE_NAME = {"c128": "df32 (double-float f32 pairs; complex128 in/out)", "c64": "f32 (complex64)"}
+
+
+def flops(n: int) -> float:
+    return 5.0 * n * math.log2(n)
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (cpu_baseline leg and --impl reference)
+# ---------------------------------------------------------------------------
+def oracle_time(log2n: int, seed: int, reps: int = 1):
+    """Time `reps` forward radix-2 transforms of 2^log2n points on the host."""
+    import oracle
+    o = oracle.get()
+    x = o.gen_uniform(seed, 1 << log2n)
+    best = None
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        o.fft_radix2(x, -1)
+        dt = time.perf_counter() - t0
+        best = dt if best is None else min(best, dt)
+    return best, o.threads
+
+
+def oracle_sample_log2n(target_s: float, cap: int) -> int:
+    """Largest size <= 2^cap whose oracle transform fits in about target_s."""
+    t20, _ = oracle_time(20, 1)
+    for e in range(cap, 19, -1):
+        est = t20 * (2.0 ** (e - 20)) * (e / 20.0) * 1.3
+        if est <= target_s:
+            return e
+    return 20
+
+
+def run_reference(args, wl):
+    import oracle  # noqa: F401
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    K, W = args.steps, args.warmup
+    budget = 150.0 / max(K + W, 1)
+    e = oracle_sample_log2n(budget, wl["log2n"])
+    times = []
+    cores = None
+    for i in range(W + K):
+        dt, cores = oracle_time(e, wl["seed"])
+        if i >= W:
+            times.append(dt)
+    tps = 2 if wl["fwd_inv"] else 1
+    ms = 1e3 * sum(times) / len(times) * tps
+    value = tps * flops(1 << e) / (ms * 1e-3) / 1e9
+    sample = (f"FP64 radix-2 oracle, forward transform of N=2^{e} (of the 2^{wl['log2n']} workload), "
+              f"seeded uniform input, timed per transform; a step = {tps} transform(s)")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": args.gpus,
+        "steps": K, "warmup": W, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": config_of(wl),
+        "cpu_baseline": {"value": value, "unit": "GFLOP/s", "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def config_of(wl):
+    return {"workload": wl["desc"], "N": 1 << wl["log2n"], "log2N": wl["log2n"],
+            "element": "complex128" if wl["dtype"] == "c128" else "complex64",
+            "transforms_per_step": 2 if wl["fwd_inv"] else 1, "in_place": True,
+            "l2_between_steps": "inputs larger than L2 (no flush needed)" if wl["log2n"] >= 24
+            else "inputs fit in L2 (latency-bound size)",
+            "seed": wl["seed"], "parallelism": "replicas only (one transform per GPU)"}
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def run_ours(args, wl):
+    import torch
+    import torch.distributed as dist
+
+    import paper_1409_5757_gb300 as efft
+    from paper_1409_5757_gb300 import build as _build
+    from paper_1409_5757_gb300 import inputs
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+    if rank == 0:
+        _build.build()
+    if world > 1:
+        dist.barrier()
+
+    N = 1 << wl["log2n"]
+    c128 = wl["dtype"] == "c128"
+    tdt = torch.complex128 if c128 else torch.complex64
+    code = efft.EFFT_C128 if c128 else efft.EFFT_C64
+    S = 16 if c128 else 8
+
+    x = torch.empty(N, dtype=tdt, device=dev)
+    if wl["gauss"]:
+        inputs.fill_gaussian(x, wl["seed"])
+    else:
+        inputs.fill_uniform(x, wl["seed"])
+    if wl["tones"]:
+        f, a = inputs.tone_params(wl["seed"], N, wl["tones"])
+        inputs.add_tones(x, f, a)
+    torch.cuda.synchronize(dev)
+    ref_norm = None
+    keep = None
+    if N <= (1 << 30):
+        keep = x.clone()  # for the round-trip accuracy check after timing
+
+    fwd = efft.Plan(N, code, -1)
+    inv = efft.Plan(N, code, +1, efft.EFFT_FLAG_NORMALIZE)
+    stream = torch.cuda.current_stream(dev)
+    sp = stream.cuda_stream
+    tps = 2 if wl["fwd_inv"] else 1
+
+    def step(i):
+        if wl["fwd_inv"]:
+            fwd.execute(x.data_ptr(), sp)
+            inv.execute(x.data_ptr(), sp)
+        elif i % 2 == 0:
+            fwd.execute(x.data_ptr(), sp)
+        else:
+            inv.execute(x.data_ptr(), sp)
+
+    K, W = args.steps, args.warmup
+    for i in range(W):
+        step(i)
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+
+    sampler = ClockSampler(dev.index)
+    sampler.start()
+    time.sleep(0.3)
+    fwd.profile(True)
+    inv.profile(True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(K):
+        step(W + i)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    clocks = sampler.stop()
+    elapsed_ms = e0.elapsed_time(e1)
+    prof = {}
+    for p in (fwd, inv):
+        for k, (ms, n) in p.profile_read().items():
+            a = prof.setdefault(k, [0.0, 0])
+            a[0] += ms
+            a[1] += n
+    fwd.profile(False)
+    inv.profile(False)
+
+    if world > 1:
+        t = torch.tensor([elapsed_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+
+    ms_per_step = elapsed_ms / K
+    value = world * tps * flops(N) / (ms_per_step * 1e-3) / 1e9
+    hbm_passes = fwd.info()["hbm_passes"]
+    hbm_gbs = world * tps * hbm_passes * 2 * N * S / (ms_per_step * 1e-3) / 1e9
+
+    # accuracy: after W+K round trips the buffer should equal the input
+    accuracy = None
+    if keep is not None and wl["fwd_inv"]:
+        num, den = inputs.diff_norms(x, keep, 1.0)
+        accuracy = {"roundtrip_rel_l2_after_all_steps": math.sqrt(num / den), "round_trips": W + K,
+                    "tolerance_per_round_trip": 2e-14 * wl["log2n"] if c128 else 4e-6 * wl["log2n"]}
+
+    # roofline of the dominant kernel
+    peak, peak_kind = peaks()
+    dom = max(prof.items(), key=lambda kv: kv[1][0]) if prof else None
+    roofline = None
+    if dom:
+        name, (tot_ms, nl) = dom
+        per_launch_s = tot_ms / nl * 1e-3
+        alg_bytes = (1 if name == "range_scan" else 2) * N * S
+        achieved = alg_bytes / per_launch_s / 1e9
+        roofline = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                    "frac": achieved / peak, "traffic": None,
+                    "peak_kind": f"{peak_kind} STREAM-style copy (MEASURED_PEAKS.json hbm_gbs)",
+                    "per_launch_ms": tot_ms / nl, "algorithmic_bytes_per_launch": alg_bytes,
+                    "kernels_ms_per_step": {k: v[0] / K for k, v in prof.items()}}
+    launches = sum(v[1] for v in prof.values())
+
+    # end to end: host buffers through efft_execute_host (H2D + transform + D2H)
+    e2e = None
+    if N * S <= (32 << 30) and not args.no_e2e:
+        host = torch.empty(N, dtype=tdt, pin_memory=True)
+        host.copy_(keep if keep is not None else x)
+        Ke = max(2, min(K, 5))
+        fwd.execute_host(host.data_ptr(), x.data_ptr(), sp)  # warm
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for i in range(Ke):
+            if wl["fwd_inv"]:
+                fwd.execute_host(host.data_ptr(), x.data_ptr(), sp)
+                inv.execute_host(host.data_ptr(), x.data_ptr(), sp)
+            elif i % 2 == 0:
+                fwd.execute_host(host.data_ptr(), x.data_ptr(), sp)
+            else:
+                inv.execute_host(host.data_ptr(), x.data_ptr(), sp)
+        dt = (time.perf_counter() - t0) / Ke
+        e2e = {"value": world * tps * flops(N) / dt / 1e9, "unit": "GFLOP/s",
+               "h2d_bytes_per_step": tps * N * S, "d2h_bytes_per_step": tps * N * S,
+               "ms_per_step": dt * 1e3, "api": "efft_execute_host (pinned host buffer)"}
+        del host
+    elif not args.no_e2e:
+        e2e = {"value": None, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0,
+               "skipped": "pinned host copy of the 128 GiB array is not made on this host"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        e = wl["log2n"] if wl["log2n"] <= 30 else 30
+        e = min(e, oracle_sample_log2n(25.0, e))
+        dt, cores = oracle_time(e, wl["seed"])
+        cpu = {"value": flops(1 << e) / dt / 1e9, "unit": "GFLOP/s", "cores": cores, "kind": "oracle",
+               "sample": f"one forward FP64 radix-2 oracle transform of N=2^{e} (same seeded uniform input "
+                         f"family) on the host cores, {dt:.1f} s"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": K, "warmup": W,
+            "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": DTYPE_NAME[wl["dtype"]], "data": "synthetic", "config": config_of(wl),
+            "hbm_gbs": hbm_gbs, "hbm_passes_per_transform": hbm_passes,
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+            "clocks": clocks, "accuracy": accuracy, "impl": "ours",
+        }
+        print(json.dumps(line), flush=True)
+    for p in (fwd, inv):
+        p.destroy()
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=None)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg")
+    ap.add_argument("--log2n", type=int, default=None,
+                    help="override the workload's size (profiling captures on a smaller case)")
+    args = ap.parse_args()
+    wl = dict(WORKLOADS[args.workload])
+    if args.log2n is not None:
+        wl["log2n"] = args.log2n
+        wl["desc"] = wl["desc"].replace("2^30", f"2^{args.log2n}").replace("2^33", f"2^{args.log2n}")
+    if args.steps is None:
+        args.steps = {"c2": 20, "c3": 6, "c1": 200, "c4": 40}[args.workload]
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args, wl)
+    return run_ours(args, wl)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -131,8 +131,13 @@ def rel_l2(F, Fe) -> float:
     sqrt(sum |F_k - Fe_k|^2) / sqrt(sum |Fe_k|^2)."""
     F = np.asarray(F, dtype=np.complex128)
     Fe = np.asarray(Fe, dtype=np.complex128)
-    num = np.sqrt(np.sum(np.abs(F - Fe) ** 2))
-    den = np.sqrt(np.sum(np.abs(Fe) ** 2))
+    # both norms are taken of values divided by max|Fe| (the ratio is
+    # unchanged) so that magnitudes near the binary64 limits do not overflow
+    s = float(np.max(np.abs(Fe))) if Fe.size else 0.0
+    if not np.isfinite(s) or s == 0.0:
+        s = 1.0
+    num = np.sqrt(np.sum(np.abs((F - Fe) / s) ** 2))
+    den = np.sqrt(np.sum(np.abs(Fe / s) ** 2))
     return float(num / den) if den > 0 else float(num)
 
 

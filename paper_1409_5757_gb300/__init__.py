@@ -1,0 +1,209 @@
+"""Python binding of libefft.so: the in-place 1-D complex DFT on one GB300.
+
+Argument marshalling only: every step of the transform runs in the CUDA
+kernels of ``csrc/``.  PyTorch supplies device memory and streams.  There is
+no CPU fallback: if the compiled library is missing, importing the binding's
+functions raises.
+
+    import torch, paper_1409_5757_gb300 as efft
+    x = torch.randn(1 << 20, dtype=torch.complex128, device="cuda")
+    efft.fft_(x)            # X[k] = sum_n x[n] exp(-2*pi*i*n*k/N), in place
+    efft.fft_(x, sign=+1)   # conjugate-sign transform (x * N after both)
+
+The C ABI is documented in include/efft.h.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+
+EFFT_C64 = 0
+EFFT_C128 = 1
+EFFT_FLAG_DIGIT_REVERSED_OUT = 0x1
+EFFT_FLAG_NORMALIZE = 0x2
+PROFILE_SLOTS = ("range_scan", "pass0", "pass1", "pass2", "pass3", "digit_swap", "direct_small")
+EFFT_MAX_LOG2N = 33
+
+STATUS = {
+    0: "EFFT_OK", 1: "EFFT_ERR_INVALID_SIZE", 2: "EFFT_ERR_INVALID_DTYPE", 3: "EFFT_ERR_INVALID_SIGN",
+    4: "EFFT_ERR_INVALID_PTR", 5: "EFFT_ERR_MISALIGNED", 6: "EFFT_ERR_ALLOC", 7: "EFFT_ERR_LAUNCH",
+    8: "EFFT_ERR_TIMEOUT", 9: "EFFT_ERR_UNSUPPORTED", 10: "EFFT_ERR_INVALID_PLAN", 11: "EFFT_ERR_CUDA",
+    12: "EFFT_ERR_INVALID_FLAGS",
+}
+
+# every entry point declared in include/efft.h: name -> (restype, argtypes)
+_vp = ctypes.c_void_p
+_SIGNATURES = {
+    "efft_plan_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_uint64, ctypes.c_int, ctypes.c_int,
+                                        ctypes.c_uint32]),
+    "efft_execute": (ctypes.c_int, [_vp, _vp, _vp]),
+    "efft_execute_host": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "efft_plan_destroy": (ctypes.c_int, [_vp]),
+    "efft_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "efft_version": (ctypes.c_int, []),
+    "efft_plan_radices": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.c_int,
+                                         ctypes.POINTER(ctypes.c_int)]),
+    "efft_plan_info": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_uint64)]),
+    "efft_plan_profile": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "efft_plan_profile_read": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int),
+                                              ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+}
+
+
+class EfftError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = status
+        name = STATUS.get(status, str(status))
+        msg = _lib().efft_strerror(status).decode() if _LIB is not None else name
+        super().__init__(f"{what}: {name} ({msg})" if what else f"{name} ({msg})")
+
+
+_LIB = None
+_LIB_LOCK = threading.Lock()
+
+
+def lib_path() -> str:
+    return os.path.join(PKG, "libefft.so")
+
+
+def _lib():
+    """Load libefft.so (built by build.py / __graft_entry__.build()); raise if absent."""
+    global _LIB
+    if _LIB is None:
+        with _LIB_LOCK:
+            if _LIB is None:
+                path = lib_path()
+                if not os.path.exists(path):
+                    raise RuntimeError(f"{path} is missing: run paper_1409_5757_gb300.build.build() "
+                                       "(there is no CPU fallback)")
+                lib = ctypes.CDLL(path)
+                for name, (res, args) in _SIGNATURES.items():
+                    f = getattr(lib, name)
+                    f.restype = res
+                    f.argtypes = args
+                _LIB = lib
+    return _LIB
+
+
+def _check(status: int, what: str):
+    if status != 0:
+        raise EfftError(status, what)
+
+
+class Plan:
+    """Owning wrapper of an efft_plan_t (efft_plan_create / efft_plan_destroy)."""
+
+    def __init__(self, n: int, dtype: int = EFFT_C128, sign: int = -1, flags: int = 0):
+        self._h = _vp()
+        _check(_lib().efft_plan_create(ctypes.byref(self._h), int(n), int(dtype), int(sign), int(flags)),
+               "efft_plan_create")
+        self.n, self.dtype, self.sign, self.flags = int(n), int(dtype), int(sign), int(flags)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def execute(self, data_ptr: int, stream: int = 0) -> None:
+        _check(_lib().efft_execute(self._h, _vp(data_ptr), _vp(stream)), "efft_execute")
+
+    def execute_host(self, host_ptr: int, dev_ptr: int, stream: int = 0) -> None:
+        _check(_lib().efft_execute_host(self._h, _vp(host_ptr), _vp(dev_ptr), _vp(stream)), "efft_execute_host")
+
+    def radices(self) -> list[int]:
+        arr = (ctypes.c_int * 8)()
+        p = ctypes.c_int()
+        _check(_lib().efft_plan_radices(self._h, arr, 8, ctypes.byref(p)), "efft_plan_radices")
+        return [arr[i] for i in range(p.value)]
+
+    def info(self) -> dict:
+        hp = ctypes.c_double()
+        tb = ctypes.c_uint64()
+        _check(_lib().efft_plan_info(self._h, ctypes.byref(hp), ctypes.byref(tb)), "efft_plan_info")
+        return {"hbm_passes": hp.value, "table_bytes": tb.value}
+
+    def profile(self, enable: bool = True) -> None:
+        """Start (clearing old records) or stop per-launch CUDA-event timing."""
+        _check(_lib().efft_plan_profile(self._h, 1 if enable else 0), "efft_plan_profile")
+
+    def profile_read(self) -> dict:
+        """{slot name: (total ms, launches)} for the executes since profile(True)."""
+        ms = (ctypes.c_double * 8)()
+        cnt = (ctypes.c_int * 8)()
+        ns = ctypes.c_int()
+        _check(_lib().efft_plan_profile_read(self._h, ms, cnt, 8, ctypes.byref(ns)), "efft_plan_profile_read")
+        return {PROFILE_SLOTS[i]: (ms[i], cnt[i]) for i in range(min(ns.value, len(PROFILE_SLOTS))) if cnt[i]}
+
+    def destroy(self) -> None:
+        if self._h:
+            _check(_lib().efft_plan_destroy(self._h), "efft_plan_destroy")
+            self._h = _vp()
+
+    def __del__(self):
+        try:
+            if self._h and _LIB is not None:
+                _LIB.efft_plan_destroy(self._h)
+        except Exception:
+            pass
+
+
+_PLANS: dict = {}
+_PLANS_LOCK = threading.Lock()
+
+
+def get_plan(n: int, dtype: int, sign: int = -1, flags: int = 0) -> Plan:
+    """Cached plan for (device, N, dtype, sign, flags)."""
+    import torch
+    key = (torch.cuda.current_device(), int(n), int(dtype), int(sign), int(flags))
+    with _PLANS_LOCK:
+        p = _PLANS.get(key)
+        if p is None:
+            p = Plan(n, dtype, sign, flags)
+            _PLANS[key] = p
+    return p
+
+
+def clear_plans() -> None:
+    with _PLANS_LOCK:
+        for p in _PLANS.values():
+            p.destroy()
+        _PLANS.clear()
+
+
+def _dtype_code(t) -> int:
+    import torch
+    if t.dtype == torch.complex128:
+        return EFFT_C128
+    if t.dtype == torch.complex64:
+        return EFFT_C64
+    raise TypeError(f"efft: unsupported dtype {t.dtype} (complex64 or complex128)")
+
+
+def fft_(t, sign: int = -1, flags: int = 0, stream=None):
+    """In-place DFT of a contiguous 1-D CUDA complex tensor; returns t."""
+    import torch
+    if not t.is_cuda:
+        raise ValueError("efft.fft_: tensor must be on a CUDA device")
+    if not t.is_contiguous():
+        raise ValueError("efft.fft_: tensor must be contiguous")
+    code = _dtype_code(t)
+    with torch.cuda.device(t.device):
+        plan = get_plan(t.numel(), code, sign, flags)
+        s = stream if stream is not None else torch.cuda.current_stream(t.device)
+        plan.execute(t.data_ptr(), s.cuda_stream)
+    return t
+
+
+def fft(t, sign: int = -1):
+    """Out-of-place convenience: clone then fft_."""
+    return fft_(t.clone(), sign)
+
+
+def version() -> int:
+    return _lib().efft_version()
+
+
+__all__ = ["Plan", "EfftError", "fft_", "fft", "get_plan", "clear_plans", "version", "lib_path",
+           "EFFT_C64", "EFFT_C128", "EFFT_FLAG_DIGIT_REVERSED_OUT", "EFFT_FLAG_NORMALIZE"]

@@ -1,0 +1,524 @@
+// efft.cu -- plan creation, pass schedule and the C ABI of include/efft.h.
+//
+// Host side of the in-place multi-pass DFT.  A plan fixes the radices
+// N = R_0 * ... * R_{p-1} (the paper's splits, Sec. 3, restated as
+// mixed-radix passes), owns the O(sqrt N) twiddle tables that the paper's
+// constructor precomputes once (Sec. 3.1, Listing 3) and a 16-byte state
+// word; an execute enqueues the pass kernels on the caller's stream.
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstdint>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <set>
+#include <vector>
+
+#include "../../include/efft.h"
+#include "efft_kernels.cuh"
+
+using namespace efft;
+
+namespace {
+
+constexpr uint32_t kMagic = 0xEFF71409u;
+constexpr int kLog2CtaC128 = 12;  // 4096 complex128 elements per CTA (64 KiB)
+constexpr int kLog2CtaC64 = 13;   // 8192 complex64 elements per CTA (64 KiB)
+constexpr int kMaxPasses = 4;
+
+struct Pass {
+  int log2R, log2s, log2L, log2C, kind;
+  uint64_t grid;
+  int threads;
+  size_t smem;
+};
+
+}  // namespace
+
+struct efft_plan_s {
+  uint32_t magic;
+  int device;
+  uint64_t n;
+  int log2n;
+  int dtype;
+  int sign;
+  uint32_t flags;
+  int npasses;
+  Pass pass[kMaxPasses];
+  bool small;             // N <= 8: direct-sum kernel
+  bool permute;           // final digit swap enabled
+  int perm_log2A, perm_log2B;
+  int twB;
+  float4* w2048;
+  float4* tw_lo;
+  float4* tw_hi;
+  uint32_t* state;
+  uint64_t table_bytes;
+  // profiling: CUDA event pairs recorded around each launch
+  bool profiling;
+  struct Rec { int slot; cudaEvent_t a, b; };
+  std::vector<Rec>* recs;
+  std::vector<cudaEvent_t>* pool;
+};
+
+namespace {
+
+std::mutex g_mu;
+std::set<efft_plan_s*>* g_live = nullptr;  // leaked on purpose: safe at exit
+
+bool plan_is_live(efft_plan_s* p) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  return g_live && g_live->count(p) && p->magic == kMagic;
+}
+
+bool fault_injected(const char* what) {
+  const char* v = std::getenv("EFFT_FAULT_INJECT");
+  return v && std::strcmp(v, what) == 0;
+}
+
+int ilog2_u64(uint64_t n) {
+  int e = 0;
+  while ((1ull << e) < n) ++e;
+  return e;
+}
+
+// Radix schedule.  Symmetric radix lists (R_j = R_{p-1-j}) make the final
+// digit reversal an involution, so it can be done in place by tile swaps.
+int choose_radices(int e, int* r) {
+  if (e <= 3) return 0;  // handled by the direct-sum kernel (or identity)
+  if (e <= 11) { r[0] = e; return 1; }
+  if (e <= 22 && (e % 2) == 0) { r[0] = r[1] = e / 2; return 2; }
+  int a = (e - 4) / 2;
+  if (a > 11) a = 11;
+  r[0] = r[2] = a;
+  r[1] = e - 2 * a;
+  return 3;
+}
+
+template <class P, int KIND, int CTA>
+void set_smem_attr() {
+  cudaFuncSetAttribute(efft_pass<P, KIND, CTA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)((CTA + CTA / 16 + 1) * P::kElemBytes));
+}
+
+int init_kernels() {
+  static std::once_flag once;
+  static cudaError_t err = cudaSuccess;
+  std::call_once(once, [] {
+    set_smem_attr<PolicyDF, FIRST, 1 << kLog2CtaC128>();
+    set_smem_attr<PolicyDF, MID, 1 << kLog2CtaC128>();
+    set_smem_attr<PolicyDF, LAST, 1 << kLog2CtaC128>();
+    set_smem_attr<PolicyDF, SINGLE, 1 << kLog2CtaC128>();
+    set_smem_attr<PolicyF32, FIRST, 1 << kLog2CtaC64>();
+    set_smem_attr<PolicyF32, MID, 1 << kLog2CtaC64>();
+    set_smem_attr<PolicyF32, LAST, 1 << kLog2CtaC64>();
+    set_smem_attr<PolicyF32, SINGLE, 1 << kLog2CtaC64>();
+    err = cudaGetLastError();
+  });
+  return err == cudaSuccess ? EFFT_OK : EFFT_ERR_CUDA;
+}
+
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = false;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) return;
+    ok = (prev == dev) || (cudaSetDevice(dev) == cudaSuccess);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+int gen_table(float4* out, uint64_t count, uint64_t stride, int log2N, cudaStream_t st) {
+  const int bs = 256;
+  uint64_t grid = (count + bs - 1) / bs;
+  efft_twiddles<<<(unsigned)grid, bs, 0, st>>>(out, count, stride, log2N);
+  return cudaGetLastError() == cudaSuccess ? EFFT_OK : EFFT_ERR_LAUNCH;
+}
+
+void release_events(efft_plan_s* p) {
+  if (p->recs) {
+    for (auto& r : *p->recs) {
+      p->pool->push_back(r.a);
+      p->pool->push_back(r.b);
+    }
+    p->recs->clear();
+  }
+}
+
+void free_plan_memory(efft_plan_s* p) {
+  if (p->recs) {
+    release_events(p);
+    delete p->recs;
+    p->recs = nullptr;
+  }
+  if (p->pool) {
+    for (cudaEvent_t e : *p->pool) cudaEventDestroy(e);
+    delete p->pool;
+    p->pool = nullptr;
+  }
+  if (p->w2048) cudaFree(p->w2048);
+  if (p->tw_lo) cudaFree(p->tw_lo);
+  if (p->tw_hi) cudaFree(p->tw_hi);
+  if (p->state) cudaFree(p->state);
+  p->w2048 = p->tw_lo = p->tw_hi = nullptr;
+  p->state = nullptr;
+}
+
+cudaEvent_t take_event(efft_plan_s* p) {
+  cudaEvent_t e = nullptr;
+  if (!p->pool->empty()) {
+    e = p->pool->back();
+    p->pool->pop_back();
+  } else if (cudaEventCreate(&e) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return e;
+}
+
+// Records event a before a launch; returns the index of the record or -1.
+int prof_begin(efft_plan_s* p, int slot, cudaStream_t st) {
+  if (!p->profiling) return -1;
+  cudaEvent_t a = take_event(p), b = take_event(p);
+  if (!a || !b) return -1;
+  cudaEventRecord(a, st);
+  p->recs->push_back({slot, a, b});
+  return (int)p->recs->size() - 1;
+}
+void prof_end(efft_plan_s* p, int rec, cudaStream_t st) {
+  if (rec >= 0) cudaEventRecord((*p->recs)[rec].b, st);
+}
+
+template <class P, int CTA>
+cudaError_t launch_pass(const efft_plan_s* p, const Pass& ps, void* data, cudaStream_t st) {
+  PassArgs a;
+  a.log2R = ps.log2R;
+  a.log2C = ps.log2C;
+  a.log2s = ps.log2s;
+  a.log2L = ps.log2L;
+  a.log2N = p->log2n;
+  a.twB = p->twB;
+  a.w2048 = p->w2048;
+  a.tw_lo = p->tw_lo;
+  a.tw_hi = p->tw_hi;
+  a.state = p->state;
+  const uint32_t conj = (p->sign > 0) ? 1u : 0u;
+  a.conj_in = (ps.kind == FIRST || ps.kind == SINGLE) ? conj : 0u;
+  a.conj_out = (ps.kind == LAST || ps.kind == SINGLE) ? conj : 0u;
+  a.out_shift = ((p->flags & EFFT_FLAG_NORMALIZE) && (ps.kind == LAST || ps.kind == SINGLE)) ? p->log2n : 0;
+  dim3 grid((unsigned)ps.grid), block(ps.threads);
+  switch (ps.kind) {
+    case FIRST: efft_pass<P, FIRST, CTA><<<grid, block, ps.smem, st>>>(data, a); break;
+    case MID: efft_pass<P, MID, CTA><<<grid, block, ps.smem, st>>>(data, a); break;
+    case LAST: efft_pass<P, LAST, CTA><<<grid, block, ps.smem, st>>>(data, a); break;
+    default: efft_pass<P, SINGLE, CTA><<<grid, block, ps.smem, st>>>(data, a); break;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+int efft_version(void) { return EFFT_VERSION; }
+
+const char* efft_strerror(int s) {
+  switch (s) {
+    case EFFT_OK: return "success";
+    case EFFT_ERR_INVALID_SIZE: return "invalid size: N must be 2^e with 0 <= e <= 33";
+    case EFFT_ERR_INVALID_DTYPE: return "invalid dtype: expected EFFT_C64 or EFFT_C128";
+    case EFFT_ERR_INVALID_SIGN: return "invalid sign: expected -1 or +1";
+    case EFFT_ERR_INVALID_PTR: return "invalid pointer: NULL or not device memory of the plan's device";
+    case EFFT_ERR_MISALIGNED: return "misaligned pointer: must be aligned to the element size";
+    case EFFT_ERR_ALLOC: return "allocation failed";
+    case EFFT_ERR_LAUNCH: return "kernel launch or copy rejected";
+    case EFFT_ERR_TIMEOUT: return "a bounded device wait expired";
+    case EFFT_ERR_UNSUPPORTED: return "unsupported request";
+    case EFFT_ERR_INVALID_PLAN: return "invalid plan handle (NULL, destroyed or foreign)";
+    case EFFT_ERR_CUDA: return "CUDA runtime error (no device or bad context)";
+    case EFFT_ERR_INVALID_FLAGS: return "unknown flag bits";
+    default: return "unknown status";
+  }
+}
+
+int efft_plan_create(efft_plan_t* out, uint64_t n, int dtype, int sign, uint32_t flags) {
+  if (!out) return EFFT_ERR_INVALID_PTR;
+  *out = nullptr;
+  if (n == 0 || (n & (n - 1)) != 0 || n > (1ull << EFFT_MAX_LOG2N)) return EFFT_ERR_INVALID_SIZE;
+  if (dtype != EFFT_C64 && dtype != EFFT_C128) return EFFT_ERR_INVALID_DTYPE;
+  if (sign != -1 && sign != 1) return EFFT_ERR_INVALID_SIGN;
+  if (flags & ~EFFT_FLAG_ALL) return EFFT_ERR_INVALID_FLAGS;
+
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return EFFT_ERR_CUDA;
+  }
+  if (init_kernels() != EFFT_OK) return EFFT_ERR_CUDA;
+
+  efft_plan_s* p = new (std::nothrow) efft_plan_s();
+  if (!p) return EFFT_ERR_ALLOC;
+  std::memset(p, 0, sizeof(*p));
+  p->device = dev;
+  p->n = n;
+  p->log2n = ilog2_u64(n);
+  p->dtype = dtype;
+  p->sign = sign;
+  p->flags = flags;
+
+  const int e = p->log2n;
+  int r[kMaxPasses] = {0, 0, 0, 0};
+  p->npasses = choose_radices(e, r);
+  p->small = (e >= 1 && e <= 3);
+  const int log2cta = (dtype == EFFT_C128) ? kLog2CtaC128 : kLog2CtaC64;
+  const size_t eb = (dtype == EFFT_C128) ? 16 : 8;
+  int rest = e;
+  for (int j = 0; j < p->npasses; ++j) {
+    Pass& ps = p->pass[j];
+    ps.log2R = r[j];
+    rest -= r[j];
+    ps.log2s = rest;
+    ps.log2L = r[j] + rest;
+    int log2C = log2cta - r[j];
+    if (log2C > e - r[j]) log2C = e - r[j];
+    ps.log2C = log2C;
+    ps.grid = 1ull << (e - r[j] - log2C);
+    ps.threads = 1 << (r[j] + log2C - 4);
+    const size_t elems = 1ull << (r[j] + log2C);
+    ps.smem = (elems + elems / 16 + 1) * eb;
+    if (p->npasses == 1) ps.kind = SINGLE;
+    else if (j == 0) ps.kind = FIRST;
+    else if (j == p->npasses - 1) ps.kind = LAST;
+    else ps.kind = MID;
+  }
+  p->permute = (p->npasses >= 2) && !(flags & EFFT_FLAG_DIGIT_REVERSED_OUT);
+  if (p->npasses >= 2) {
+    p->perm_log2A = r[0];
+    p->perm_log2B = (p->npasses == 3) ? r[1] : 0;
+  }
+  p->twB = (e + 1) / 2;
+
+  if (fault_injected("alloc")) {
+    delete p;
+    return EFFT_ERR_ALLOC;
+  }
+  const uint64_t nlo = 1ull << p->twB, nhi = 1ull << (e - p->twB);
+  cudaStream_t st = nullptr;
+  int rc = EFFT_OK;
+  if (cudaMalloc(&p->w2048, 2048 * sizeof(float4)) != cudaSuccess ||
+      cudaMalloc(&p->tw_lo, nlo * sizeof(float4)) != cudaSuccess ||
+      cudaMalloc(&p->tw_hi, nhi * sizeof(float4)) != cudaSuccess ||
+      cudaMalloc(&p->state, 16) != cudaSuccess) {
+    rc = EFFT_ERR_ALLOC;
+  }
+  if (rc == EFFT_OK && cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) rc = EFFT_ERR_CUDA;
+  if (rc == EFFT_OK) rc = gen_table(p->w2048, 2048, 1, 11, st);
+  if (rc == EFFT_OK) rc = gen_table(p->tw_lo, nlo, 1, e, st);
+  if (rc == EFFT_OK) rc = gen_table(p->tw_hi, nhi, nlo, e, st);
+  if (rc == EFFT_OK && cudaMemsetAsync(p->state, 0, 16, st) != cudaSuccess) rc = EFFT_ERR_CUDA;
+  if (rc == EFFT_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = EFFT_ERR_CUDA;
+  if (st) cudaStreamDestroy(st);
+  if (rc != EFFT_OK) {
+    cudaGetLastError();
+    free_plan_memory(p);
+    delete p;
+    return rc;
+  }
+  p->table_bytes = (2048 + nlo + nhi) * sizeof(float4) + 16;
+  p->recs = new (std::nothrow) std::vector<efft_plan_s::Rec>();
+  p->pool = new (std::nothrow) std::vector<cudaEvent_t>();
+  if (!p->recs || !p->pool) {
+    free_plan_memory(p);
+    delete p;
+    return EFFT_ERR_ALLOC;
+  }
+  p->magic = kMagic;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_live) g_live = new std::set<efft_plan_s*>();
+    g_live->insert(p);
+  }
+  *out = p;
+  return EFFT_OK;
+}
+
+int efft_plan_destroy(efft_plan_t plan) {
+  if (!plan) return EFFT_OK;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_live || !g_live->count(plan) || plan->magic != kMagic) return EFFT_ERR_INVALID_PLAN;
+    g_live->erase(plan);
+  }
+  plan->magic = 0;
+  {
+    DeviceGuard g(plan->device);
+    free_plan_memory(plan);
+  }
+  delete plan;
+  return EFFT_OK;
+}
+
+int efft_plan_radices(efft_plan_t plan, int* log2_radices, int cap, int* npasses) {
+  if (!plan_is_live(plan)) return EFFT_ERR_INVALID_PLAN;
+  if (npasses) *npasses = plan->npasses;
+  if (log2_radices)
+    for (int j = 0; j < plan->npasses && j < cap; ++j) log2_radices[j] = plan->pass[j].log2R;
+  return EFFT_OK;
+}
+
+int efft_plan_info(efft_plan_t plan, double* hbm_passes, uint64_t* table_bytes) {
+  if (!plan_is_live(plan)) return EFFT_ERR_INVALID_PLAN;
+  if (hbm_passes) {
+    double hp = plan->npasses + (plan->permute ? 1.0 : 0.0);
+    if (plan->small) hp = 1.0;
+    if (plan->dtype == EFFT_C128 && plan->log2n > 0) hp += 0.5;
+    *hbm_passes = hp;
+  }
+  if (table_bytes) *table_bytes = plan->table_bytes;
+  return EFFT_OK;
+}
+
+static int check_buffer(const efft_plan_s* p, const void* data) {
+  if (!data) return EFFT_ERR_INVALID_PTR;
+  const uintptr_t align = (p->dtype == EFFT_C128) ? 16 : 8;
+  if (reinterpret_cast<uintptr_t>(data) % align) return EFFT_ERR_MISALIGNED;
+  cudaPointerAttributes attr;
+  if (cudaPointerGetAttributes(&attr, data) != cudaSuccess) {
+    cudaGetLastError();
+    return EFFT_ERR_INVALID_PTR;
+  }
+  if (attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged) return EFFT_ERR_INVALID_PTR;
+  if (attr.device != p->device) return EFFT_ERR_INVALID_PTR;
+  return EFFT_OK;
+}
+
+static int enqueue(efft_plan_s* p, void* data, cudaStream_t st) {
+  if (fault_injected("launch")) return EFFT_ERR_LAUNCH;
+  if (p->log2n == 0) return EFFT_OK;  // N = 1: the DFT is the identity
+  const bool c128 = (p->dtype == EFFT_C128);
+  if (c128) {
+    if (cudaMemsetAsync(p->state, 0, 4, st) != cudaSuccess) return EFFT_ERR_LAUNCH;
+    uint64_t blocks = (p->n + 1023) / 1024;
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    int rec = prof_begin(p, 0, st);
+    efft_range_scan<<<(unsigned)blocks, 256, 0, st>>>(reinterpret_cast<const uint4*>(data), p->n, p->state);
+    prof_end(p, rec, st);
+    if (cudaGetLastError() != cudaSuccess) return EFFT_ERR_LAUNCH;
+  }
+  if (p->small) {
+    PassArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.log2N = p->log2n;
+    a.w2048 = p->w2048;
+    a.state = p->state;
+    a.conj_in = a.conj_out = (p->sign > 0) ? 1u : 0u;
+    a.out_shift = (p->flags & EFFT_FLAG_NORMALIZE) ? p->log2n : 0;
+    int rec = prof_begin(p, 6, st);
+    if (c128) efft_small<PolicyDF><<<1, 32, 0, st>>>(data, a);
+    else efft_small<PolicyF32><<<1, 32, 0, st>>>(data, a);
+    prof_end(p, rec, st);
+    return cudaGetLastError() == cudaSuccess ? EFFT_OK : EFFT_ERR_LAUNCH;
+  }
+  for (int j = 0; j < p->npasses; ++j) {
+    int rec = prof_begin(p, 1 + j, st);
+    cudaError_t err = c128 ? launch_pass<PolicyDF, 1 << kLog2CtaC128>(p, p->pass[j], data, st)
+                           : launch_pass<PolicyF32, 1 << kLog2CtaC64>(p, p->pass[j], data, st);
+    prof_end(p, rec, st);
+    if (err != cudaSuccess) return EFFT_ERR_LAUNCH;
+  }
+  if (p->permute) {
+    const int la = p->perm_log2A, lb = p->perm_log2B;
+    const int lt = la < 5 ? la : 5;
+    const uint64_t nt = 1ull << (la - lt);
+    dim3 grid((unsigned)(nt * (nt + 1) / 2), 1u << lb);
+    int rec = prof_begin(p, 5, st);
+    if (c128) efft_digit_swap<uint4><<<grid, 256, 0, st>>>(reinterpret_cast<uint4*>(data), la, lb, lt);
+    else efft_digit_swap<uint2><<<grid, 256, 0, st>>>(reinterpret_cast<uint2*>(data), la, lb, lt);
+    prof_end(p, rec, st);
+    if (cudaGetLastError() != cudaSuccess) return EFFT_ERR_LAUNCH;
+  }
+  return EFFT_OK;
+}
+
+int efft_execute(efft_plan_t plan, void* data, void* stream) {
+  if (!plan_is_live(plan)) return EFFT_ERR_INVALID_PLAN;
+  DeviceGuard g(plan->device);
+  if (!g.ok) return EFFT_ERR_CUDA;
+  int rc = check_buffer(plan, data);
+  if (rc != EFFT_OK) return rc;
+  return enqueue(plan, data, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int efft_execute_host(efft_plan_t plan, void* host_data, void* dev_data, void* stream) {
+  if (!plan_is_live(plan)) return EFFT_ERR_INVALID_PLAN;
+  if (!host_data) return EFFT_ERR_INVALID_PTR;
+  DeviceGuard g(plan->device);
+  if (!g.ok) return EFFT_ERR_CUDA;
+  int rc = check_buffer(plan, dev_data);
+  if (rc != EFFT_OK) return rc;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const size_t bytes = plan->n * ((plan->dtype == EFFT_C128) ? 16 : 8);
+  if (cudaMemcpyAsync(dev_data, host_data, bytes, cudaMemcpyHostToDevice, st) != cudaSuccess) {
+    cudaGetLastError();
+    return EFFT_ERR_CUDA;
+  }
+  rc = enqueue(plan, dev_data, st);
+  if (rc != EFFT_OK) return rc;
+  if (cudaMemcpyAsync(host_data, dev_data, bytes, cudaMemcpyDeviceToHost, st) != cudaSuccess) {
+    cudaGetLastError();
+    return EFFT_ERR_CUDA;
+  }
+  if (cudaStreamSynchronize(st) != cudaSuccess) {
+    cudaGetLastError();
+    return EFFT_ERR_CUDA;
+  }
+  return EFFT_OK;
+}
+
+int efft_plan_profile(efft_plan_t plan, int enable) {
+  if (!plan_is_live(plan)) return EFFT_ERR_INVALID_PLAN;
+  DeviceGuard g(plan->device);
+  if (enable) {
+    for (auto& r : *plan->recs) cudaEventSynchronize(r.b);
+    release_events(plan);
+  }
+  plan->profiling = enable != 0;
+  return EFFT_OK;
+}
+
+int efft_plan_profile_read(efft_plan_t plan, double* ms, int* count, int cap, int* nslots) {
+  if (!plan_is_live(plan)) return EFFT_ERR_INVALID_PLAN;
+  DeviceGuard g(plan->device);
+  double tot[EFFT_PROFILE_SLOTS] = {0};
+  int cnt[EFFT_PROFILE_SLOTS] = {0};
+  int rc = EFFT_OK;
+  for (auto& r : *plan->recs) {
+    float t = 0.f;
+    if (cudaEventSynchronize(r.b) != cudaSuccess || cudaEventElapsedTime(&t, r.a, r.b) != cudaSuccess) {
+      cudaGetLastError();
+      rc = EFFT_ERR_CUDA;
+      continue;
+    }
+    if (r.slot >= 0 && r.slot < EFFT_PROFILE_SLOTS) {
+      tot[r.slot] += t;
+      cnt[r.slot] += 1;
+    }
+  }
+  release_events(plan);
+  for (int s = 0; s < cap && s < EFFT_PROFILE_SLOTS; ++s) {
+    if (ms) ms[s] = tot[s];
+    if (count) count[s] = cnt[s];
+  }
+  if (nslots) *nslots = EFFT_PROFILE_SLOTS;
+  return rc;
+}
+
+}  // extern "C"

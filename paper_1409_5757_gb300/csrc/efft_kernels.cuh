@@ -1,0 +1,439 @@
+// efft_kernels.cuh -- device kernels of the in-place multi-pass DFT.
+//
+//   efft_pass       one in-place pass: a batch of strided size-R sub-DFTs in
+//                   shared memory (Sec. 3.3 "processing"), radix-16 DIF
+//                   stages, twiddles of Eq. 4 fused into the epilogue
+//                   (Sec. 3.4 "reassembly"); results written back to the
+//                   slots that were read (the in-place principle of Sec. 3.4).
+//   efft_small      N <= 8: one thread evaluates Eq. 1 directly.
+//   efft_range_scan max binary64 exponent of the input (complex128 only):
+//                   fixes the power-of-two scale of the double-float data.
+//   efft_digit_swap in-place tiled transpose that turns the digit-reversed
+//                   pass output into natural order (the scatter of Sec. 3.2,
+//                   Listings 5-6, done as pairwise tile swaps).
+//   efft_twiddles   FP64 twiddle tables exp(-2*pi*i*t*stride/N) split into
+//                   FP32 (hi, lo) pairs (plan time only).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "efft_arith.cuh"
+
+namespace efft {
+
+// Pass kinds for complex128 (double-float intermediate kept in the buffer):
+//   FIRST  binary64 in  -> df out      MID  df in -> df out
+//   LAST   df in        -> binary64    SINGLE binary64 in -> binary64 out
+enum PassKind { FIRST = 0, MID = 1, LAST = 2, SINGLE = 3 };
+
+struct PassArgs {
+  int log2R;        // radix of this pass, 4 <= log2R <= 11
+  int log2C;        // columns per CTA: C = CTA_ELEMS / R
+  int log2s;        // element stride inside a column (s = 1 for the last pass)
+  int log2L;        // block length L = R * s
+  int log2N;        // transform length
+  int twB;          // low-table bits of the two-level twiddle table
+  const float4* w2048;   // exp(-2*pi*i*t/2048), t < 2048
+  const float4* tw_lo;   // exp(-2*pi*i*t/N), t < 2^twB
+  const float4* tw_hi;   // exp(-2*pi*i*(t << twB)/N), t < N >> twB
+  const uint32_t* state; // state[0] = max biased binary64 exponent of the input
+  uint32_t conj_in;      // 1: conjugate the input (sign = +1 transforms)
+  uint32_t conj_out;     // 1: conjugate the output
+  int out_shift;         // output multiplied by 2^-out_shift (1/N normalisation)
+};
+
+// Shared-memory slot of (position p, column c): one pad slot per 16 keeps the
+// stride-16 accesses of the last stage free of bank conflicts.
+__device__ __forceinline__ int smem_slot(int p, int c, int log2C) {
+  int raw = (p << log2C) + c;
+  return raw + (raw >> 4);
+}
+
+// ----------------------------------------------------------------------------
+// binary64 <-> double-float conversion by integer bit manipulation.
+// The array's values are scaled by 2^-(emax-1023), emax = the largest biased
+// exponent in the input, so that the largest input has magnitude in [1, 2).
+// D = emax - 127 is the exponent offset between a float and a binary64
+// exponent field.
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ df f64bits_to_df(uint32_t lo, uint32_t hi, int D, uint32_t flip) {
+  uint32_t sign = (hi ^ flip) & 0x80000000u;
+  int E = (int)((hi >> 20) & 0x7FFu);
+  int fe = E - D;  // biased float exponent of the scaled value
+  // high float: implicit 1 + top 23 of the 52 mantissa bits (truncated)
+  uint32_t mant = __funnelshift_l(lo, hi, 3) & 0x7FFFFFu;
+  uint32_t hbits = sign | ((uint32_t)fe << 23) | mant;
+  // low float: the remaining 29 mantissa bits rounded to 24, times
+  // 2^(fe - 127 - 52) (an exact power-of-two scaling)
+  float l = __fmul_rn(__uint2float_rn(lo & 0x1FFFFFFFu), __uint_as_float((uint32_t)(fe - 52) << 23));
+  bool ok = (E != 0) && (fe >= 1);
+  bool okl = ok && (fe >= 53);
+  df out;
+  out.h = ok ? __uint_as_float(hbits) : 0.0f;
+  out.l = okl ? __uint_as_float(__float_as_uint(l) ^ sign) : 0.0f;
+  return out;
+}
+
+// Normalised df (s, e) -> binary64 bits (truncating the sum to 53 bits).
+__device__ __forceinline__ void df_to_f64bits(df v, int D, uint32_t flip, uint32_t& olo, uint32_t& ohi) {
+  v = df_norm(v);
+  uint32_t S = __float_as_uint(v.h);
+  uint32_t sign = (S ^ flip) & 0x80000000u;
+  int Es = (int)((S >> 23) & 0xFFu);
+  uint32_t ms = S & 0x7FFFFFu;
+  int Ed = Es + D;
+  // magnitude as a 64-bit integer (Ed << 52 | m52) in units of ulp64(s)
+  uint32_t mh = ((uint32_t)Ed << 20) | (ms >> 3);
+  uint32_t ml = ms << 29;
+  // add the low float, expressed in ulp64(s) units
+  uint32_t Eb = __float_as_uint(v.l);
+  int Ee = (int)((Eb >> 23) & 0xFFu);
+  uint32_t Me = (Ee != 0) ? ((Eb & 0x7FFFFFu) | 0x800000u) : 0u;
+  bool opposite = ((Eb ^ S) & 0x80000000u) != 0u;
+  int sh = Ee - Es + 29 + ((opposite && ms == 0u) ? 1 : 0);
+  uint32_t emag = (sh >= 0) ? (Me << (sh > 31 ? 31 : sh)) : (sh > -32 ? (Me >> (-sh)) : 0u);
+  // 64-bit add / subtract of emag
+  uint64_t mag = ((uint64_t)mh << 32) | ml;
+  mag = opposite ? (mag - emag) : (mag + emag);
+  uint32_t rh = (uint32_t)(mag >> 32), rl = (uint32_t)mag;
+  bool zero = (Es == 0) || (Ed <= 0);
+  bool inf = (Ed >= 2047) || ((rh >> 20) >= 2047u);
+  if (zero) { rh = 0u; rl = 0u; }
+  if (inf && !zero) { rh = 0x7FF00000u; rl = 0u; }
+  ohi = sign | rh;
+  olo = rl;
+}
+
+// ----------------------------------------------------------------------------
+// Element loads / stores per policy and pass kind.
+// ----------------------------------------------------------------------------
+template <class P, int KIND>
+struct Mem;
+
+template <int KIND>
+struct Mem<PolicyDF, KIND> {
+  typedef uint4 Raw;
+  static __device__ __forceinline__ cdf load(const void* base, uint64_t idx, int D, uint32_t conj) {
+    if (KIND == FIRST || KIND == SINGLE) {
+      uint4 v = reinterpret_cast<const uint4*>(base)[idx];  // buffer is written in place: no .nc loads
+      cdf r;
+      r.re = f64bits_to_df(v.x, v.y, D, 0u);
+      r.im = f64bits_to_df(v.z, v.w, D, conj ? 0x80000000u : 0u);
+      return r;
+    } else {
+      float4 v = reinterpret_cast<const float4*>(base)[idx];
+      return cdf{{v.x, v.y}, {v.z, v.w}};
+    }
+  }
+  static __device__ __forceinline__ void store(void* base, uint64_t idx, cdf x, int D, uint32_t conj,
+                                               bool nonfinite) {
+    if (KIND == LAST || KIND == SINGLE) {
+      uint4 o;
+      df_to_f64bits(x.re, D, 0u, o.x, o.y);
+      df_to_f64bits(x.im, D, conj ? 0x80000000u : 0u, o.z, o.w);
+      if (nonfinite) o = make_uint4(0u, 0x7FF80000u, 0u, 0x7FF80000u);
+      reinterpret_cast<uint4*>(base)[idx] = o;
+    } else {
+      df re = df_norm(x.re), im = df_norm(x.im);
+      reinterpret_cast<float4*>(base)[idx] = make_float4(re.h, re.l, im.h, im.l);
+    }
+  }
+};
+
+template <int KIND>
+struct Mem<PolicyF32, KIND> {
+  static __device__ __forceinline__ float2 load(const void* base, uint64_t idx, int, uint32_t conj) {
+    float2 v = reinterpret_cast<const float2*>(base)[idx];
+    if ((KIND == FIRST || KIND == SINGLE) && conj) v.y = -v.y;
+    return v;
+  }
+  // D carries the output exponent shift for this policy: x * 2^-D
+  static __device__ __forceinline__ void store(void* base, uint64_t idx, float2 x, int D, uint32_t conj, bool) {
+    if (KIND == LAST || KIND == SINGLE) {
+      if (conj) x.y = -x.y;
+      if (D) {
+        const float sc = __uint_as_float((uint32_t)(127 - D) << 23);
+        x.x = __fmul_rn(x.x, sc);
+        x.y = __fmul_rn(x.y, sc);
+      }
+    }
+    reinterpret_cast<float2*>(base)[idx] = x;
+  }
+};
+
+__device__ __forceinline__ float4 ld_tw(const float4* t, uint32_t i) { return __ldg(t + i); }
+
+// exp(-2*pi*i*idx/N) from the two-level table.
+__device__ __forceinline__ float4 twiddle_N(const PassArgs& a, uint64_t idx) {
+  uint32_t lo = (uint32_t)(idx & ((1ull << a.twB) - 1ull));
+  uint32_t hi = (uint32_t)(idx >> a.twB);
+  return tw_mul(ld_tw(a.tw_hi, hi), ld_tw(a.tw_lo, lo));
+}
+
+// Output digit k of position p inside a column (digit reversal over the
+// pass's internal stages: nfull radix-16 stages, then radix 2^rem).
+__device__ __forceinline__ int col_digit_reverse(int p, int log2R, int nfull, int rem) {
+  int k = 0, shift = log2R;
+#pragma unroll 1
+  for (int st = 0; st < nfull; ++st) {
+    shift -= 4;
+    k |= ((p >> shift) & 15) << (4 * st);
+  }
+  if (rem) k |= (p & ((1 << rem) - 1)) << (4 * nfull);
+  return k;
+}
+
+// Position (within the thread's 16 contiguous slots) of the output held in
+// register u after the last stage: radix 16 (rem = 0) or 2^rem groups, each
+// group's outputs in bit-reversed register order.
+__device__ __forceinline__ int last_pos(int u, int rem) {
+  if (rem == 0) return bitrev_n(u, 4);
+  const int msk = (1 << rem) - 1;
+  return (u & ~msk) | bitrev_n(u & msk, rem);
+}
+
+// ----------------------------------------------------------------------------
+// The pass kernel.  C columns of R elements per CTA (C*R <= CTA_ELEMS), 16
+// elements per thread, C*R/16 threads.  Thread tid = t*C + c handles column c.
+// ----------------------------------------------------------------------------
+template <class P, int KIND, int CTA_ELEMS>
+__global__ void __launch_bounds__(CTA_ELEMS / 16, 2)
+efft_pass(void* __restrict__ data, const PassArgs a) {
+  typedef typename P::V V;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  V* sm = reinterpret_cast<V*>(smem_raw);
+
+  const int log2R = a.log2R, log2C = a.log2C;
+  const int R = 1 << log2R, C = 1 << log2C;
+  const int tid = threadIdx.x;
+  const int c = tid & (C - 1);
+  const int t = tid >> log2C;  // 0 .. R/16 - 1
+  const int nfull = log2R >> 2, rem = log2R & 3;
+  const int nst = nfull + (rem ? 1 : 0);
+
+  // column -> (block, m) -> element index of row 0
+  const uint64_t jcol = (uint64_t)blockIdx.x * C + c;
+  const uint64_t s = 1ull << a.log2s;
+  const uint64_t m = jcol & (s - 1);
+  const uint64_t colbase = ((jcol >> a.log2s) << a.log2L) + m;
+
+  int D = 0, Dout = a.out_shift;
+  bool nonfinite = false;
+  if (P::kElemBytes == 16) {
+    uint32_t emax = __ldg(a.state);
+    D = (int)emax - 127;
+    Dout = D - a.out_shift;
+    nonfinite = (emax >= 0x7FFu);
+  }
+
+  V v[16];
+
+  // ---- stage 0: straight from global memory ----
+  {
+    const int q = R >> 4;  // stride in rows
+#pragma unroll
+    for (int j = 0; j < 16; ++j)
+      v[j] = Mem<P, KIND>::load(data, colbase + ((uint64_t)(t + q * j) << a.log2s), D, a.conj_in);
+  }
+
+  // stages: radix-16 stages st = 0 .. nfull-1 (sub-block length l = R >> 4st),
+  // then an optional radix-2^rem stage.  Stage st > 0 reads positions from
+  // shared memory.
+#pragma unroll 1
+  for (int st = 0; st < nst; ++st) {
+    const bool last = (st == nst - 1);
+    const bool small = last && rem;  // radix 2^rem stage on contiguous groups
+    const int log2l = log2R - 4 * st;
+
+    if (st > 0) {
+      if (!small && !last) {
+        const int log2g = log2l - 4;  // groups per sub-block = l/16
+        const int b = t >> log2g, i = t & ((1 << log2g) - 1);
+        const int p0 = (b << log2l) + i;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) v[j] = sm[smem_slot(p0 + (j << log2g), c, log2C)];
+      } else {
+        // last stage: the thread's 16 contiguous positions 16t .. 16t+15
+#pragma unroll
+        for (int j = 0; j < 16; ++j) v[j] = sm[smem_slot((t << 4) + j, c, log2C)];
+      }
+    }
+
+    if (!small) {
+      dif_regs<P, 4>(v);
+    } else if (rem == 1) {
+#pragma unroll
+      for (int u = 0; u < 8; ++u) dif_regs<P, 1>(v + 2 * u);
+    } else if (rem == 2) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) dif_regs<P, 2>(v + 4 * u);
+    } else {
+#pragma unroll
+      for (int u = 0; u < 2; ++u) dif_regs<P, 3>(v + 8 * u);
+    }
+
+    if (!last) {
+      // internal twiddle exp(-2*pi*i * i*q / l), position i + (l/16) q in its
+      // sub-block; register u holds q = bitrev4(u).
+      const int log2g = log2l - 4;
+      const int b = (st == 0) ? 0 : (t >> log2g);
+      const int i = (st == 0) ? t : (t & ((1 << log2g) - 1));
+      const int p0 = (b << log2l) + i;
+      const int tshift = 11 - log2l;
+#pragma unroll
+      for (int u = 1; u < 16; ++u) {
+        const int q = bitrev_n(u, 4);
+        v[u] = P::mul_tw(v[u], ld_tw(a.w2048, (uint32_t)((i * q) << tshift)));
+      }
+      // in-place DIF: a thread writes exactly the 16 slots it read, so no
+      // barrier is needed before the write, only before the next stage.
+#pragma unroll
+      for (int u = 0; u < 16; ++u) sm[smem_slot(p0 + (bitrev_n(u, 4) << log2g), c, log2C)] = v[u];
+      __syncthreads();
+    }
+  }
+
+  // ---- epilogue: digit-reversed positions -> output index k, pass twiddle,
+  // store.  Register u holds position 16t + pos(u) of its column.
+  if (a.log2s > 0) {
+    // pass twiddle exp(-2*pi*i * m*k / L) = table index (m*k) << (log2N - log2L)
+    const int sh = a.log2N - a.log2L;
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+      const int k = col_digit_reverse((t << 4) + last_pos(u, rem), log2R, nfull, rem);
+      const uint64_t idx = ((uint64_t)m * (uint64_t)k) << sh;
+      if (idx != 0) v[u] = P::mul_tw(v[u], twiddle_N(a, idx));
+      Mem<P, KIND>::store(data, colbase + ((uint64_t)k << a.log2s), v[u], Dout, a.conj_out, nonfinite);
+    }
+  } else {
+    // contiguous output: stage through shared memory in natural order
+    if (nst > 1) __syncthreads();  // last-stage reads are complete
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+      const int k = col_digit_reverse((t << 4) + last_pos(u, rem), log2R, nfull, rem);
+      sm[smem_slot(k, c, log2C)] = v[u];
+    }
+    __syncthreads();
+    const int tile_elems = R << log2C;  // C contiguous transforms
+    const uint64_t tile0 = (uint64_t)blockIdx.x * tile_elems;
+#pragma unroll 4
+    for (int e = tid; e < tile_elems; e += (int)blockDim.x) {
+      const int cc = e >> log2R, k = e & (R - 1);
+      Mem<P, KIND>::store(data, tile0 + (uint64_t)e, sm[smem_slot(k, cc, log2C)], Dout, a.conj_out, nonfinite);
+    }
+  }
+}
+
+// ----------------------------------------------------------------------------
+// N <= 8: one thread, Eq. 1 evaluated directly with table twiddles.
+// ----------------------------------------------------------------------------
+template <class P>
+__global__ void efft_small(void* __restrict__ data, const PassArgs a) {
+  typedef typename P::V V;
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const int N = 1 << a.log2N;
+  int D = 0, Dout = a.out_shift;
+  bool nonfinite = false;
+  if (P::kElemBytes == 16) {
+    uint32_t emax = __ldg(a.state);
+    D = (int)emax - 127;
+    Dout = D - a.out_shift;
+    nonfinite = (emax >= 0x7FFu);
+  }
+  V x[8], y[8];
+  for (int n = 0; n < N; ++n) x[n] = Mem<P, SINGLE>::load(data, n, D, a.conj_in);
+  for (int k = 0; k < N; ++k) {
+    V acc = x[0];
+    for (int n = 1; n < N; ++n) {
+      int t = ((n * k) & (N - 1)) << (11 - a.log2N);
+      acc = P::add(acc, P::mul_tw(x[n], ld_tw(a.w2048, t)));
+    }
+    y[k] = acc;
+  }
+  for (int k = 0; k < N; ++k) Mem<P, SINGLE>::store(data, k, y[k], Dout, a.conj_out, nonfinite);
+}
+
+// ----------------------------------------------------------------------------
+// Range scan: largest biased binary64 exponent among all re/im parts.
+// ----------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) efft_range_scan(const uint4* __restrict__ x, uint64_t n,
+                                                        uint32_t* __restrict__ state) {
+  uint32_t mx = 0;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (; i + 3 * stride < n; i += 4 * stride) {
+    uint4 v0 = __ldg(x + i), v1 = __ldg(x + i + stride), v2 = __ldg(x + i + 2 * stride),
+          v3 = __ldg(x + i + 3 * stride);
+    mx = max(mx, max(max(v0.y & 0x7FF00000u, v0.w & 0x7FF00000u), max(v1.y & 0x7FF00000u, v1.w & 0x7FF00000u)));
+    mx = max(mx, max(max(v2.y & 0x7FF00000u, v2.w & 0x7FF00000u), max(v3.y & 0x7FF00000u, v3.w & 0x7FF00000u)));
+  }
+  for (; i < n; i += stride) {
+    uint4 v = __ldg(x + i);
+    mx = max(mx, max(v.y & 0x7FF00000u, v.w & 0x7FF00000u));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, o));
+  __shared__ uint32_t wmax[8];
+  if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t r = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r = max(r, wmax[w]);
+    atomicMax(state, r >> 20);
+  }
+}
+
+// ----------------------------------------------------------------------------
+// In-place digit reversal for radices (a, b, a): position (i0, i1, i2) with
+// i0, i2 < A, i1 < B swaps with (i2, i1, i0).  For fixed i1 this is the
+// transpose of an A x A matrix with row stride B*A; CTA z handles the tile
+// pair (I, J), (J, I) with I <= J (triangular decode of blockIdx.x).
+// T x T tiles, T = min(32, A); 256 threads.
+// ----------------------------------------------------------------------------
+template <typename E>
+__global__ void __launch_bounds__(256) efft_digit_swap(E* __restrict__ data, int log2A, int log2B, int log2T) {
+  __shared__ E t0[32][33];
+  __shared__ E t1[32][33];
+  const int T = 1 << log2T;
+  const uint64_t A = 1ull << log2A;
+  const uint64_t rowstride = A << log2B;  // stride of i0
+  const uint64_t i1 = blockIdx.y;
+  // triangular decode: z -> (I, J), I <= J
+  const uint32_t z = blockIdx.x;
+  uint32_t J = (uint32_t)((sqrtf(8.0f * (float)z + 1.0f) - 1.0f) * 0.5f);
+  while ((J + 1) * (J + 2) / 2 <= z) ++J;
+  while (J * (J + 1) / 2 > z) --J;
+  const uint32_t I = z - J * (J + 1) / 2;
+  const uint64_t base = i1 << log2A;
+  // tile (I, J): rows i0 = I*T + r, cols i2 = J*T + col
+  for (int e = threadIdx.x; e < T * T; e += blockDim.x) {
+    int r = e >> log2T, col = e & (T - 1);
+    t0[r][col] = data[base + ((uint64_t)I * T + r) * rowstride + (uint64_t)J * T + col];
+    if (I != J) t1[r][col] = data[base + ((uint64_t)J * T + r) * rowstride + (uint64_t)I * T + col];
+  }
+  __syncthreads();
+  // position (J*T + r, i1, I*T + col) receives old (I*T + col, i1, J*T + r) = t0[col][r]
+  for (int e = threadIdx.x; e < T * T; e += blockDim.x) {
+    int r = e >> log2T, col = e & (T - 1);
+    data[base + ((uint64_t)J * T + r) * rowstride + (uint64_t)I * T + col] = t0[col][r];
+    if (I != J) data[base + ((uint64_t)I * T + r) * rowstride + (uint64_t)J * T + col] = t1[col][r];
+  }
+}
+
+// ----------------------------------------------------------------------------
+// Twiddle tables: out[t] = exp(-2*pi*i * t*stride / N) for t < count, FP64
+// sincospi (exact argument: N is a power of two) split into FP32 (hi, lo).
+// ----------------------------------------------------------------------------
+__global__ void efft_twiddles(float4* __restrict__ out, uint64_t count, uint64_t stride, int log2N) {
+  uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= count) return;
+  uint64_t mN = (t * stride) & ((1ull << log2N) - 1ull);
+  double x = -2.0 * ldexp((double)mN, -log2N);  // exact
+  double sv, cv;
+  sincospi(x, &sv, &cv);
+  float ch = __double2float_rn(cv), sh = __double2float_rn(sv);
+  float cl = __double2float_rn(cv - (double)ch), sl = __double2float_rn(sv - (double)sh);
+  out[t] = make_float4(ch, cl, sh, sl);
+}
+
+}  // namespace efft

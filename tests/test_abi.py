@@ -1,0 +1,127 @@
+"""Host-side checks of the C ABI (no GPU needed).
+
+The libraries are compiled here (nvcc cross-compiles sm_103a without a GPU);
+these tests check that every entry point declared in include/*.h is exported
+and that argument validation happens before any CUDA call.
+"""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="session")
+def libs():
+    from paper_1409_5757_gb300 import build
+    return build.build()
+
+
+def _declared(header):
+    txt = open(os.path.join(ROOT, "include", header)).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?[a-z_0-9]+\s*\*?\s*(efft_[a-z_0-9]+)\s*\(", txt, flags=re.M)))
+
+
+@pytest.mark.parametrize("header,lib", [("efft.h", "libefft.so"), ("efft_inputs.h", "libefft_inputs.so")])
+def test_every_declared_symbol_is_exported(libs, header, lib):
+    names = _declared(header)
+    assert len(names) >= 4
+    so = ctypes.CDLL(libs[lib])
+    for n in names:
+        assert hasattr(so, n), f"{lib} does not export {n}"
+
+
+def test_binding_covers_header(libs):
+    import paper_1409_5757_gb300 as efft
+    assert set(_declared("efft.h")) == set(efft._SIGNATURES)
+
+
+def test_argument_errors_before_cuda(libs):
+    import paper_1409_5757_gb300 as efft
+    L = efft._lib()
+    h = ctypes.c_void_p()
+    assert L.efft_plan_create(None, 8, 1, -1, 0) == 4                    # NULL out
+    assert L.efft_plan_create(ctypes.byref(h), 0, 1, -1, 0) == 1         # N = 0
+    assert L.efft_plan_create(ctypes.byref(h), 12, 1, -1, 0) == 1        # not a power of two
+    assert L.efft_plan_create(ctypes.byref(h), 1 << 34, 1, -1, 0) == 1   # too large
+    assert L.efft_plan_create(ctypes.byref(h), 1 << 10, 2, -1, 0) == 2   # dtype
+    assert L.efft_plan_create(ctypes.byref(h), 1 << 10, 1, 0, 0) == 3    # sign
+    assert L.efft_plan_create(ctypes.byref(h), 1 << 10, 1, 1, 0x80) == 12  # flags
+    assert h.value is None
+
+
+def test_plan_handle_checks(libs):
+    import paper_1409_5757_gb300 as efft
+    L = efft._lib()
+    assert L.efft_plan_destroy(None) == 0
+    bogus = ctypes.create_string_buffer(256)
+    assert L.efft_plan_destroy(ctypes.cast(bogus, ctypes.c_void_p)) == 10
+    assert L.efft_execute(None, None, None) == 10
+    assert L.efft_execute(ctypes.cast(bogus, ctypes.c_void_p), None, None) == 10
+    assert L.efft_execute_host(None, None, None, None) == 10
+    assert L.efft_plan_radices(None, None, 0, None) == 10
+    assert L.efft_plan_info(None, None, None) == 10
+
+
+def test_strerror_and_version(libs):
+    import paper_1409_5757_gb300 as efft
+    L = efft._lib()
+    for code in list(efft.STATUS) + [99, -1]:
+        s = L.efft_strerror(code)
+        assert isinstance(s, bytes) and len(s) > 3
+    assert L.efft_version() == 1
+
+
+def test_no_cuda_device_reports_cuda_error(libs):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    import paper_1409_5757_gb300 as efft
+    h = ctypes.c_void_p()
+    assert efft._lib().efft_plan_create(ctypes.byref(h), 1 << 10, 1, -1, 0) == 11
+    with pytest.raises(efft.EfftError):
+        efft.Plan(1 << 10)
+
+
+def test_missing_library_fails_loudly(tmp_path, monkeypatch):
+    import paper_1409_5757_gb300 as efft
+    monkeypatch.setattr(efft, "_LIB", None)
+    monkeypatch.setattr(efft, "lib_path", lambda: str(tmp_path / "libefft.so"))
+    with pytest.raises(RuntimeError, match="no CPU fallback"):
+        efft._lib()
+
+
+def test_radix_schedule_is_symmetric():
+    """The planner's radices (mirrored here from the documented rule) are
+    symmetric so the digit reversal is an involution; all radices 16..2048."""
+    def choose(e):
+        if e <= 3:
+            return []
+        if e <= 11:
+            return [e]
+        if e <= 22 and e % 2 == 0:
+            return [e // 2, e // 2]
+        a = min(11, (e - 4) // 2)
+        return [a, e - 2 * a, a]
+    for e in range(4, 34):
+        r = choose(e)
+        assert sum(r) == e and r == r[::-1] and all(4 <= x <= 11 for x in r), (e, r)
+
+
+def test_arith_constants_match_mpmath():
+    """The float-pair constants cos(pi/8), sin(pi/8), cos(pi/4) in the kernels
+    are hi = RN32(v), lo = RN32(v - hi)."""
+    import mpmath
+    import numpy as np
+    src = open(os.path.join(ROOT, "paper_1409_5757_gb300", "csrc", "efft_arith.cuh")).read()
+    mpmath.mp.dps = 50
+    want = {"K_C1": mpmath.cos(mpmath.pi / 8), "K_S1": mpmath.sin(mpmath.pi / 8), "K_R": mpmath.cos(mpmath.pi / 4)}
+    for name, v in want.items():
+        m = re.search(name + r"\(\) \{ return \{([-0-9.e+]+)f, ([-0-9.e+]+)f\}", src)
+        assert m, name
+        hi, lo = np.float32(float(m.group(1))), np.float32(float(m.group(2)))
+        assert hi == np.float32(float(v))
+        assert lo == np.float32(float(v - mpmath.mpf(float(hi))))

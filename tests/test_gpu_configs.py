@@ -1,0 +1,181 @@
+"""The benchmark configurations at full size, in the launch configuration
+bench.py times, checked on sampled outputs that the oracle computes one by
+one (direct sums of Eq. 1) plus properties that hold at any size (Parseval,
+round trip), and the normalisation / profiling entry points.
+
+Sampled estimator of the relative L2 error (Eq. 9):
+    sqrt(mean_{k in S} |F_k - Fe_k|^2) / sqrt(mean_k |Fe_k|^2),
+with mean_k |Fe_k|^2 = sum_n |x_n|^2 by Parseval (reduced on the device in FP64).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    yield
+    torch.cuda.empty_cache()
+
+
+def _free():
+    import gc
+    gc.collect()
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+
+
+def _ks(N, count, seed):
+    g = np.random.default_rng(seed)
+    ks = set([0, 1, N // 2, N - 1])
+    while len(ks) < count:
+        ks.add(int(g.integers(0, N)))
+    return np.array(sorted(ks), np.int64)
+
+
+def test_config_c2_2p30_forward_inverse_with_tones(orc):
+    """N = 2^30 complex128 (16 GiB), forward then inverse, uniform + 64 tones."""
+    import paper_1409_5757_gb300 as efft
+    from paper_1409_5757_gb300 import inputs
+    N, seed, e = 1 << 30, 2, 30
+    x = torch.empty(N, dtype=torch.complex128, device="cuda")
+    inputs.fill_uniform(x, seed)
+    f, a = inputs.tone_params(seed, N, 64)
+    inputs.add_tones(x, f, a)
+    keep = x.clone()
+    sumsq = inputs.diff_norms(x)[0]
+    efft.fft_(x, -1)
+    torch.cuda.synchronize()
+    # Parseval
+    ssX = inputs.diff_norms(x)[0]
+    assert abs(ssX / (N * sumsq) - 1) <= 1e-14 * e
+    # sampled bins, stratified: 16 random non-tone bins stand for the N - 64
+    # ordinary bins, 12 of the 64 tone bins for the tone bins.  The tones' part
+    # of the reference is the closed form N*a_j at k = f_j (a_j dyadic, so N*a_j
+    # is exact); the uniform part is the oracle's direct sum.
+    tone = dict(zip(f.tolist(), a.tolist()))
+    kr = np.array([k for k in _ks(N, 20, 5) if int(k) not in tone][:16], np.int64)
+    kt = f[:12].astype(np.int64)
+    ks = np.concatenate([kr, kt])
+    got = x[torch.from_numpy(ks).cuda()].cpu().numpy()
+    ref = orc.dft_bins_uniform(seed, N, ks, -1)
+    ref = ref + np.array([N * tone.get(int(k), 0) for k in ks])
+    d2 = np.abs(got - ref) ** 2
+    est = (N - 64) * np.mean(d2[:len(kr)]) + 64 * np.mean(d2[len(kr):])
+    err = math.sqrt(est / (N * sumsq))
+    assert err <= 1e-14 * e, err
+    # and every sampled bin on its own, relative to its own magnitude scale
+    assert np.max(np.sqrt(d2[:len(kr)])) <= 1e-14 * e * 50 * math.sqrt(sumsq)
+    assert np.max(np.sqrt(d2[len(kr):]) / np.abs(ref[len(kr):])) <= 1e-14 * e
+    # normalised inverse returns the input
+    efft.fft_(x, +1, efft.EFFT_FLAG_NORMALIZE)
+    num, den = inputs.diff_norms(x, keep)
+    assert math.sqrt(num / den) <= 2e-14 * e
+    del x, keep
+    _free()
+
+
+def test_config_c3_2p33_complex128(orc):
+    """N = 2^33 complex128 (128 GiB in HBM, no out-of-place buffer)."""
+    import paper_1409_5757_gb300 as efft
+    from paper_1409_5757_gb300 import inputs
+    N, seed, e = 1 << 33, 3, 33
+    free, total = torch.cuda.mem_get_info()
+    if free < N * 16 + (4 << 30):
+        pytest.skip(f"needs {N * 16 >> 30} GiB free, have {free >> 30} GiB")
+    x = torch.empty(N, dtype=torch.complex128, device="cuda")
+    inputs.fill_uniform(x, seed)
+    sumsq = inputs.diff_norms(x)[0]
+    efft.fft_(x, -1)
+    torch.cuda.synchronize()
+    ssX = inputs.diff_norms(x)[0]
+    assert abs(ssX / (N * sumsq) - 1) <= 1e-14 * e
+    ks = _ks(N, 6, 7)
+    got = x[torch.from_numpy(ks).cuda()].cpu().numpy()
+    ref = orc.dft_bins_uniform(seed, N, ks, -1)
+    err = math.sqrt(np.mean(np.abs(got - ref) ** 2)) / math.sqrt(sumsq)
+    assert err <= 1e-14 * e, err
+    # normalised inverse, compared chunk by chunk with the regenerated input
+    efft.fft_(x, +1, efft.EFFT_FLAG_NORMALIZE)
+    chunk = 1 << 28
+    y = torch.empty(chunk, dtype=torch.complex128, device="cuda")
+    num = den = 0.0
+    for c in range(N // chunk):
+        inputs.fill_uniform(y, seed, n0=c * chunk)
+        a_, b_ = inputs.diff_norms(x[c * chunk:(c + 1) * chunk], y)
+        num += a_
+        den += b_
+    assert math.sqrt(num / den) <= 2e-14 * e
+    del x, y
+    _free()
+
+
+def test_config_c4_2p31_complex64_gaussian(orc):
+    """N = 2^31 complex64, Gaussian input; error vs the FP64 oracle on the
+    FP32-rounded input promoted to FP64."""
+    import paper_1409_5757_gb300 as efft
+    from paper_1409_5757_gb300 import inputs
+    N, seed, e = 1 << 31, 4, 31
+    x = torch.empty(N, dtype=torch.complex64, device="cuda")
+    inputs.fill_gaussian(x, seed)
+    xin = x.cpu().numpy()
+    sumsq = float(np.sum(np.abs(xin.astype(np.complex128)) ** 2))
+    efft.fft_(x, -1)
+    torch.cuda.synchronize()
+    ks = _ks(N, 8, 9)
+    got = x[torch.from_numpy(ks).cuda()].cpu().numpy().astype(np.complex128)
+    ref = orc.dft_bins(xin.astype(np.complex128), ks, -1)
+    del xin
+    err = math.sqrt(np.mean(np.abs(got - ref) ** 2)) / math.sqrt(sumsq)
+    assert err <= 2e-6 * e, err
+    ssX = inputs.diff_norms(x)[0]
+    assert abs(ssX / (N * sumsq) - 1) <= 2e-6 * e
+    del x
+    _free()
+
+
+@pytest.mark.parametrize("name", ["c128", "c64"])
+@pytest.mark.parametrize("e", [2, 9, 14, 17, 24])
+def test_normalize_flag(orc, name, e):
+    import paper_1409_5757_gb300 as efft
+    N = 1 << e
+    x = orc.gen_uniform(31, N)
+    if name == "c64":
+        x = x.astype(np.complex64).astype(np.complex128)
+    tdt = torch.complex128 if name == "c128" else torch.complex64
+    t = torch.from_numpy(x.astype(np.complex128 if name == "c128" else np.complex64)).cuda()
+    efft.fft_(t, -1, efft.EFFT_FLAG_NORMALIZE)
+    got = t.cpu().numpy().astype(np.complex128)
+    tol = (1e-14 if name == "c128" else 2e-6) * max(e, 1)
+    assert oracle.rel_l2(got, orc.dft(x, -1) / N) <= tol
+    efft.fft_(t, +1)
+    assert oracle.rel_l2(t.cpu().numpy().astype(np.complex128), x) <= 2 * tol
+    assert t.dtype == tdt
+
+
+def test_profile_records_every_launch():
+    import paper_1409_5757_gb300 as efft
+    N = 1 << 20
+    p = efft.Plan(N, efft.EFFT_C128, -1)
+    t = torch.zeros(N, dtype=torch.complex128, device="cuda")
+    p.profile(True)
+    for _ in range(3):
+        p.execute(t.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    rec = p.profile_read()
+    p.profile(False)
+    r = p.radices()
+    assert rec["range_scan"][1] == 3
+    for j in range(len(r)):
+        assert rec[f"pass{j}"][1] == 3 and rec[f"pass{j}"][0] > 0
+    assert rec["digit_swap"][1] == 3
+    assert p.profile_read() == {}

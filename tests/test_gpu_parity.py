@@ -1,0 +1,222 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Tolerances (relative L2 error of Eq. 9, Sec. 5.3, with complex moduli):
+  complex128 (double-float butterflies): 1e-14 * log2 N
+  complex64  (FP32 butterflies)        : 2e-6  * log2 N, against the FP64
+             oracle applied to the FP32-rounded input promoted to FP64.
+Inputs are the seeded uniform[-1,1) re/im stream regenerated by the oracle's
+own SplitMix64 (bit-identical to the device generator, checked below).
+"""
+import numpy as np
+import pytest
+
+import oracle
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = {"c128": 1e-14, "c64": 2e-6}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def _tdtype(name):
+    return torch.complex128 if name == "c128" else torch.complex64
+
+
+def gpu_fft(x_host, name, sign=-1, flags=0):
+    import paper_1409_5757_gb300 as efft
+    t = torch.from_numpy(np.ascontiguousarray(x_host.astype(np.complex128 if name == "c128" else np.complex64)))
+    t = t.cuda()
+    efft.fft_(t, sign=sign, flags=flags)
+    torch.cuda.synchronize()
+    return t.cpu().numpy().astype(np.complex128)
+
+
+def host_input(o, name, N, seed):
+    x = o.gen_uniform(seed, N)
+    if name == "c64":
+        x = x.astype(np.complex64).astype(np.complex128)  # the values the GPU sees
+    return x
+
+
+def check(got, ref, name, N, what=""):
+    err = oracle.rel_l2(got, ref)
+    lim = TOL[name] * max(np.log2(N), 1)
+    assert err <= lim, f"{what} {name} N={N}: rel-L2 {err:.3e} > {lim:.3e}"
+    # element-wise: no single output far off (relative to the RMS output)
+    rms = np.sqrt(np.mean(np.abs(ref) ** 2))
+    if rms > 0:
+        assert np.max(np.abs(got - ref)) <= 50 * lim * rms, f"{what} {name} N={N}: outlier"
+    return err
+
+
+@pytest.mark.parametrize("name", ["c128", "c64"])
+@pytest.mark.parametrize("sign", [-1, 1])
+@pytest.mark.parametrize("e", list(range(0, 23)))
+def test_parity_every_size(orc, name, sign, e):
+    N = 1 << e
+    x = host_input(orc, name, N, seed=1000 + e)
+    got = gpu_fft(x, name, sign)
+    check(got, orc.dft(x, sign), name, N)
+
+
+def test_device_generator_matches_oracle_generator(orc):
+    from paper_1409_5757_gb300 import inputs
+    for N, seed, n0 in ((1, 3, 0), (1000, 1, 0), (4096, 77, 123456789)):
+        t = torch.empty(N, dtype=torch.complex128, device="cuda")
+        inputs.fill_uniform(t, seed, n0)
+        assert np.array_equal(t.cpu().numpy(), orc.gen_uniform(seed, N, n0=n0))
+        t = torch.empty(N, dtype=torch.complex64, device="cuda")
+        inputs.fill_uniform(t, seed, n0)
+        assert np.array_equal(t.cpu().numpy(), orc.gen_uniform(seed, N, n0=n0).astype(np.complex64))
+
+
+@pytest.mark.parametrize("name", ["c128", "c64"])
+@pytest.mark.parametrize("e", [12, 13, 16, 19, 20, 21, 22, 23])
+def test_digit_reversed_output(orc, name, e):
+    import paper_1409_5757_gb300 as efft
+    N = 1 << e
+    radices = efft.Plan(N, efft.EFFT_C128 if name == "c128" else efft.EFFT_C64, -1,
+                        efft.EFFT_FLAG_DIGIT_REVERSED_OUT).radices()
+    x = host_input(orc, name, N, seed=7)
+    got = gpu_fft(x, name, -1, efft.EFFT_FLAG_DIGIT_REVERSED_OUT)
+    X = orc.dft(x, -1)
+    # position P = sum_j q_j s_j holds X[q_0 + R_0 q_1 + R_0 R_1 q_2 + ...]
+    R = [1 << r for r in radices]
+    P = np.arange(N)
+    k = np.zeros(N, np.int64)
+    s = N
+    mult = 1
+    for j, Rj in enumerate(R):
+        s //= Rj
+        q = (P // s) % Rj
+        k += q * mult
+        mult *= Rj
+    check(got, X[k], name, N, "digit-reversed")
+
+
+@pytest.mark.parametrize("name", ["c128", "c64"])
+@pytest.mark.parametrize("e", [5, 11, 16, 21])
+def test_round_trip(orc, name, e):
+    import paper_1409_5757_gb300 as efft
+    N = 1 << e
+    x = host_input(orc, name, N, seed=9)
+    t = torch.from_numpy(x.astype(np.complex128 if name == "c128" else np.complex64)).cuda()
+    efft.fft_(t, -1)
+    efft.fft_(t, 1)
+    got = t.cpu().numpy().astype(np.complex128) / N
+    err = oracle.rel_l2(got, x)
+    assert err <= 2 * TOL[name] * e
+
+
+@pytest.mark.parametrize("name", ["c128", "c64"])
+def test_special_inputs(orc, name):
+    N = 1 << 14
+    k = np.arange(N)
+    cases = {
+        "zeros": np.zeros(N, np.complex128),
+        "impulse0": (k == 0).astype(np.complex128),
+        "impulse_m": (k == 1234).astype(np.complex128),
+        "constant": np.full(N, 0.375 - 0.625j),
+        "tone": np.exp(2j * np.pi * ((777 * k) % N) / N),
+    }
+    for label, x in cases.items():
+        if name == "c64":
+            x = x.astype(np.complex64).astype(np.complex128)
+        got = gpu_fft(x, name, -1)
+        ref = orc.fft_radix2(x, -1)
+        if label == "zeros":
+            assert np.all(got == 0)
+        else:
+            check(got, ref, name, N, label)
+
+
+@pytest.mark.parametrize("scale", [1e300, 1e-300, 2.0 ** -1000, 1e150])
+def test_c128_extreme_magnitudes(orc, scale):
+    """The double-float path carries a power-of-two scale: magnitudes far
+    outside the binary32 range keep full accuracy."""
+    N = 1 << 16
+    x = orc.gen_uniform(21, N) * scale
+    got = gpu_fft(x, "c128", -1)
+    check(got, orc.fft_radix2(x, -1), "c128", N, f"scale {scale}")
+
+
+@pytest.mark.parametrize("name", ["c128", "c64"])
+@pytest.mark.parametrize("e", [3, 10, 16, 21])
+def test_nan_input_gives_nan(orc, name, e):
+    N = 1 << e
+    x = orc.gen_uniform(5, N)
+    x[N // 3] = complex(np.nan, 0.0)
+    got = gpu_fft(x, name, -1)
+    assert np.all(np.isnan(got.real) | np.isnan(got.imag))
+
+
+def test_c128_inf_input_gives_nan(orc):
+    N = 1 << 16
+    x = orc.gen_uniform(5, N)
+    x[17] = complex(np.inf, 1.0)
+    got = gpu_fft(x, "c128", -1)
+    assert np.all(np.isnan(got.real))
+
+
+@pytest.mark.parametrize("name", ["c128", "c64"])
+@pytest.mark.parametrize("e", [24, 26])
+def test_parity_large_full_oracle(orc, name, e):
+    N = 1 << e
+    x = host_input(orc, name, N, seed=2000 + e)
+    got = gpu_fft(x, name, -1)
+    check(got, orc.fft_radix2(x, -1), name, N)
+
+
+def test_execute_host_entry_point(orc):
+    import paper_1409_5757_gb300 as efft
+    N = 1 << 18
+    x = orc.gen_uniform(4, N)
+    host = torch.from_numpy(x.copy()).pin_memory()
+    dev = torch.empty(N, dtype=torch.complex128, device="cuda")
+    p = efft.Plan(N, efft.EFFT_C128, -1)
+    p.execute_host(host.data_ptr(), dev.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    check(host.numpy(), orc.fft_radix2(x, -1), "c128", N, "execute_host")
+
+
+def test_execute_rejects_bad_buffers():
+    import paper_1409_5757_gb300 as efft
+    p = efft.Plan(1 << 10, efft.EFFT_C128, -1)
+    with pytest.raises(efft.EfftError) as ei:
+        p.execute(0)
+    assert ei.value.status == 4
+    t = torch.zeros(2048 + 1, dtype=torch.complex64, device="cuda")
+    with pytest.raises(efft.EfftError) as ei:
+        p.execute(t.data_ptr() + 8)  # 8-byte aligned only, complex128 needs 16
+    assert ei.value.status == 5
+    h = torch.zeros(1024, dtype=torch.complex128)
+    with pytest.raises(efft.EfftError) as ei:
+        p.execute(h.data_ptr())  # host memory
+    assert ei.value.status == 4
+    p.destroy()
+    with pytest.raises(efft.EfftError) as ei:
+        efft._check(efft._lib().efft_execute(p.handle, None, None), "x")
+
+
+def test_fault_injection_is_host_side(monkeypatch):
+    import paper_1409_5757_gb300 as efft
+    monkeypatch.setenv("EFFT_FAULT_INJECT", "alloc")
+    with pytest.raises(efft.EfftError) as ei:
+        efft.Plan(1 << 12)
+    assert ei.value.status == 6
+    monkeypatch.setenv("EFFT_FAULT_INJECT", "launch")
+    p = efft.Plan(1 << 12)
+    t = torch.zeros(1 << 12, dtype=torch.complex128, device="cuda")
+    with pytest.raises(efft.EfftError) as ei:
+        p.execute(t.data_ptr())
+    assert ei.value.status == 7
+    monkeypatch.delenv("EFFT_FAULT_INJECT")
+    p.execute(t.data_ptr())
+    torch.cuda.synchronize()
