@@ -165,6 +165,36 @@ int efft_plan_info(efft_plan_t plan, double* hbm_passes, uint64_t* table_bytes);
 int efft_plan_profile(efft_plan_t plan, int enable);
 int efft_plan_profile_read(efft_plan_t plan, double* ms, int* count, int cap, int* nslots);
 
+/*
+ * One transform that allocates nothing (the paper has no counterpart; this
+ * is for callers that cannot call cudaMalloc: a framework whose pooled
+ * allocator owns all device memory, or a pipeline that cannot afford
+ * cudaMalloc's implicit device-wide synchronisation).
+ *
+ * Computes what a plan created with (n, dtype, sign, flags) and efft_execute
+ * compute, with the same kernels, on the `data` buffer (the caller's device
+ * memory, as for efft_execute) on `stream`.  Instead of plan-owned memory it
+ * uses one file-scope device array of the library holding the twiddle
+ * tables (2048 + 2 * 4096 complex entries) and a 16-byte state word,
+ * 160 KiB plus 256 bytes, that every GPU which loads the library keeps until
+ * the process exits.  No cudaMalloc, cudaFree or allocating library call is
+ * made.
+ *  n      a power of two, 1 <= n <= 2^EFFT_NOALLOC_MAX_LOG2N; larger n is
+ *         rejected with EFFT_ERR_INVALID_SIZE (use a plan instead).
+ * Set-up: the first call on a device (with that device current) looks up
+ * the array's device address and enqueues the table generation; make that
+ * first call before any stream capture.  The tables are regenerated, on the
+ * call's stream, whenever n differs from the previous call on the device.
+ * Every call shares the array, which keeps the last call's contents; the
+ * state word is cleared by each call before use.  Calls whose work overlaps
+ * on the GPU (different streams without ordering) race on the array and give
+ * undefined results: order them.
+ * Errors: as efft_plan_create (argument checks) and efft_execute (buffer
+ * checks, LAUNCH).
+ */
+#define EFFT_NOALLOC_MAX_LOG2N 24
+int efft_execute_noalloc(void* data, uint64_t n, int dtype, int sign, uint32_t flags, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

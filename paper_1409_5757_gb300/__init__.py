@@ -50,6 +50,7 @@ _SIGNATURES = {
     "efft_plan_profile": (ctypes.c_int, [_vp, ctypes.c_int]),
     "efft_plan_profile_read": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int),
                                               ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+    "efft_execute_noalloc": (ctypes.c_int, [_vp, ctypes.c_uint64, ctypes.c_int, ctypes.c_int, ctypes.c_uint32, _vp]),
 }
 
 

@@ -23,7 +23,8 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-lineinfo", "-std=c++17", "-shared", "-Xcompiler", "-fPIC", "-I", INC]
 
 LIBS = {
-    "libefft.so": (["efft.cu"], ["efft.cu", "efft_kernels.cuh", "efft_arith.cuh"], ["efft.h"]),
+    "libefft.so": (["efft.cu", "efft_noalloc.cu"],
+                   ["efft.cu", "efft_noalloc.cu", "efft_kernels.cuh", "efft_arith.cuh"], ["efft.h"]),
     "libefft_inputs.so": (["inputs.cu"], ["inputs.cu"], ["efft_inputs.h"]),
 }
 

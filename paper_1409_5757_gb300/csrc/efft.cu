@@ -522,3 +522,72 @@ int efft_plan_profile_read(efft_plan_t plan, double* ms, int* count, int cap, in
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Internal helper for efft_execute_noalloc (efft_noalloc.cu): the same launch
+// sequence as efft_execute, for a plan description built on the stack whose
+// twiddle tables and state word live in caller-provided device memory.
+// Allocates nothing; enqueues the table generation first when `regen`.
+// ---------------------------------------------------------------------------
+int efft_internal_run_in_scratch(void* scratch, size_t scratch_bytes, bool regen, void* data, uint64_t n,
+                                 int dtype, int sign, uint32_t flags, cudaStream_t st) {
+  if (init_kernels() != EFFT_OK) return EFFT_ERR_CUDA;
+  efft_plan_s p;
+  std::memset(&p, 0, sizeof(p));
+  if (cudaGetDevice(&p.device) != cudaSuccess) {
+    cudaGetLastError();
+    return EFFT_ERR_CUDA;
+  }
+  p.n = n;
+  p.log2n = ilog2_u64(n);
+  p.dtype = dtype;
+  p.sign = sign;
+  p.flags = flags;
+  const int e = p.log2n;
+  int r[kMaxPasses] = {0, 0, 0, 0};
+  p.npasses = choose_radices(e, r);
+  p.small = (e >= 1 && e <= 3);
+  const int log2cta = (dtype == EFFT_C128) ? kLog2CtaC128 : kLog2CtaC64;
+  const size_t eb = (dtype == EFFT_C128) ? 16 : 8;
+  int rest = e;
+  for (int j = 0; j < p.npasses; ++j) {
+    Pass& ps = p.pass[j];
+    ps.log2R = r[j];
+    rest -= r[j];
+    ps.log2s = rest;
+    ps.log2L = r[j] + rest;
+    int log2C = log2cta - r[j];
+    if (log2C > e - r[j]) log2C = e - r[j];
+    ps.log2C = log2C;
+    ps.grid = 1ull << (e - r[j] - log2C);
+    ps.threads = 1 << (r[j] + log2C - 4);
+    const size_t elems = 1ull << (r[j] + log2C);
+    ps.smem = (elems + elems / 16 + 1) * eb;
+    if (p.npasses == 1) ps.kind = SINGLE;
+    else if (j == 0) ps.kind = FIRST;
+    else if (j == p.npasses - 1) ps.kind = LAST;
+    else ps.kind = MID;
+  }
+  p.permute = (p.npasses >= 2) && !(flags & EFFT_FLAG_DIGIT_REVERSED_OUT);
+  if (p.npasses >= 2) {
+    p.perm_log2A = r[0];
+    p.perm_log2B = (p.npasses == 3) ? r[1] : 0;
+  }
+  p.twB = (e + 1) / 2;
+  const uint64_t nlo = 1ull << p.twB, nhi = 1ull << (e - p.twB);
+  const size_t state_off = (2048 + nlo + nhi) * sizeof(float4);
+  if (state_off + 16 > scratch_bytes) return EFFT_ERR_INVALID_SIZE;
+  float4* base = reinterpret_cast<float4*>(scratch);
+  p.w2048 = base;
+  p.tw_lo = base + 2048;
+  p.tw_hi = base + 2048 + nlo;
+  p.state = reinterpret_cast<uint32_t*>(reinterpret_cast<unsigned char*>(scratch) + state_off);
+  int rc = check_buffer(&p, data);
+  if (rc != EFFT_OK) return rc;
+  if (regen) {
+    if ((rc = gen_table(p.w2048, 2048, 1, 11, st)) != EFFT_OK) return rc;
+    if ((rc = gen_table(p.tw_lo, nlo, 1, e, st)) != EFFT_OK) return rc;
+    if ((rc = gen_table(p.tw_hi, nhi, nlo, e, st)) != EFFT_OK) return rc;
+  }
+  return enqueue(&p, data, st);
+}
