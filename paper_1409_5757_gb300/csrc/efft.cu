@@ -103,6 +103,27 @@ void set_smem_attr() {
                        (int)((CTA + CTA / 16 + 1) * P::kElemBytes));
 }
 
+// specialised kernels: radices 2^8 .. 2^11 at full CTA width
+template <class P, int KIND, int LOG2CTA>
+void set_smem_attr_fx() {
+  const int bytes = (int)(((1 << LOG2CTA) + (1 << LOG2CTA) / 16 + 1) * P::kElemBytes);
+  cudaFuncSetAttribute(efft_pass_fx<P, KIND, 8, LOG2CTA - 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  cudaFuncSetAttribute(efft_pass_fx<P, KIND, 9, LOG2CTA - 9>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  cudaFuncSetAttribute(efft_pass_fx<P, KIND, 10, LOG2CTA - 10>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  cudaFuncSetAttribute(efft_pass_fx<P, KIND, 11, LOG2CTA - 11>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
+template <class P, int KIND, int LOG2CTA>
+bool launch_fx(int log2R, dim3 grid, dim3 block, size_t smem, cudaStream_t st, void* data, const PassArgs& a) {
+  switch (log2R) {
+    case 8: efft_pass_fx<P, KIND, 8, LOG2CTA - 8><<<grid, block, smem, st>>>(data, a); return true;
+    case 9: efft_pass_fx<P, KIND, 9, LOG2CTA - 9><<<grid, block, smem, st>>>(data, a); return true;
+    case 10: efft_pass_fx<P, KIND, 10, LOG2CTA - 10><<<grid, block, smem, st>>>(data, a); return true;
+    case 11: efft_pass_fx<P, KIND, 11, LOG2CTA - 11><<<grid, block, smem, st>>>(data, a); return true;
+    default: return false;
+  }
+}
+
 int init_kernels() {
   static std::once_flag once;
   static cudaError_t err = cudaSuccess;
@@ -115,6 +136,12 @@ int init_kernels() {
     set_smem_attr<PolicyF32, MID, 1 << kLog2CtaC64>();
     set_smem_attr<PolicyF32, LAST, 1 << kLog2CtaC64>();
     set_smem_attr<PolicyF32, SINGLE, 1 << kLog2CtaC64>();
+    set_smem_attr_fx<PolicyDF, FIRST, kLog2CtaC128>();
+    set_smem_attr_fx<PolicyDF, MID, kLog2CtaC128>();
+    set_smem_attr_fx<PolicyDF, LAST, kLog2CtaC128>();
+    set_smem_attr_fx<PolicyF32, FIRST, kLog2CtaC64>();
+    set_smem_attr_fx<PolicyF32, MID, kLog2CtaC64>();
+    set_smem_attr_fx<PolicyF32, LAST, kLog2CtaC64>();
     err = cudaGetLastError();
   });
   return err == cudaSuccess ? EFFT_OK : EFFT_ERR_CUDA;
@@ -212,6 +239,16 @@ cudaError_t launch_pass(const efft_plan_s* p, const Pass& ps, void* data, cudaSt
   a.conj_out = (ps.kind == LAST || ps.kind == SINGLE) ? conj : 0u;
   a.out_shift = ((p->flags & EFFT_FLAG_NORMALIZE) && (ps.kind == LAST || ps.kind == SINGLE)) ? p->log2n : 0;
   dim3 grid((unsigned)ps.grid), block(ps.threads);
+  constexpr int LOG2CTA = (P::kElemBytes == 16) ? kLog2CtaC128 : kLog2CtaC64;
+  if (ps.kind != SINGLE && ps.log2R >= 8 && ps.log2R <= 11 && ps.log2R + ps.log2C == LOG2CTA) {
+    bool ok = false;
+    switch (ps.kind) {
+      case FIRST: ok = launch_fx<P, FIRST, LOG2CTA>(ps.log2R, grid, block, ps.smem, st, data, a); break;
+      case MID: ok = launch_fx<P, MID, LOG2CTA>(ps.log2R, grid, block, ps.smem, st, data, a); break;
+      default: ok = launch_fx<P, LAST, LOG2CTA>(ps.log2R, grid, block, ps.smem, st, data, a); break;
+    }
+    if (ok) return cudaGetLastError();
+  }
   switch (ps.kind) {
     case FIRST: efft_pass<P, FIRST, CTA><<<grid, block, ps.smem, st>>>(data, a); break;
     case MID: efft_pass<P, MID, CTA><<<grid, block, ps.smem, st>>>(data, a); break;

@@ -26,7 +26,7 @@ namespace efft {
 // double-float scalars
 // ---------------------------------------------------------------------------
 struct df { float h, l; };
-struct cdf { df re, im; };
+struct __align__(16) cdf { df re, im; };  // 16-byte aligned: one 128-bit access
 
 __device__ __forceinline__ df df_add(df a, df b) {
   // TwoSum(a.h, b.h) (Knuth), low parts added without renormalisation.

@@ -325,6 +325,167 @@ efft_pass(void* __restrict__ data, const PassArgs a) {
 }
 
 // ----------------------------------------------------------------------------
+// Compile-time specialised pass kernel for the radices that carry the large
+// sizes (R = 2^LR, LR = 8..11; C = 2^LC columns per CTA, C*R = CTA size).
+// Same algorithm as efft_pass; with R and C known at compile time every
+// shared-memory address is a per-thread base plus an immediate, and the pass
+// twiddle exp(-2*pi*i*m*k/L) is factored as W_t * V_c[u]: k = kt | kc(u)
+// (digit reversal is a bit permutation, so the thread's part kt and the
+// register's part kc(u) occupy disjoint bits), W_t = exp(-2*pi*i*m*kt/L) is
+// formed once per thread and V_c[u] = exp(-2*pi*i*m_c*kc(u)/L) once per column
+// into shared memory, instead of two L2 table lookups per element.
+// ----------------------------------------------------------------------------
+__host__ __device__ constexpr int bitrev_c(int v, int bits) {
+  int r = 0;
+  for (int b = 0; b < bits; ++b) r |= ((v >> b) & 1) << (bits - 1 - b);
+  return r;
+}
+// output index k of column position p (see col_digit_reverse)
+__host__ __device__ constexpr int digit_rev_c(int p, int LR) {
+  int nfull = LR / 4, rem = LR % 4, k = 0, shift = LR;
+  for (int st = 0; st < nfull; ++st) {
+    shift -= 4;
+    k |= ((p >> shift) & 15) << (4 * st);
+  }
+  if (rem) k |= (p & ((1 << rem) - 1)) << (4 * nfull);
+  return k;
+}
+__host__ __device__ constexpr int last_pos_c(int u, int rem) {
+  return rem == 0 ? bitrev_c(u, 4) : ((u & ~((1 << rem) - 1)) | bitrev_c(u & ((1 << rem) - 1), rem));
+}
+// padded slot offset of a raw offset that is a multiple of C (C a power of two)
+__host__ __device__ constexpr int pad_off(int raw) { return raw + (raw >> 4); }
+
+template <class P, int LOG>
+__device__ __forceinline__ void dif_groups(typename P::V* v) {
+  // 16 registers as 16 / 2^LOG independent radix-2^LOG DIF groups
+#pragma unroll
+  for (int g = 0; g < 16; g += (1 << LOG)) dif_regs<P, LOG>(v + g);
+}
+
+template <class P, int KIND, int LR, int LC>
+__global__ void __launch_bounds__(1 << (LR + LC - 4), 2)
+efft_pass_fx(void* __restrict__ data, const PassArgs a) {
+  typedef typename P::V V;
+  constexpr int R = 1 << LR, C = 1 << LC, TPC = R >> 4;
+  constexpr int NFULL = LR / 4, REM = LR % 4, NST = NFULL + (REM ? 1 : 0);
+  constexpr int NMID = NST - 2;  // radix-16 stages between the first and the last
+  constexpr bool STRIDED = (KIND == FIRST || KIND == MID);
+  static_assert(LR >= 5 && LR <= 12, "radix range");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  V* sm = reinterpret_cast<V*>(smem_raw);
+  __shared__ float4 vtw[STRIDED ? 16 * C : 1];
+
+  const int tid = threadIdx.x;
+  const int c = tid & (C - 1);
+  const int t = tid >> LC;
+  const uint64_t jcol = (uint64_t)blockIdx.x * C + c;
+  uint64_t m = 0, colbase, step;
+  if (STRIDED) {
+    step = 1ull << a.log2s;
+    m = jcol & (step - 1);
+    colbase = ((jcol >> a.log2s) << a.log2L) + m;
+  } else {
+    step = 1;
+    colbase = jcol << LR;
+  }
+
+  int D = 0, Dout = a.out_shift;
+  bool nonfinite = false;
+  if (P::kElemBytes == 16) {
+    uint32_t emax = __ldg(a.state);
+    D = (int)emax - 127;
+    Dout = D - a.out_shift;
+    nonfinite = (emax >= 0x7FFu);
+  }
+
+  const int kt = digit_rev_c(t << 4, LR);
+  float4 wt = make_float4(1.f, 0.f, 0.f, 0.f);
+  if (STRIDED) {
+    const int sh = a.log2N - a.log2L;
+    if (tid < 16 * C) {
+      const int cc = tid >> 4, u = tid & 15;
+      const uint64_t mc = ((uint64_t)blockIdx.x * C + cc) & (step - 1);
+      const int kc = digit_rev_c(last_pos_c(u, REM), LR);
+      vtw[tid] = twiddle_N(a, (mc * (uint64_t)kc) << sh);
+    }
+    wt = twiddle_N(a, (m * (uint64_t)kt) << sh);
+  }
+
+  V v[16];
+  // ---- stage 0: rows t + TPC*j straight from global memory ----
+  {
+    const uint64_t b0 = colbase + (uint64_t)t * step, sj = (uint64_t)TPC * step;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) v[j] = Mem<P, KIND>::load(data, b0 + (uint64_t)j * sj, D, a.conj_in);
+  }
+  dif_regs<P, 4>(v);
+  {
+    // exp(-2*pi*i * t*q / R), q = bitrev4(u), to positions t + TPC*q
+#pragma unroll
+    for (int u = 1; u < 16; ++u)
+      v[u] = P::mul_tw(v[u], ld_tw(a.w2048, (uint32_t)(t * bitrev_c(u, 4)) << (11 - LR)));
+    const int sb = smem_slot(t, c, LC);
+#pragma unroll
+    for (int u = 0; u < 16; ++u) sm[sb + pad_off(bitrev_c(u, 4) * TPC * C)] = v[u];
+  }
+  __syncthreads();
+
+  // ---- middle radix-16 stages ----
+#pragma unroll
+  for (int st = 1; st <= NMID; ++st) {
+    const int log2l = LR - 4 * st;      // sub-block length
+    const int log2g = log2l - 4;        // groups per sub-block
+    const int b = t >> log2g, i = t & ((1 << log2g) - 1);
+    const int sb = smem_slot((b << log2l) + i, c, LC);
+    const int gstep = (1 << log2g) * C;  // raw step between group members
+#pragma unroll
+    for (int j = 0; j < 16; ++j) v[j] = sm[sb + pad_off(j * gstep)];
+    dif_regs<P, 4>(v);
+#pragma unroll
+    for (int u = 1; u < 16; ++u)
+      v[u] = P::mul_tw(v[u], ld_tw(a.w2048, (uint32_t)(i * bitrev_c(u, 4)) << (11 - log2l)));
+    // in place: the thread writes exactly the slots it read
+#pragma unroll
+    for (int u = 0; u < 16; ++u) sm[sb + pad_off(bitrev_c(u, 4) * gstep)] = v[u];
+    __syncthreads();
+  }
+
+  // ---- last stage: the thread's 16 contiguous positions 16t .. 16t+15 ----
+  {
+    const int sb = smem_slot(t << 4, c, LC);
+#pragma unroll
+    for (int j = 0; j < 16; ++j) v[j] = sm[sb + pad_off(j * C)];
+    if (REM == 0) dif_regs<P, 4>(v);
+    else dif_groups<P, (REM == 0 ? 4 : REM)>(v);
+  }
+
+  if (STRIDED) {
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+      const int k = kt | digit_rev_c(last_pos_c(u, REM), LR);
+      const float4 tw = tw_mul(wt, vtw[c * 16 + u]);
+      v[u] = P::mul_tw(v[u], tw);
+      Mem<P, KIND>::store(data, colbase + ((uint64_t)k << a.log2s), v[u], Dout, a.conj_out, nonfinite);
+    }
+  } else {
+    __syncthreads();  // last-stage reads are complete before the slots are reused
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+      const int k = kt | digit_rev_c(last_pos_c(u, REM), LR);
+      sm[smem_slot(k, c, LC)] = v[u];
+    }
+    __syncthreads();
+    const uint64_t tile0 = (uint64_t)blockIdx.x * (R * C);
+#pragma unroll 4
+    for (int e = tid; e < R * C; e += (R * C) / 16) {
+      const int cc = e >> LR, k = e & (R - 1);
+      Mem<P, KIND>::store(data, tile0 + (uint64_t)e, sm[smem_slot(k, cc, LC)], Dout, a.conj_out, nonfinite);
+    }
+  }
+}
+
+// ----------------------------------------------------------------------------
 // N <= 8: one thread, Eq. 1 evaluated directly with table twiddles.
 // ----------------------------------------------------------------------------
 template <class P>
