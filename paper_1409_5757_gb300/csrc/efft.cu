@@ -136,9 +136,9 @@ int init_kernels() {
     set_smem_attr<PolicyF32, MID, 1 << kLog2CtaC64>();
     set_smem_attr<PolicyF32, LAST, 1 << kLog2CtaC64>();
     set_smem_attr<PolicyF32, SINGLE, 1 << kLog2CtaC64>();
-    set_smem_attr_fx<PolicyDF, FIRST, kLog2CtaC128>();
-    set_smem_attr_fx<PolicyDF, MID, kLog2CtaC128>();
-    set_smem_attr_fx<PolicyDF, LAST, kLog2CtaC128>();
+    set_smem_attr_fx<PolicyDF2, FIRST, kLog2CtaC128>();
+    set_smem_attr_fx<PolicyDF2, MID, kLog2CtaC128>();
+    set_smem_attr_fx<PolicyDF2, LAST, kLog2CtaC128>();
     set_smem_attr_fx<PolicyF32, FIRST, kLog2CtaC64>();
     set_smem_attr_fx<PolicyF32, MID, kLog2CtaC64>();
     set_smem_attr_fx<PolicyF32, LAST, kLog2CtaC64>();
@@ -221,7 +221,8 @@ void prof_end(efft_plan_s* p, int rec, cudaStream_t st) {
   if (rec >= 0) cudaEventRecord((*p->recs)[rec].b, st);
 }
 
-template <class P, int CTA>
+// P: policy of the generic kernel; PFX: policy of the specialised kernels
+template <class P, class PFX, int CTA>
 cudaError_t launch_pass(const efft_plan_s* p, const Pass& ps, void* data, cudaStream_t st) {
   PassArgs a;
   a.log2R = ps.log2R;
@@ -243,9 +244,9 @@ cudaError_t launch_pass(const efft_plan_s* p, const Pass& ps, void* data, cudaSt
   if (ps.kind != SINGLE && ps.log2R >= 8 && ps.log2R <= 11 && ps.log2R + ps.log2C == LOG2CTA) {
     bool ok = false;
     switch (ps.kind) {
-      case FIRST: ok = launch_fx<P, FIRST, LOG2CTA>(ps.log2R, grid, block, ps.smem, st, data, a); break;
-      case MID: ok = launch_fx<P, MID, LOG2CTA>(ps.log2R, grid, block, ps.smem, st, data, a); break;
-      default: ok = launch_fx<P, LAST, LOG2CTA>(ps.log2R, grid, block, ps.smem, st, data, a); break;
+      case FIRST: ok = launch_fx<PFX, FIRST, LOG2CTA>(ps.log2R, grid, block, ps.smem, st, data, a); break;
+      case MID: ok = launch_fx<PFX, MID, LOG2CTA>(ps.log2R, grid, block, ps.smem, st, data, a); break;
+      default: ok = launch_fx<PFX, LAST, LOG2CTA>(ps.log2R, grid, block, ps.smem, st, data, a); break;
     }
     if (ok) return cudaGetLastError();
   }
@@ -466,8 +467,8 @@ static int enqueue(efft_plan_s* p, void* data, cudaStream_t st) {
   }
   for (int j = 0; j < p->npasses; ++j) {
     int rec = prof_begin(p, 1 + j, st);
-    cudaError_t err = c128 ? launch_pass<PolicyDF, 1 << kLog2CtaC128>(p, p->pass[j], data, st)
-                           : launch_pass<PolicyF32, 1 << kLog2CtaC64>(p, p->pass[j], data, st);
+    cudaError_t err = c128 ? launch_pass<PolicyDF, PolicyDF2, 1 << kLog2CtaC128>(p, p->pass[j], data, st)
+                           : launch_pass<PolicyF32, PolicyF32, 1 << kLog2CtaC64>(p, p->pass[j], data, st);
     prof_end(p, rec, st);
     if (err != cudaSuccess) return EFFT_ERR_LAUNCH;
   }

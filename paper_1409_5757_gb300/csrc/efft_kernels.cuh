@@ -115,14 +115,17 @@ struct Mem<PolicyDF, KIND> {
   typedef uint4 Raw;
   static __device__ __forceinline__ cdf load(const void* base, uint64_t idx, int D, uint32_t conj) {
     if (KIND == FIRST || KIND == SINGLE) {
-      uint4 v = reinterpret_cast<const uint4*>(base)[idx];  // buffer is written in place: no .nc loads
+      // data is read once per pass: cache in L2 only (ld.global.cg) so that L1
+      // keeps the twiddle tables; coherent at L2 (the buffer is written in place)
+      uint4 v = __ldcg(reinterpret_cast<const uint4*>(base) + idx);
       cdf r;
       r.re = f64bits_to_df(v.x, v.y, D, 0u);
       r.im = f64bits_to_df(v.z, v.w, D, conj ? 0x80000000u : 0u);
       return r;
     } else {
-      float4 v = reinterpret_cast<const float4*>(base)[idx];
-      return cdf{{v.x, v.y}, {v.z, v.w}};
+      // intermediate double-float layout: {re.h, im.h, re.l, im.l}
+      float4 v = __ldcg(reinterpret_cast<const float4*>(base) + idx);
+      return cdf{{v.x, v.z}, {v.y, v.w}};
     }
   }
   static __device__ __forceinline__ void store(void* base, uint64_t idx, cdf x, int D, uint32_t conj,
@@ -135,7 +138,35 @@ struct Mem<PolicyDF, KIND> {
       reinterpret_cast<uint4*>(base)[idx] = o;
     } else {
       df re = df_norm(x.re), im = df_norm(x.im);
-      reinterpret_cast<float4*>(base)[idx] = make_float4(re.h, re.l, im.h, im.l);
+      reinterpret_cast<float4*>(base)[idx] = make_float4(re.h, im.h, re.l, im.l);
+    }
+  }
+};
+
+template <int KIND>
+struct Mem<PolicyDF2, KIND> {
+  static __device__ __forceinline__ cdf2 load(const void* base, uint64_t idx, int D, uint32_t conj) {
+    if (KIND == FIRST || KIND == SINGLE) {
+      uint4 v = __ldcg(reinterpret_cast<const uint4*>(base) + idx);
+      df re = f64bits_to_df(v.x, v.y, D, 0u);
+      df im = f64bits_to_df(v.z, v.w, D, conj ? 0x80000000u : 0u);
+      return cdf2{make_float2(re.h, im.h), make_float2(re.l, im.l)};
+    } else {
+      float4 v = __ldcg(reinterpret_cast<const float4*>(base) + idx);
+      return cdf2{make_float2(v.x, v.y), make_float2(v.z, v.w)};
+    }
+  }
+  static __device__ __forceinline__ void store(void* base, uint64_t idx, cdf2 x, int D, uint32_t conj,
+                                               bool nonfinite) {
+    if (KIND == LAST || KIND == SINGLE) {
+      uint4 o;
+      df_to_f64bits(df{x.h.x, x.l.x}, D, 0u, o.x, o.y);
+      df_to_f64bits(df{x.h.y, x.l.y}, D, conj ? 0x80000000u : 0u, o.z, o.w);
+      if (nonfinite) o = make_uint4(0u, 0x7FF80000u, 0u, 0x7FF80000u);
+      reinterpret_cast<uint4*>(base)[idx] = o;
+    } else {
+      x = c2norm(x);
+      reinterpret_cast<float4*>(base)[idx] = make_float4(x.h.x, x.h.y, x.l.x, x.l.y);
     }
   }
 };
@@ -143,7 +174,7 @@ struct Mem<PolicyDF, KIND> {
 template <int KIND>
 struct Mem<PolicyF32, KIND> {
   static __device__ __forceinline__ float2 load(const void* base, uint64_t idx, int, uint32_t conj) {
-    float2 v = reinterpret_cast<const float2*>(base)[idx];
+    float2 v = __ldcg(reinterpret_cast<const float2*>(base) + idx);
     if ((KIND == FIRST || KIND == SINGLE) && conj) v.y = -v.y;
     return v;
   }
@@ -374,7 +405,7 @@ efft_pass_fx(void* __restrict__ data, const PassArgs a) {
   static_assert(LR >= 5 && LR <= 12, "radix range");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V* sm = reinterpret_cast<V*>(smem_raw);
-  __shared__ float4 vtw[STRIDED ? 16 * C : 1];
+  __shared__ typename P::TW vtw[STRIDED ? 16 * C : 1];
 
   const int tid = threadIdx.x;
   const int c = tid & (C - 1);
@@ -400,16 +431,16 @@ efft_pass_fx(void* __restrict__ data, const PassArgs a) {
   }
 
   const int kt = digit_rev_c(t << 4, LR);
-  float4 wt = make_float4(1.f, 0.f, 0.f, 0.f);
+  typename P::TW wt;
   if (STRIDED) {
     const int sh = a.log2N - a.log2L;
     if (tid < 16 * C) {
       const int cc = tid >> 4, u = tid & 15;
       const uint64_t mc = ((uint64_t)blockIdx.x * C + cc) & (step - 1);
       const int kc = digit_rev_c(last_pos_c(u, REM), LR);
-      vtw[tid] = twiddle_N(a, (mc * (uint64_t)kc) << sh);
+      vtw[tid] = P::expand(twiddle_N(a, (mc * (uint64_t)kc) << sh));
     }
-    wt = twiddle_N(a, (m * (uint64_t)kt) << sh);
+    wt = P::expand(twiddle_N(a, (m * (uint64_t)kt) << sh));
   }
 
   V v[16];
@@ -424,7 +455,7 @@ efft_pass_fx(void* __restrict__ data, const PassArgs a) {
     // exp(-2*pi*i * t*q / R), q = bitrev4(u), to positions t + TPC*q
 #pragma unroll
     for (int u = 1; u < 16; ++u)
-      v[u] = P::mul_tw(v[u], ld_tw(a.w2048, (uint32_t)(t * bitrev_c(u, 4)) << (11 - LR)));
+      v[u] = P::mul_tw(v[u], P::int_tw(a.w2048, nullptr, (uint32_t)(t * bitrev_c(u, 4)) << (11 - LR)));
     const int sb = smem_slot(t, c, LC);
 #pragma unroll
     for (int u = 0; u < 16; ++u) sm[sb + pad_off(bitrev_c(u, 4) * TPC * C)] = v[u];
@@ -444,7 +475,7 @@ efft_pass_fx(void* __restrict__ data, const PassArgs a) {
     dif_regs<P, 4>(v);
 #pragma unroll
     for (int u = 1; u < 16; ++u)
-      v[u] = P::mul_tw(v[u], ld_tw(a.w2048, (uint32_t)(i * bitrev_c(u, 4)) << (11 - log2l)));
+      v[u] = P::mul_tw(v[u], P::int_tw(a.w2048, nullptr, (uint32_t)(i * bitrev_c(u, 4)) << (11 - log2l)));
     // in place: the thread writes exactly the slots it read
 #pragma unroll
     for (int u = 0; u < 16; ++u) sm[sb + pad_off(bitrev_c(u, 4) * gstep)] = v[u];
@@ -464,8 +495,7 @@ efft_pass_fx(void* __restrict__ data, const PassArgs a) {
 #pragma unroll
     for (int u = 0; u < 16; ++u) {
       const int k = kt | digit_rev_c(last_pos_c(u, REM), LR);
-      const float4 tw = tw_mul(wt, vtw[c * 16 + u]);
-      v[u] = P::mul_tw(v[u], tw);
+      v[u] = P::pass_tw(v[u], wt, vtw[c * 16 + u]);
       Mem<P, KIND>::store(data, colbase + ((uint64_t)k << a.log2s), v[u], Dout, a.conj_out, nonfinite);
     }
   } else {
