@@ -126,6 +126,30 @@ int efft_execute(efft_plan_t plan, void* data, void* stream);
  */
 int efft_execute_host(efft_plan_t plan, void* host_data, void* dev_data, void* stream);
 
+/*
+ * Stream `count` host arrays through the device with the copies overlapped
+ * with the transforms.  Array i is copied from host_in[i] into device buffer
+ * dev_bufs[i % nbufs], the plans[0 .. nplans) are applied to it in order, in
+ * place, and the result is copied to host_out[i].  Copies in, transforms and
+ * copies out run on three streams (the transforms on `stream`), so array i+1
+ * is copied in and array i-1 copied out while array i is transformed; a
+ * buffer is reused only after the copy-out of its previous array finished.
+ * With nbufs >= 3 the copies in both directions also overlap each other.
+ * Synchronous: returns when every result is in host memory.
+ *  plans      nplans >= 1 live plans with the same n and dtype.
+ *  host_in    count host pointers (pinned memory gives the full copy rate).
+ *  host_out   count host pointers; host_out[i] may equal host_in[i] but must
+ *             not overlap any host_in[j], j != i.  Several host_in entries may
+ *             share memory, and so may several host_out entries (the copies
+ *             out are issued in order on one stream).
+ *  dev_bufs   nbufs >= 1 device buffers of n*S bytes on the plans' device.
+ * Errors: INVALID_PLAN, INVALID_PTR, MISALIGNED, INVALID_SIZE (plans of
+ * different n or dtype, count < 0, nplans or nbufs < 1), LAUNCH, CUDA.
+ */
+int efft_execute_host_stream(const efft_plan_t* plans, int nplans, void* const* host_in,
+                             void* const* host_out, int count, void* const* dev_bufs, int nbufs,
+                             void* stream);
+
 /* Destroy a plan and free its device tables.  NULL is accepted (no-op).
  * Errors: INVALID_PLAN for a handle that is not a live plan. */
 int efft_plan_destroy(efft_plan_t plan);

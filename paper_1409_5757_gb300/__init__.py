@@ -51,6 +51,9 @@ _SIGNATURES = {
     "efft_plan_profile_read": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int),
                                               ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     "efft_execute_noalloc": (ctypes.c_int, [_vp, ctypes.c_uint64, ctypes.c_int, ctypes.c_int, ctypes.c_uint32, _vp]),
+    "efft_execute_host_stream": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, ctypes.POINTER(_vp),
+                                                ctypes.POINTER(_vp), ctypes.c_int, ctypes.POINTER(_vp), ctypes.c_int,
+                                                _vp]),
 }
 
 
@@ -150,6 +153,20 @@ class Plan:
             pass
 
 
+def execute_host_stream(plans, host_in, host_out, dev_bufs, stream: int = 0) -> None:
+    """efft_execute_host_stream: host arrays (data pointers) through the plans
+    in order, copies overlapped with the transforms; synchronous."""
+    n = len(host_in)
+    if len(host_out) != n:
+        raise ValueError("host_in and host_out differ in length")
+    P = (_vp * len(plans))(*[p.handle for p in plans])
+    HI = (_vp * max(n, 1))(*[_vp(x) for x in host_in])
+    HO = (_vp * max(n, 1))(*[_vp(x) for x in host_out])
+    DB = (_vp * len(dev_bufs))(*[_vp(x) for x in dev_bufs])
+    _check(_lib().efft_execute_host_stream(P, len(plans), HI, HO, n, DB, len(dev_bufs), _vp(stream)),
+           "efft_execute_host_stream")
+
+
 _PLANS: dict = {}
 _PLANS_LOCK = threading.Lock()
 
@@ -206,5 +223,5 @@ def version() -> int:
     return _lib().efft_version()
 
 
-__all__ = ["Plan", "EfftError", "fft_", "fft", "get_plan", "clear_plans", "version", "lib_path",
+__all__ = ["Plan", "EfftError", "fft_", "fft", "get_plan", "clear_plans", "version", "lib_path", "execute_host_stream",
            "EFFT_C64", "EFFT_C128", "EFFT_FLAG_DIGIT_REVERSED_OUT", "EFFT_FLAG_NORMALIZE"]

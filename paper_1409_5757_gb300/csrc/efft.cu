@@ -521,6 +521,75 @@ int efft_execute_host(efft_plan_t plan, void* host_data, void* dev_data, void* s
   return EFFT_OK;
 }
 
+int efft_execute_host_stream(const efft_plan_t* plans, int nplans, void* const* host_in,
+                             void* const* host_out, int count, void* const* dev_bufs, int nbufs,
+                             void* stream) {
+  if (!plans || nplans < 1 || nbufs < 1 || count < 0) return EFFT_ERR_INVALID_SIZE;
+  for (int j = 0; j < nplans; ++j) {
+    if (!plan_is_live(plans[j])) return EFFT_ERR_INVALID_PLAN;
+    if (plans[j]->n != plans[0]->n || plans[j]->dtype != plans[0]->dtype ||
+        plans[j]->device != plans[0]->device)
+      return EFFT_ERR_INVALID_SIZE;
+  }
+  if (count == 0) return EFFT_OK;
+  if (!host_in || !host_out || !dev_bufs) return EFFT_ERR_INVALID_PTR;
+  for (int i = 0; i < count; ++i)
+    if (!host_in[i] || !host_out[i]) return EFFT_ERR_INVALID_PTR;
+  efft_plan_s* p0 = plans[0];
+  DeviceGuard g(p0->device);
+  if (!g.ok) return EFFT_ERR_CUDA;
+  for (int b = 0; b < nbufs; ++b) {
+    int rc = check_buffer(p0, dev_bufs[b]);
+    if (rc != EFFT_OK) return rc;
+  }
+  const size_t bytes = p0->n * ((p0->dtype == EFFT_C128) ? 16 : 8);
+  cudaStream_t sc = reinterpret_cast<cudaStream_t>(stream);
+  cudaStream_t sin = nullptr, sout = nullptr;
+  std::vector<cudaEvent_t> ev_in(nbufs, nullptr), ev_comp(nbufs, nullptr), ev_out(nbufs, nullptr);
+  std::vector<bool> used(nbufs, false);
+  int rc = EFFT_OK;
+  if (cudaStreamCreateWithFlags(&sin, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&sout, cudaStreamNonBlocking) != cudaSuccess)
+    rc = EFFT_ERR_CUDA;
+  for (int b = 0; rc == EFFT_OK && b < nbufs; ++b) {
+    if (cudaEventCreateWithFlags(&ev_in[b], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ev_comp[b], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ev_out[b], cudaEventDisableTiming) != cudaSuccess)
+      rc = EFFT_ERR_CUDA;
+  }
+  for (int i = 0; rc == EFFT_OK && i < count; ++i) {
+    const int b = i % nbufs;
+    void* buf = dev_bufs[b];
+    // copy in once the buffer's previous result has been copied out
+    if (used[b] && cudaStreamWaitEvent(sin, ev_out[b], 0) != cudaSuccess) { rc = EFFT_ERR_CUDA; break; }
+    if (cudaMemcpyAsync(buf, host_in[i], bytes, cudaMemcpyHostToDevice, sin) != cudaSuccess ||
+        cudaEventRecord(ev_in[b], sin) != cudaSuccess) { rc = EFFT_ERR_CUDA; break; }
+    // transforms in order on the caller's stream
+    if (cudaStreamWaitEvent(sc, ev_in[b], 0) != cudaSuccess) { rc = EFFT_ERR_CUDA; break; }
+    for (int j = 0; rc == EFFT_OK && j < nplans; ++j) rc = enqueue(plans[j], buf, sc);
+    if (rc != EFFT_OK) break;
+    if (cudaEventRecord(ev_comp[b], sc) != cudaSuccess) { rc = EFFT_ERR_CUDA; break; }
+    // copy out
+    if (cudaStreamWaitEvent(sout, ev_comp[b], 0) != cudaSuccess ||
+        cudaMemcpyAsync(host_out[i], buf, bytes, cudaMemcpyDeviceToHost, sout) != cudaSuccess ||
+        cudaEventRecord(ev_out[b], sout) != cudaSuccess) { rc = EFFT_ERR_CUDA; break; }
+    used[b] = true;
+  }
+  // drain everything that was enqueued, even after an error
+  if (sin) cudaStreamSynchronize(sin);
+  cudaStreamSynchronize(sc);
+  if (sout && cudaStreamSynchronize(sout) != cudaSuccess && rc == EFFT_OK) rc = EFFT_ERR_CUDA;
+  for (int b = 0; b < nbufs; ++b) {
+    if (ev_in[b]) cudaEventDestroy(ev_in[b]);
+    if (ev_comp[b]) cudaEventDestroy(ev_comp[b]);
+    if (ev_out[b]) cudaEventDestroy(ev_out[b]);
+  }
+  if (sin) cudaStreamDestroy(sin);
+  if (sout) cudaStreamDestroy(sout);
+  if (rc != EFFT_OK) cudaGetLastError();
+  return rc;
+}
+
 int efft_plan_profile(efft_plan_t plan, int enable) {
   if (!plan_is_live(plan)) return EFFT_ERR_INVALID_PLAN;
   DeviceGuard g(plan->device);

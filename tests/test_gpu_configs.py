@@ -179,3 +179,33 @@ def test_profile_records_every_launch():
         assert rec[f"pass{j}"][1] == 3 and rec[f"pass{j}"][0] > 0
     assert rec["digit_swap"][1] == 3
     assert p.profile_read() == {}
+
+
+@pytest.mark.parametrize("nbufs", [1, 2, 3])
+def test_execute_host_stream(orc, nbufs):
+    """Host arrays streamed through [forward, normalised inverse] and through
+    [forward] alone, copies overlapped with the transforms."""
+    import paper_1409_5757_gb300 as efft
+    N, e, count = 1 << 18, 18, 5
+    fwd = efft.Plan(N, efft.EFFT_C128, -1)
+    inv = efft.Plan(N, efft.EFFT_C128, +1, efft.EFFT_FLAG_NORMALIZE)
+    xs = [orc.gen_uniform(700 + i, N) for i in range(count)]
+    hin = [torch.from_numpy(x.copy()).pin_memory() for x in xs]
+    hout = [torch.empty(N, dtype=torch.complex128).pin_memory() for _ in range(count)]
+    bufs = [torch.empty(N, dtype=torch.complex128, device="cuda") for _ in range(nbufs)]
+    stream = torch.cuda.current_stream().cuda_stream
+    efft.execute_host_stream([fwd, inv], [h.data_ptr() for h in hin], [h.data_ptr() for h in hout],
+                             [b.data_ptr() for b in bufs], stream)
+    for i in range(count):
+        assert oracle.rel_l2(hout[i].numpy(), xs[i]) <= 2e-14 * e
+    # forward only, output written over the input arrays
+    efft.execute_host_stream([fwd], [h.data_ptr() for h in hin], [h.data_ptr() for h in hin],
+                             [b.data_ptr() for b in bufs], stream)
+    for i in range(count):
+        assert oracle.rel_l2(hin[i].numpy(), orc.fft_radix2(xs[i], -1)) <= 1e-14 * e
+    # argument checks
+    other = efft.Plan(N // 2, efft.EFFT_C128, -1)
+    with pytest.raises(efft.EfftError) as ei:
+        efft.execute_host_stream([fwd, other], [hin[0].data_ptr()], [hout[0].data_ptr()], [bufs[0].data_ptr()])
+    assert ei.value.status == 1
+    efft.execute_host_stream([fwd], [], [], [bufs[0].data_ptr()])  # count 0 is a no-op
