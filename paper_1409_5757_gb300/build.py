@@ -1,11 +1,14 @@
 """Compile the CUDA libraries in-tree for sm_103a.
 
-    libefft.so         the transform (csrc/efft.cu; C ABI in include/efft.h)
+    libefft.so         the transform (csrc/efft.cu, efft_fx_df2.cu,
+                       efft_fx_f32.cu, efft_noalloc.cu; C ABI in include/efft.h)
     libefft_inputs.so  seeded device inputs and norms (csrc/inputs.cu;
                        include/efft_inputs.h), test/benchmark harness only
 
-Both are built with one -gencode (compute_103a -> sm_103a) in parallel; a
-library is rebuilt only when one of its sources is newer than the .so.
+Every translation unit is compiled to an object with one -gencode
+(compute_103a -> sm_103a), all in parallel, then linked; a library is
+rebuilt only when one of its sources or headers is newer than the .so.
+Objects go to _build/ (not tracked).
 """
 from __future__ import annotations
 
@@ -18,20 +21,21 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 INC = os.path.join(ROOT, "include")
+OBJ = os.path.join(ROOT, "_build")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-COMMON = ["-O3", "-lineinfo", "-std=c++17", "-shared", "-Xcompiler", "-fPIC", "-I", INC]
+COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INC]
 
+# library -> (translation units, headers they depend on)
 LIBS = {
-    "libefft.so": (["efft.cu", "efft_noalloc.cu"],
-                   ["efft.cu", "efft_noalloc.cu", "efft_kernels.cuh", "efft_arith.cuh"], ["efft.h"]),
-    "libefft_inputs.so": (["inputs.cu"], ["inputs.cu"], ["efft_inputs.h"]),
+    "libefft.so": (["efft.cu", "efft_fx_df2.cu", "efft_fx_f32.cu", "efft_noalloc.cu"],
+                   ["efft_kernels.cuh", "efft_arith.cuh"], ["efft.h"]),
+    "libefft_inputs.so": (["inputs.cu"], [], ["efft_inputs.h"]),
 }
 
 
 def nvcc() -> str:
-    cand = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
-    return cand
+    return shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
 
 
 def lib_path(name: str) -> str:
@@ -42,37 +46,51 @@ def _stale(name: str) -> bool:
     out = lib_path(name)
     if not os.path.exists(out):
         return True
-    _, deps, hdrs = LIBS[name]
+    srcs, hdrs, incs = LIBS[name]
     t = os.path.getmtime(out)
-    srcs = [os.path.join(CSRC, d) for d in deps] + [os.path.join(INC, h) for h in hdrs]
-    return any(os.path.getmtime(s) > t for s in srcs)
+    deps = [os.path.join(CSRC, d) for d in srcs + hdrs] + [os.path.join(INC, h) for h in incs]
+    return any(os.path.getmtime(s) > t for s in deps)
 
 
 def build(force: bool = False, verbose: bool = False) -> dict:
     """Build both libraries; returns {name: path}."""
+    os.makedirs(OBJ, exist_ok=True)
+    todo = [name for name in LIBS if force or _stale(name)]
     procs = []
-    for name, (srcs, _, _) in LIBS.items():
-        if not force and not _stale(name):
-            continue
-        out = lib_path(name)
-        tmp = out + ".tmp"
-        cmd = [nvcc(), *ARCH, *COMMON, "-o", tmp, *[os.path.join(CSRC, s) for s in srcs]]
-        if verbose:
-            print(" ".join(cmd), flush=True)
-        procs.append((name, out, tmp, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
+    for name in todo:
+        for src in LIBS[name][0]:
+            obj = os.path.join(OBJ, src.replace(".cu", f".{os.getpid()}.o"))
+            cmd = [nvcc(), *ARCH, *COMMON, "-c", "-o", obj, os.path.join(CSRC, src)]
+            if verbose:
+                print(" ".join(cmd), flush=True)
+            procs.append((name, src, obj, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
     errors = []
-    for name, out, tmp, p in procs:
+    objs = {name: [] for name in todo}
+    for name, src, obj, p in procs:
         log, _ = p.communicate()
         if p.returncode != 0:
-            errors.append(f"{name}:\n{log.decode(errors='replace')}")
+            errors.append(f"{src}:\n{log.decode(errors='replace')}")
         else:
-            os.replace(tmp, out)
+            objs[name].append(obj)
             if verbose and log:
                 print(log.decode(errors="replace"))
     if errors:
         raise RuntimeError("nvcc failed:\n" + "\n".join(errors))
+    for name in todo:
+        out = lib_path(name)
+        tmp = out + f".{os.getpid()}.tmp"
+        cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs[name]]
+        r = subprocess.run(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)
+        for o in objs[name]:
+            try:
+                os.remove(o)
+            except OSError:
+                pass
+        if r.returncode != 0:
+            raise RuntimeError(f"link of {name} failed:\n{r.stdout.decode(errors='replace')}")
+        os.replace(tmp, out)
     return {name: lib_path(name) for name in LIBS}
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose=True))
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))

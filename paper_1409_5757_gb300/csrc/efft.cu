@@ -21,6 +21,55 @@
 
 using namespace efft;
 
+namespace efft {
+// ----------------------------------------------------------------------------
+// Range scan: largest biased binary64 exponent among all re/im parts.
+// ----------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) efft_range_scan(const uint4* __restrict__ x, uint64_t n,
+                                                        uint32_t* __restrict__ state) {
+  uint32_t mx = 0;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (; i + 3 * stride < n; i += 4 * stride) {
+    uint4 v0 = __ldg(x + i), v1 = __ldg(x + i + stride), v2 = __ldg(x + i + 2 * stride),
+          v3 = __ldg(x + i + 3 * stride);
+    mx = max(mx, max(max(v0.y & 0x7FF00000u, v0.w & 0x7FF00000u), max(v1.y & 0x7FF00000u, v1.w & 0x7FF00000u)));
+    mx = max(mx, max(max(v2.y & 0x7FF00000u, v2.w & 0x7FF00000u), max(v3.y & 0x7FF00000u, v3.w & 0x7FF00000u)));
+  }
+  for (; i < n; i += stride) {
+    uint4 v = __ldg(x + i);
+    mx = max(mx, max(v.y & 0x7FF00000u, v.w & 0x7FF00000u));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, o));
+  __shared__ uint32_t wmax[8];
+  if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t r = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r = max(r, wmax[w]);
+    atomicMax(state, r >> 20);
+  }
+}
+
+// ----------------------------------------------------------------------------
+// Twiddle tables: out[t] = exp(-2*pi*i * t*stride / N) for t < count, FP64
+// sincospi (exact argument: N is a power of two) split into FP32 (hi, lo).
+// ----------------------------------------------------------------------------
+__global__ void efft_twiddles(float4* __restrict__ out, uint64_t count, uint64_t stride, int log2N) {
+  uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= count) return;
+  uint64_t mN = (t * stride) & ((1ull << log2N) - 1ull);
+  double x = -2.0 * ldexp((double)mN, -log2N);  // exact
+  double sv, cv;
+  sincospi(x, &sv, &cv);
+  float ch = __double2float_rn(cv), sh = __double2float_rn(sv);
+  float cl = __double2float_rn(cv - (double)ch), sl = __double2float_rn(sv - (double)sh);
+  out[t] = make_float4(ch, cl, sh, sl);
+}
+
+}  // namespace efft
+
 namespace {
 
 constexpr uint32_t kMagic = 0xEFF71409u;
@@ -86,12 +135,20 @@ int ilog2_u64(uint64_t n) {
 
 // Radix schedule.  Symmetric radix lists (R_j = R_{p-1-j}) make the final
 // digit reversal an involution, so it can be done in place by tile swaps.
+// For three passes (a, b, a) the table prefers radices 2^8..2^11 (the
+// specialised kernels), few internal stages (2^8 = 16*16 is the cheapest per
+// bit) and, once the array is large, at most 2^10 rows in the first pass: its
+// columns span the whole array, and 2^11 rows at page-sized strides exceed
+// the GPU's address-translation reach (measured: 2^30 with (10,10,10) runs
+// 10% faster than (11,8,11)).  2^32 and 2^33 need 2^11 in the first pass.
 int choose_radices(int e, int* r) {
   if (e <= 3) return 0;  // handled by the direct-sum kernel (or identity)
   if (e <= 11) { r[0] = e; return 1; }
   if (e <= 22 && (e % 2) == 0) { r[0] = r[1] = e / 2; return 2; }
-  int a = (e - 4) / 2;
-  if (a > 11) a = 11;
+  static const int kA[34] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0,
+                             /*13*/ 4, 0, /*15*/ 5, 0, /*17*/ 6, 0, /*19*/ 7, 0, /*21*/ 8, 0,
+                             /*23*/ 8, 8, 8, 8, 8, /*28*/ 10, /*29*/ 9, /*30*/ 10, /*31*/ 10, /*32*/ 11, /*33*/ 11};
+  const int a = kA[e];
   r[0] = r[2] = a;
   r[1] = e - 2 * a;
   return 3;
@@ -101,27 +158,6 @@ template <class P, int KIND, int CTA>
 void set_smem_attr() {
   cudaFuncSetAttribute(efft_pass<P, KIND, CTA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)((CTA + CTA / 16 + 1) * P::kElemBytes));
-}
-
-// specialised kernels: radices 2^8 .. 2^11 at full CTA width
-template <class P, int KIND, int LOG2CTA>
-void set_smem_attr_fx() {
-  const int bytes = (int)(((1 << LOG2CTA) + (1 << LOG2CTA) / 16 + 1) * P::kElemBytes);
-  cudaFuncSetAttribute(efft_pass_fx<P, KIND, 8, LOG2CTA - 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  cudaFuncSetAttribute(efft_pass_fx<P, KIND, 9, LOG2CTA - 9>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  cudaFuncSetAttribute(efft_pass_fx<P, KIND, 10, LOG2CTA - 10>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  cudaFuncSetAttribute(efft_pass_fx<P, KIND, 11, LOG2CTA - 11>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-}
-
-template <class P, int KIND, int LOG2CTA>
-bool launch_fx(int log2R, dim3 grid, dim3 block, size_t smem, cudaStream_t st, void* data, const PassArgs& a) {
-  switch (log2R) {
-    case 8: efft_pass_fx<P, KIND, 8, LOG2CTA - 8><<<grid, block, smem, st>>>(data, a); return true;
-    case 9: efft_pass_fx<P, KIND, 9, LOG2CTA - 9><<<grid, block, smem, st>>>(data, a); return true;
-    case 10: efft_pass_fx<P, KIND, 10, LOG2CTA - 10><<<grid, block, smem, st>>>(data, a); return true;
-    case 11: efft_pass_fx<P, KIND, 11, LOG2CTA - 11><<<grid, block, smem, st>>>(data, a); return true;
-    default: return false;
-  }
 }
 
 int init_kernels() {
@@ -136,13 +172,10 @@ int init_kernels() {
     set_smem_attr<PolicyF32, MID, 1 << kLog2CtaC64>();
     set_smem_attr<PolicyF32, LAST, 1 << kLog2CtaC64>();
     set_smem_attr<PolicyF32, SINGLE, 1 << kLog2CtaC64>();
-    set_smem_attr_fx<PolicyDF2, FIRST, kLog2CtaC128>();
-    set_smem_attr_fx<PolicyDF2, MID, kLog2CtaC128>();
-    set_smem_attr_fx<PolicyDF2, LAST, kLog2CtaC128>();
-    set_smem_attr_fx<PolicyF32, FIRST, kLog2CtaC64>();
-    set_smem_attr_fx<PolicyF32, MID, kLog2CtaC64>();
-    set_smem_attr_fx<PolicyF32, LAST, kLog2CtaC64>();
+    cudaError_t e1 = fx_set_attrs_df2();
+    cudaError_t e2 = fx_set_attrs_f32();
     err = cudaGetLastError();
+    if (err == cudaSuccess) err = (e1 != cudaSuccess) ? e1 : e2;
   });
   return err == cudaSuccess ? EFFT_OK : EFFT_ERR_CUDA;
 }
@@ -242,12 +275,8 @@ cudaError_t launch_pass(const efft_plan_s* p, const Pass& ps, void* data, cudaSt
   dim3 grid((unsigned)ps.grid), block(ps.threads);
   constexpr int LOG2CTA = (P::kElemBytes == 16) ? kLog2CtaC128 : kLog2CtaC64;
   if (ps.kind != SINGLE && ps.log2R >= 8 && ps.log2R <= 11 && ps.log2R + ps.log2C == LOG2CTA) {
-    bool ok = false;
-    switch (ps.kind) {
-      case FIRST: ok = launch_fx<PFX, FIRST, LOG2CTA>(ps.log2R, grid, block, ps.smem, st, data, a); break;
-      case MID: ok = launch_fx<PFX, MID, LOG2CTA>(ps.log2R, grid, block, ps.smem, st, data, a); break;
-      default: ok = launch_fx<PFX, LAST, LOG2CTA>(ps.log2R, grid, block, ps.smem, st, data, a); break;
-    }
+    const bool ok = (P::kElemBytes == 16) ? fx_launch_df2(ps.kind, ps.log2R, grid, block, ps.smem, st, data, a)
+                                          : fx_launch_f32(ps.kind, ps.log2R, grid, block, ps.smem, st, data, a);
     if (ok) return cudaGetLastError();
   }
   switch (ps.kind) {

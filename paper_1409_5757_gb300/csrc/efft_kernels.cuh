@@ -545,36 +545,6 @@ __global__ void efft_small(void* __restrict__ data, const PassArgs a) {
 }
 
 // ----------------------------------------------------------------------------
-// Range scan: largest biased binary64 exponent among all re/im parts.
-// ----------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) efft_range_scan(const uint4* __restrict__ x, uint64_t n,
-                                                        uint32_t* __restrict__ state) {
-  uint32_t mx = 0;
-  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  for (; i + 3 * stride < n; i += 4 * stride) {
-    uint4 v0 = __ldg(x + i), v1 = __ldg(x + i + stride), v2 = __ldg(x + i + 2 * stride),
-          v3 = __ldg(x + i + 3 * stride);
-    mx = max(mx, max(max(v0.y & 0x7FF00000u, v0.w & 0x7FF00000u), max(v1.y & 0x7FF00000u, v1.w & 0x7FF00000u)));
-    mx = max(mx, max(max(v2.y & 0x7FF00000u, v2.w & 0x7FF00000u), max(v3.y & 0x7FF00000u, v3.w & 0x7FF00000u)));
-  }
-  for (; i < n; i += stride) {
-    uint4 v = __ldg(x + i);
-    mx = max(mx, max(v.y & 0x7FF00000u, v.w & 0x7FF00000u));
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, o));
-  __shared__ uint32_t wmax[8];
-  if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = mx;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    uint32_t r = 0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r = max(r, wmax[w]);
-    atomicMax(state, r >> 20);
-  }
-}
-
-// ----------------------------------------------------------------------------
 // In-place digit reversal for radices (a, b, a): position (i0, i1, i2) with
 // i0, i2 < A, i1 < B swaps with (i2, i1, i0).  For fixed i1 this is the
 // transpose of an A x A matrix with row stride B*A; CTA z handles the tile
@@ -611,20 +581,14 @@ __global__ void __launch_bounds__(256) efft_digit_swap(E* __restrict__ data, int
   }
 }
 
-// ----------------------------------------------------------------------------
-// Twiddle tables: out[t] = exp(-2*pi*i * t*stride / N) for t < count, FP64
-// sincospi (exact argument: N is a power of two) split into FP32 (hi, lo).
-// ----------------------------------------------------------------------------
-__global__ void efft_twiddles(float4* __restrict__ out, uint64_t count, uint64_t stride, int log2N) {
-  uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= count) return;
-  uint64_t mN = (t * stride) & ((1ull << log2N) - 1ull);
-  double x = -2.0 * ldexp((double)mN, -log2N);  // exact
-  double sv, cv;
-  sincospi(x, &sv, &cv);
-  float ch = __double2float_rn(cv), sh = __double2float_rn(sv);
-  float cl = __double2float_rn(cv - (double)ch), sl = __double2float_rn(sv - (double)sh);
-  out[t] = make_float4(ch, cl, sh, sl);
-}
+// Launch interface of the specialised kernels (one translation unit per
+// policy, compiled in parallel): efft_fx_df2.cu (complex128, packed
+// double-float), efft_fx_f32.cu (complex64).
+cudaError_t fx_set_attrs_df2();
+bool fx_launch_df2(int kind, int log2R, dim3 grid, dim3 block, size_t smem, cudaStream_t st, void* data,
+                   const PassArgs& a);
+cudaError_t fx_set_attrs_f32();
+bool fx_launch_f32(int kind, int log2R, dim3 grid, dim3 block, size_t smem, cudaStream_t st, void* data,
+                   const PassArgs& a);
 
 }  // namespace efft

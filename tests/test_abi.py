@@ -95,8 +95,15 @@ def test_missing_library_fails_loudly(tmp_path, monkeypatch):
 
 
 def test_radix_schedule_is_symmetric():
-    """The planner's radices (mirrored here from the documented rule) are
-    symmetric so the digit reversal is an involution; all radices 16..2048."""
+    """The planner's three-pass table (read from the source) gives symmetric
+    radices, so the digit reversal is an involution; all radices 16..2048,
+    and at most 2^10 rows in the first pass below 2^32."""
+    src = open(os.path.join(ROOT, "paper_1409_5757_gb300", "csrc", "efft.cu")).read()
+    body = src[src.index("static const int kA[34] = {") + len("static const int kA[34] = {"):]
+    body = body[:body.index("};")]
+    kA = [int(v) for v in re.sub(r"/\*.*?\*/", "", body).replace("\n", " ").split(",")]
+    assert len(kA) == 34
+
     def choose(e):
         if e <= 3:
             return []
@@ -104,11 +111,12 @@ def test_radix_schedule_is_symmetric():
             return [e]
         if e <= 22 and e % 2 == 0:
             return [e // 2, e // 2]
-        a = min(11, (e - 4) // 2)
-        return [a, e - 2 * a, a]
+        return [kA[e], e - 2 * kA[e], kA[e]]
     for e in range(4, 34):
         r = choose(e)
         assert sum(r) == e and r == r[::-1] and all(4 <= x <= 11 for x in r), (e, r)
+        if 28 <= e <= 31:
+            assert r[0] <= 10, (e, r)
 
 
 def test_arith_constants_match_mpmath():
