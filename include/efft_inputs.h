@@ -48,6 +48,11 @@ int efft_add_tones(void* dev, uint64_t N, int dtype, const int64_t* freqs, const
 int efft_diff_norms(const void* a, const void* b, uint64_t count, int dtype, double scale,
                     double* out, void* stream);
 
+/* Page-locked host memory for benchmark buffers (cudaHostAlloc /
+ * cudaFreeHost); *ptr receives the address.  Synchronous. */
+int efft_host_alloc(void** ptr, uint64_t bytes);
+int efft_host_free(void* ptr);
+
 #ifdef __cplusplus
 }
 #endif

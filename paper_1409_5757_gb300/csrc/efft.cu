@@ -76,6 +76,7 @@ constexpr uint32_t kMagic = 0xEFF71409u;
 constexpr int kLog2CtaC128 = 12;  // 4096 complex128 elements per CTA (64 KiB)
 constexpr int kLog2CtaC64 = 13;   // 8192 complex64 elements per CTA (64 KiB)
 constexpr int kMaxPasses = 4;
+constexpr size_t kCopyChunk = size_t(1) << 30;  // host copies of the streaming entry point
 
 struct Pass {
   int log2R, log2s, log2L, log2C, kind;
@@ -591,17 +592,29 @@ int efft_execute_host_stream(const efft_plan_t* plans, int nplans, void* const* 
     void* buf = dev_bufs[b];
     // copy in once the buffer's previous result has been copied out
     if (used[b] && cudaStreamWaitEvent(sin, ev_out[b], 0) != cudaSuccess) { rc = EFFT_ERR_CUDA; break; }
-    if (cudaMemcpyAsync(buf, host_in[i], bytes, cudaMemcpyHostToDevice, sin) != cudaSuccess ||
-        cudaEventRecord(ev_in[b], sin) != cudaSuccess) { rc = EFFT_ERR_CUDA; break; }
+    // copies in 1 GiB pieces: the two copy directions then interleave on the
+    // link (measured 16+16 GiB: 118 ms whole, 100 ms in pieces)
+    for (size_t o = 0; rc == EFFT_OK && o < bytes; o += kCopyChunk) {
+      const size_t len = (bytes - o < kCopyChunk) ? bytes - o : kCopyChunk;
+      if (cudaMemcpyAsync(static_cast<char*>(buf) + o, static_cast<const char*>(host_in[i]) + o, len,
+                          cudaMemcpyHostToDevice, sin) != cudaSuccess)
+        rc = EFFT_ERR_CUDA;
+    }
+    if (rc != EFFT_OK || cudaEventRecord(ev_in[b], sin) != cudaSuccess) { rc = EFFT_ERR_CUDA; break; }
     // transforms in order on the caller's stream
     if (cudaStreamWaitEvent(sc, ev_in[b], 0) != cudaSuccess) { rc = EFFT_ERR_CUDA; break; }
     for (int j = 0; rc == EFFT_OK && j < nplans; ++j) rc = enqueue(plans[j], buf, sc);
     if (rc != EFFT_OK) break;
     if (cudaEventRecord(ev_comp[b], sc) != cudaSuccess) { rc = EFFT_ERR_CUDA; break; }
     // copy out
-    if (cudaStreamWaitEvent(sout, ev_comp[b], 0) != cudaSuccess ||
-        cudaMemcpyAsync(host_out[i], buf, bytes, cudaMemcpyDeviceToHost, sout) != cudaSuccess ||
-        cudaEventRecord(ev_out[b], sout) != cudaSuccess) { rc = EFFT_ERR_CUDA; break; }
+    if (cudaStreamWaitEvent(sout, ev_comp[b], 0) != cudaSuccess) { rc = EFFT_ERR_CUDA; break; }
+    for (size_t o = 0; rc == EFFT_OK && o < bytes; o += kCopyChunk) {
+      const size_t len = (bytes - o < kCopyChunk) ? bytes - o : kCopyChunk;
+      if (cudaMemcpyAsync(static_cast<char*>(host_out[i]) + o, static_cast<const char*>(buf) + o, len,
+                          cudaMemcpyDeviceToHost, sout) != cudaSuccess)
+        rc = EFFT_ERR_CUDA;
+    }
+    if (rc != EFFT_OK || cudaEventRecord(ev_out[b], sout) != cudaSuccess) { rc = EFFT_ERR_CUDA; break; }
     used[b] = true;
   }
   // drain everything that was enqueued, even after an error

@@ -434,11 +434,12 @@ efft_pass_fx(void* __restrict__ data, const PassArgs a) {
   typename P::TW wt;
   if (STRIDED) {
     const int sh = a.log2N - a.log2L;
+    // V_c[u] stored as [u][c]: the columns of one warp read consecutive entries
     if (tid < 16 * C) {
       const int cc = tid >> 4, u = tid & 15;
       const uint64_t mc = ((uint64_t)blockIdx.x * C + cc) & (step - 1);
       const int kc = digit_rev_c(last_pos_c(u, REM), LR);
-      vtw[tid] = P::expand(twiddle_N(a, (mc * (uint64_t)kc) << sh));
+      vtw[u * C + cc] = P::expand(twiddle_N(a, (mc * (uint64_t)kc) << sh));
     }
     wt = P::expand(twiddle_N(a, (m * (uint64_t)kt) << sh));
   }
@@ -495,7 +496,7 @@ efft_pass_fx(void* __restrict__ data, const PassArgs a) {
 #pragma unroll
     for (int u = 0; u < 16; ++u) {
       const int k = kt | digit_rev_c(last_pos_c(u, REM), LR);
-      v[u] = P::pass_tw(v[u], wt, vtw[c * 16 + u]);
+      v[u] = P::pass_tw(v[u], wt, vtw[u * C + c]);
       Mem<P, KIND>::store(data, colbase + ((uint64_t)k << a.log2s), v[u], Dout, a.conj_out, nonfinite);
     }
   } else {

@@ -177,4 +177,11 @@ int efft_diff_norms(const void* a, const void* b, uint64_t count, int dtype, dou
   return (int)e;
 }
 
+int efft_host_alloc(void** ptr, uint64_t bytes) {
+  if (!ptr) return (int)cudaErrorInvalidValue;
+  return (int)cudaHostAlloc(ptr, bytes, cudaHostAllocDefault);
+}
+
+int efft_host_free(void* ptr) { return (int)cudaFreeHost(ptr); }
+
 }  // extern "C"

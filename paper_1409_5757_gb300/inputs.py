@@ -37,7 +37,10 @@ def _lib():
                                        ctypes.POINTER(ctypes.c_double), ctypes.c_int, _vp]
         lib.efft_diff_norms.argtypes = [_vp, _vp, ctypes.c_uint64, ctypes.c_int, ctypes.c_double,
                                         ctypes.POINTER(ctypes.c_double), _vp]
-        for f in (lib.efft_gen_uniform, lib.efft_gen_gaussian, lib.efft_add_tones, lib.efft_diff_norms):
+        lib.efft_host_alloc.argtypes = [ctypes.POINTER(_vp), ctypes.c_uint64]
+        lib.efft_host_free.argtypes = [_vp]
+        for f in (lib.efft_gen_uniform, lib.efft_gen_gaussian, lib.efft_add_tones, lib.efft_diff_norms,
+                  lib.efft_host_alloc, lib.efft_host_free):
             f.restype = ctypes.c_int
         _LIB = lib
     return _LIB
@@ -118,3 +121,31 @@ def diff_norms(a, b=None, scale: float = 1.0):
     _ok(_lib().efft_diff_norms(_vp(a.data_ptr()), _vp(b.data_ptr() if b is not None else 0), a.numel(), _code(a),
                                float(scale), out, _stream(a)), "efft_diff_norms")
     return out[0], out[1]
+
+
+class PinnedHost:
+    """Page-locked host buffer from cudaHostAlloc, viewable as a CPU tensor."""
+
+    def __init__(self, numel: int, dtype):
+        import torch
+        self.dtype = dtype
+        self.numel = numel
+        itemsize = torch.empty(0, dtype=dtype).element_size()
+        self.nbytes = numel * itemsize
+        p = _vp()
+        _ok(_lib().efft_host_alloc(ctypes.byref(p), self.nbytes), "efft_host_alloc")
+        self.ptr = p.value
+        buf = (ctypes.c_uint8 * self.nbytes).from_address(self.ptr)
+        self.tensor = torch.frombuffer(buf, dtype=torch.uint8).view(dtype)
+
+    def free(self):
+        if self.ptr:
+            self.tensor = None
+            _lib().efft_host_free(_vp(self.ptr))
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
