@@ -55,6 +55,50 @@ def flops(n: int) -> float:
     return 5.0 * n * math.log2(n)
 
 
+def max_over_ranks(value: float, device=None) -> float:
+    """The largest value over all ranks (the job's time is its slowest rank)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return value
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world: int, transforms_per_step: int, n: int, ms_per_step: float) -> float:
+    """Whole-job GFLOP/s: every rank transforms its own array (replicas)."""
+    return world * transforms_per_step * flops(n) / (ms_per_step * 1e-3) / 1e9
+
+
+def kernel_fingerprint() -> str:
+    import hashlib
+    h = hashlib.sha1()
+    for f in ("efft_kernels.cuh", "efft_arith.cuh", "efft_fx_df2.cu", "efft_fx_f32.cu"):
+        with open(os.path.join(ROOT, "paper_1409_5757_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(workload: str, log2n: int, kernel: str):
+    """DRAM bytes per launch and pipe figures from the committed ncu summary,
+    or None when there is none for this kernel or the kernel changed since."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+    try:
+        fp = kernel_fingerprint()
+        with open(path) as f:
+            for line in f:
+                if not line.strip() or line.startswith("#"):
+                    continue
+                w, e, k, b, fma, issue, src_fp, *src = line.split()
+                if w == workload and int(e) == log2n and k == kernel and src_fp == fp:
+                    return {"bytes": float(b), "fma_pipe_pct": float(fma), "issue_pct": float(issue),
+                            "source": " ".join(src)}
+    except (OSError, ValueError):
+        pass
+    return None
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -280,13 +324,9 @@ def run_ours(args, wl):
     fwd.profile(False)
     inv.profile(False)
 
-    if world > 1:
-        t = torch.tensor([elapsed_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
-
+    elapsed_ms = max_over_ranks(elapsed_ms, dev)
     ms_per_step = elapsed_ms / K
-    value = world * tps * flops(N) / (ms_per_step * 1e-3) / 1e9
+    value = job_rate(world, tps, N, ms_per_step)
     hbm_passes = fwd.info()["hbm_passes"]
     hbm_gbs = world * tps * hbm_passes * 2 * N * S / (ms_per_step * 1e-3) / 1e9
 
@@ -306,8 +346,13 @@ def run_ours(args, wl):
         per_launch_s = tot_ms / nl * 1e-3
         alg_bytes = (1 if name == "range_scan" else 2) * N * S
         achieved = alg_bytes / per_launch_s / 1e9
+        tr = measured_traffic(args.workload, wl["log2n"], name)
         roofline = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                    "frac": achieved / peak, "traffic": None,
+                    "frac": achieved / peak, "traffic": tr["bytes"] if tr else None,
+                    "traffic_source": tr["source"] if tr else None,
+                    "fp32_view": ({"fma_pipe_active_pct": tr["fma_pipe_pct"], "issue_active_pct": tr["issue_pct"],
+                                   "note": "the double-float pass kernels are bound by FP32 issue, not HBM"}
+                                  if tr else None),
                     "peak_kind": f"{peak_kind} STREAM-style copy (MEASURED_PEAKS.json hbm_gbs)",
                     "per_launch_ms": tot_ms / nl, "algorithmic_bytes_per_launch": alg_bytes,
                     "kernels_ms_per_step": {k: v[0] / K for k, v in prof.items()}}
