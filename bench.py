@@ -1,7 +1,7 @@
 #!/usr/bin/env python3
 """Throughput of the in-place 1-D complex DFT on GB300.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload c2|c3|c1|c4]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload c2|c3|c1|c4|c5]
                     [--impl ours|reference]
 
 Default workload (the headline configuration): one step = a forward DFT
@@ -10,6 +10,10 @@ N = 2^30 complex128 points in place (16 GiB), input uniform[-1,1) re/im plus
 64 seeded tones.  value = 5*N*log2(N) flop per transform x transforms / time
 (GFLOP/s, BASELINE metric), whole job.  The input (16 GiB) is larger than the
 129 MB L2, so no flush is needed between timed iterations.
+
+Workload c5 (batched, mixed sizes): 256 complex64 transforms of 2^12..2^24
+points in one arena, each direction one efft_batch_execute (one CUDA graph
+launch); a step = forward + normalised conjugate-sign transform of all 256.
 
 --impl reference times the CPU oracle (the FP64 radix-2 FFT, as it stands)
 on the host cores on a bounded sample of the same workload.
@@ -47,6 +51,10 @@ WORKLOADS = {
                desc="complex128 N=2^20 in place, one transform per step; uniform[-1,1) re/im"),
     "c4": dict(log2n=31, dtype="c64", seed=4, tones=0, fwd_inv=False, gauss=True,
                desc="complex64 N=2^31 in place, one transform per step; Gaussian(0,1) re/im"),
+    "c5": dict(batch=256, emin=12, emax=24, log2n=24, dtype="c64", seed=5, tones=0, fwd_inv=True, gauss=False,
+               desc="256 complex64 transforms in place, N_i = 2^e_i with e_i uniform in {12..24} (seed 5), "
+                    "one graph launch per direction: forward, then the normalised conjugate-sign transform; "
+                    "uniform[-1,1) re/im"),
 }
 DTYPE_NAME = {"c128": "df32 (double-float f32 pairs; complex128 in/out)", "c64": "f32 (complex64)"}
 
@@ -191,11 +199,62 @@ def oracle_sample_log2n(target_s: float, cap: int) -> int:
     return 20
 
 
+def batch_sizes(wl):
+    """The batch workload's log2 sizes: uniform integers in [emin, emax] from
+    numpy's default generator seeded with the workload seed."""
+    import numpy as np
+    return [int(e) for e in np.random.default_rng(wl["seed"]).integers(wl["emin"], wl["emax"] + 1, wl["batch"])]
+
+
+def oracle_batch_time(wl, budget_s: float):
+    """The oracle's forward transforms of the batch's arrays, in batch order,
+    until budget_s has passed: (flop, seconds, transforms, threads)."""
+    import oracle
+    o = oracle.get()
+    fl, el, k = 0.0, 0.0, 0
+    for i, e in enumerate(batch_sizes(wl)):
+        x = o.gen_uniform(wl["seed"] * 1000 + i, 1 << e)
+        t0 = time.perf_counter()
+        o.fft_radix2(x, -1)
+        el += time.perf_counter() - t0
+        fl += flops(1 << e)
+        k += 1
+        if el >= budget_s:
+            break
+    return fl, el, k, o.threads
+
+
+def run_reference_batch(args, wl):
+    K, W = args.steps, args.warmup
+    budget = 150.0 / max(K + W, 1)
+    rates, cores, k = [], None, 0
+    for i in range(W + K):
+        fl, el, k, cores = oracle_batch_time(wl, budget)
+        if i >= W:
+            rates.append(fl / el)
+    value = statistics.mean(rates) / 1e9
+    total = sum(2 * flops(1 << e) for e in batch_sizes(wl))
+    ms = total / (value * 1e9) * 1e3
+    sample = (f"FP64 radix-2 oracle, forward transforms of the first {k} arrays of the batch (in batch order) "
+              f"per step, about {budget:.0f} s of host time; a full step is 2 x 256 transforms")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": args.gpus,
+        "steps": K, "warmup": W, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config_of(wl),
+        "cpu_baseline": {"value": value, "unit": "GFLOP/s", "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_reference(args, wl):
     import oracle  # noqa: F401
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
+    if wl.get("batch"):
+        return run_reference_batch(args, wl)
     K, W = args.steps, args.warmup
     budget = 150.0 / max(K + W, 1)
     e = oracle_sample_log2n(budget, wl["log2n"])
@@ -223,6 +282,13 @@ def run_reference(args, wl):
 
 
 def config_of(wl):
+    if wl.get("batch"):
+        es = batch_sizes(wl)
+        return {"workload": wl["desc"], "transforms": len(es), "log2N_min": min(es), "log2N_max": max(es),
+                "elements_total": sum(1 << e for e in es), "element": "complex64" if wl["dtype"] == "c64"
+                else "complex128", "transforms_per_step": 2 * len(es), "in_place": True,
+                "l2_between_steps": "inputs larger than L2 (no flush needed)", "seed": wl["seed"],
+                "parallelism": "replicas only (one batch per GPU)"}
     return {"workload": wl["desc"], "N": 1 << wl["log2n"], "log2N": wl["log2n"],
             "element": "complex128" if wl["dtype"] == "c128" else "complex64",
             "transforms_per_step": 2 if wl["fwd_inv"] else 1, "in_place": True,
@@ -415,6 +481,145 @@ def run_ours(args, wl):
     return 0
 
 
+def run_batch(args, wl):
+    """Workload c5: two batch executes per step over one arena."""
+    import torch
+    import torch.distributed as dist
+
+    import paper_1409_5757_gb300 as efft
+    from paper_1409_5757_gb300 import build as _build
+    from paper_1409_5757_gb300 import inputs
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+    if rank == 0:
+        _build.build()
+    if world > 1:
+        dist.barrier()
+
+    es = batch_sizes(wl)
+    c128 = wl["dtype"] == "c128"
+    tdt = torch.complex128 if c128 else torch.complex64
+    code = efft.EFFT_C128 if c128 else efft.EFFT_C64
+    S = 16 if c128 else 8
+    total = sum(1 << e for e in es)
+    offs = [0]
+    for e in es:
+        offs.append(offs[-1] + (1 << e))
+    arena = torch.empty(total, dtype=tdt, device=dev)
+    inputs.fill_uniform(arena, wl["seed"])
+    keep = arena.clone()
+    ptrs = [arena.data_ptr() + o * S for o in offs[:-1]]
+    sizes = [1 << e for e in es]
+    fwd = efft.Batch(sizes, code, -1)
+    inv = efft.Batch(sizes, code, +1, efft.EFFT_FLAG_NORMALIZE)
+    kernels = fwd.info()["kernels"] + inv.info()["kernels"]
+    stream = torch.cuda.current_stream(dev)
+    sp = stream.cuda_stream
+
+    def step():
+        fwd.execute(ptrs, sp)
+        inv.execute(ptrs, sp)
+
+    K, W = args.steps, args.warmup
+    for _ in range(W):
+        step()
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    sampler = ClockSampler(dev.index)
+    sampler.start()
+    time.sleep(0.3)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * K + 1)]
+    ev[0].record(stream)
+    for i in range(K):
+        fwd.execute(ptrs, sp)
+        ev[2 * i + 1].record(stream)
+        inv.execute(ptrs, sp)
+        ev[2 * i + 2].record(stream)
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    clocks = sampler.stop()
+    elapsed_ms = ev[0].elapsed_time(ev[2 * K])
+    graph_ms = [ev[j].elapsed_time(ev[j + 1]) for j in range(2 * K)]
+
+    elapsed_ms = max_over_ranks(elapsed_ms, dev)
+    ms_per_step = elapsed_ms / K
+    step_flop = 2 * sum(flops(n) for n in sizes)
+    value = world * step_flop / (ms_per_step * 1e-3) / 1e9
+    passes = {}
+    for e in sorted(set(es)):
+        passes[e] = efft.Plan(1 << e, code, -1).info()["hbm_passes"]
+    step_bytes = 2 * sum(passes[e] * 2 * (1 << e) * S for e in es)
+    hbm_gbs = world * step_bytes / (ms_per_step * 1e-3) / 1e9
+
+    num, den = inputs.diff_norms(arena, keep, 1.0)
+    accuracy = {"roundtrip_rel_l2_after_all_steps": math.sqrt(num / den), "round_trips": W + K,
+                "tolerance_per_round_trip": 2e-14 * wl["emax"] if c128 else 4e-6 * wl["emax"]}
+
+    peak, peak_kind = peaks()
+    per_graph_s = statistics.median(graph_ms) * 1e-3
+    achieved = step_bytes / 2 / per_graph_s / 1e9
+    roofline = {"bound": "hbm", "kernel": "one batch graph launch (all kernels of 256 transforms)",
+                "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                "peak_kind": f"{peak_kind} STREAM-style copy (MEASURED_PEAKS.json hbm_gbs)",
+                "per_launch_ms": per_graph_s * 1e3, "algorithmic_bytes_per_launch": step_bytes / 2,
+                "graph_kernel_nodes": kernels // 2}
+
+    e2e = None
+    if not args.no_e2e:
+        # the public API with host data: pinned host arena -> device, both batch
+        # executes, device -> pinned host, every step
+        hin = torch.empty(total, dtype=tdt, pin_memory=True)
+        hin.copy_(keep)
+        hout = torch.empty(total, dtype=tdt, pin_memory=True)
+        Ke = max(3, K)
+        for i in range(Ke + 1):
+            if i == 1:
+                torch.cuda.synchronize(dev)
+                t0 = time.perf_counter()
+            arena.copy_(hin, non_blocking=True)
+            step()
+            hout.copy_(arena, non_blocking=True)
+        torch.cuda.synchronize(dev)
+        dt = (time.perf_counter() - t0) / Ke
+        e2e = {"value": world * step_flop / dt / 1e9, "unit": "GFLOP/s", "h2d_bytes_per_step": total * S,
+               "d2h_bytes_per_step": total * S, "ms_per_step": dt * 1e3, "steps": Ke,
+               "api": "efft_batch_execute x2 between torch pinned-memory copies of the whole arena"}
+        del hin, hout
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        fl, el, k, cores = oracle_batch_time(wl, 20.0)
+        cpu = {"value": fl / el / 1e9, "unit": "GFLOP/s", "cores": cores, "kind": "oracle",
+               "sample": f"forward FP64 radix-2 oracle transforms of the first {k} arrays of the batch, {el:.1f} s"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": K, "warmup": W,
+            "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": DTYPE_NAME[wl["dtype"]], "data": "synthetic", "config": config_of(wl),
+            "hbm_gbs": hbm_gbs, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": K * kernels, "clocks": clocks, "accuracy": accuracy, "impl": "ours",
+        }
+        print(json.dumps(line), flush=True)
+    fwd.destroy()
+    inv.destroy()
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -432,11 +637,13 @@ def main():
         wl["log2n"] = args.log2n
         wl["desc"] = wl["desc"].replace("2^30", f"2^{args.log2n}").replace("2^33", f"2^{args.log2n}")
     if args.steps is None:
-        args.steps = {"c2": 20, "c3": 6, "c1": 200, "c4": 40}[args.workload]
+        args.steps = {"c2": 20, "c3": 6, "c1": 200, "c4": 40, "c5": 40}[args.workload]
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args, wl)
+    if wl.get("batch"):
+        return run_batch(args, wl)
     return run_ours(args, wl)
 
 

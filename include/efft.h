@@ -78,7 +78,17 @@ enum efft_status {
  *    two).  Not part of Eq. 1, which is unnormalised; with sign = +1 it gives
  *    the inverse DFT, so forward then normalised inverse returns x. */
 #define EFFT_FLAG_NORMALIZE 0x2u
-#define EFFT_FLAG_ALL 0x3u
+/*  EFFT_FLAG_AUTOTUNE: choose the radix schedule by measurement instead of
+ *    the built-in table (the GPU counterpart of the paper's scan over the
+ *    split depth s and the worker count, Sec. 5.2, Figs. 6-7).  A schedule
+ *    cached for (device, n, dtype) by an earlier tuning is reused; otherwise,
+ *    if n*S <= EFFT_AUTOTUNE_MAX_BYTES, efft_plan_create allocates a
+ *    temporary n*S-byte buffer and runs efft_plan_autotune on it.  Larger n
+ *    keep the table's schedule unless efft_plan_autotune is called with a
+ *    caller buffer.  Results are unchanged up to rounding. */
+#define EFFT_FLAG_AUTOTUNE 0x4u
+#define EFFT_FLAG_ALL 0x7u
+#define EFFT_AUTOTUNE_MAX_BYTES (1ull << 31)
 
 typedef struct efft_plan_s* efft_plan_t;
 
@@ -150,6 +160,38 @@ int efft_execute_host_stream(const efft_plan_t* plans, int nplans, void* const* 
                              void* const* host_out, int count, void* const* dev_bufs, int nbufs,
                              void* stream);
 
+/*
+ * Create a plan with an explicit radix schedule (log2 R_0 .. log2 R_{p-1});
+ * otherwise as efft_plan_create.  Accepted schedules:
+ *  p = 0 for n <= 8 (direct sums);
+ *  p = 1 with log2 R_0 = log2 n in [4, 11];
+ *  p = 2 or 3 with every log2 R_j in [4, 11], sum log2 n, and R_0 = R_{p-1}
+ *    (symmetric: the digit reversal is then an involution, done in place).
+ * Any other schedule: EFFT_ERR_UNSUPPORTED (before any CUDA call).
+ * EFFT_FLAG_AUTOTUNE is rejected here (EFFT_ERR_INVALID_FLAGS).
+ */
+int efft_plan_create_with_radices(efft_plan_t* out, uint64_t n, int dtype, int sign, uint32_t flags,
+                                  const int* log2_radices, int npasses);
+
+/*
+ * Time every accepted schedule (above) for the plan's n and switch the plan
+ * to the fastest; the choice is cached for (device, n, dtype) and used by
+ * later plans created with EFFT_FLAG_AUTOTUNE.  Each candidate is run on
+ * `scratch` (n*S bytes of the caller's device memory on the plan's device;
+ * its contents are overwritten) on `stream`, twice untimed and then a few
+ * times between CUDA events; its time is the median.  Synchronous.  No
+ * execute of the plan may be in flight, and the plan must not be used by
+ * another host thread meanwhile.
+ *  cand_log2r  [out, may be NULL] room for cap*4 ints: candidate c's
+ *              log2 radices at [4c, 4c+4), unused entries 0.
+ *  cand_ms     [out, may be NULL] room for cap doubles: candidate c's time.
+ *  ncand       [out, may be NULL] number of candidates (may exceed cap).
+ * For n <= 8 there is nothing to tune (*ncand = 1, the direct-sum kernel).
+ * Errors: INVALID_PLAN, INVALID_PTR, MISALIGNED, LAUNCH, CUDA.
+ */
+int efft_plan_autotune(efft_plan_t plan, void* scratch, void* stream, int* cand_log2r, double* cand_ms,
+                       int cap, int* ncand);
+
 /* Destroy a plan and free its device tables.  NULL is accepted (no-op).
  * Errors: INVALID_PLAN for a handle that is not a live plan. */
 int efft_plan_destroy(efft_plan_t plan);
@@ -218,6 +260,44 @@ int efft_plan_profile_read(efft_plan_t plan, double* ms, int* count, int cap, in
  */
 #define EFFT_NOALLOC_MAX_LOG2N 24
 int efft_execute_noalloc(void* data, uint64_t n, int dtype, int sign, uint32_t flags, void* stream);
+
+/*
+ * Batches: `count` independent in-place transforms of mixed power-of-two
+ * sizes run by one CUDA graph launch.  The paper's many sub-FFTs of one
+ * split (Sec. 3.3), whose order is left to the Cilk scheduler, become one
+ * user-level batch whose order is fixed once, at creation.
+ *
+ * efft_batch_create: transform i has sizes[i] points (a power of two,
+ *   1 <= sizes[i] <= 2^EFFT_MAX_LOG2N); all share dtype, sign and flags
+ *   (EFFT_FLAG_AUTOTUNE applies per distinct size).  Transforms of equal
+ *   size share one plan and run in the same kernel launches (one grid row
+ *   per transform); distinct sizes run as parallel branches of one CUDA
+ *   graph that is captured here and replayed by every execute.  Allocates
+ *   the plans' tables, a device array of `count` pointers, 16 bytes of
+ *   device state per transform and pinned host staging for
+ *   EFFT_BATCH_INFLIGHT * count pointers, then synchronises.
+ *   Errors: INVALID_SIZE (count < 1, a bad size, more than 65535 transforms
+ *   of one size), INVALID_PTR (sizes NULL), the plan errors, ALLOC, CUDA.
+ * efft_batch_execute: data is a HOST array of `count` device pointers;
+ *   data[i] is transform i's buffer with the rules of efft_execute.  The
+ *   pointers are copied to pinned staging, then to the device on `stream`
+ *   ahead of the graph launch, so `data` may be reused on return.
+ *   Asynchronous.  Executes of one batch must be stream-ordered (they share
+ *   the device pointer array and state); at most EFFT_BATCH_INFLIGHT of them
+ *   are outstanding: the next one first waits on the host for the oldest.
+ *   Errors: INVALID_PLAN (not a live batch), INVALID_PTR, MISALIGNED, LAUNCH.
+ * efft_batch_info: *ngroups = number of distinct sizes; *kernels = kernel
+ *   nodes in the graph (kernel launches per execute).  Either may be NULL.
+ * efft_batch_destroy: waits for the batch's outstanding executes, then
+ *   frees everything.  NULL is a no-op; INVALID_PLAN for a foreign handle.
+ */
+#define EFFT_BATCH_INFLIGHT 4
+typedef struct efft_batch_s* efft_batch_t;
+int efft_batch_create(efft_batch_t* out, const uint64_t* sizes, int count, int dtype, int sign,
+                      uint32_t flags);
+int efft_batch_execute(efft_batch_t batch, void* const* data, void* stream);
+int efft_batch_info(efft_batch_t batch, int* ngroups, int* kernels);
+int efft_batch_destroy(efft_batch_t batch);
 
 #ifdef __cplusplus
 }

@@ -24,6 +24,8 @@ EFFT_C64 = 0
 EFFT_C128 = 1
 EFFT_FLAG_DIGIT_REVERSED_OUT = 0x1
 EFFT_FLAG_NORMALIZE = 0x2
+EFFT_FLAG_AUTOTUNE = 0x4
+EFFT_BATCH_INFLIGHT = 4
 PROFILE_SLOTS = ("range_scan", "pass0", "pass1", "pass2", "pass3", "digit_swap", "direct_small")
 EFFT_MAX_LOG2N = 33
 
@@ -54,6 +56,15 @@ _SIGNATURES = {
     "efft_execute_host_stream": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, ctypes.POINTER(_vp),
                                                 ctypes.POINTER(_vp), ctypes.c_int, ctypes.POINTER(_vp), ctypes.c_int,
                                                 _vp]),
+    "efft_plan_create_with_radices": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_uint64, ctypes.c_int, ctypes.c_int,
+                                                     ctypes.c_uint32, ctypes.POINTER(ctypes.c_int), ctypes.c_int]),
+    "efft_plan_autotune": (ctypes.c_int, [_vp, _vp, _vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
+                                          ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+    "efft_batch_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.POINTER(ctypes.c_uint64), ctypes.c_int,
+                                         ctypes.c_int, ctypes.c_int, ctypes.c_uint32]),
+    "efft_batch_execute": (ctypes.c_int, [_vp, ctypes.POINTER(_vp), _vp]),
+    "efft_batch_info": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+    "efft_batch_destroy": (ctypes.c_int, [_vp]),
 }
 
 
@@ -100,10 +111,19 @@ def _check(status: int, what: str):
 class Plan:
     """Owning wrapper of an efft_plan_t (efft_plan_create / efft_plan_destroy)."""
 
-    def __init__(self, n: int, dtype: int = EFFT_C128, sign: int = -1, flags: int = 0):
+    def __init__(self, n: int, dtype: int = EFFT_C128, sign: int = -1, flags: int = 0, radices=None):
+        """radices: optional explicit schedule, log2 R_0..R_{p-1}
+        (efft_plan_create_with_radices); None = the built-in table, or the
+        measured choice with EFFT_FLAG_AUTOTUNE."""
         self._h = _vp()
-        _check(_lib().efft_plan_create(ctypes.byref(self._h), int(n), int(dtype), int(sign), int(flags)),
-               "efft_plan_create")
+        if radices is None:
+            _check(_lib().efft_plan_create(ctypes.byref(self._h), int(n), int(dtype), int(sign), int(flags)),
+                   "efft_plan_create")
+        else:
+            r = (ctypes.c_int * max(len(radices), 1))(*[int(v) for v in radices])
+            _check(_lib().efft_plan_create_with_radices(ctypes.byref(self._h), int(n), int(dtype), int(sign),
+                                                        int(flags), r, len(radices)),
+                   "efft_plan_create_with_radices")
         self.n, self.dtype, self.sign, self.flags = int(n), int(dtype), int(sign), int(flags)
 
     @property
@@ -128,6 +148,17 @@ class Plan:
         _check(_lib().efft_plan_info(self._h, ctypes.byref(hp), ctypes.byref(tb)), "efft_plan_info")
         return {"hbm_passes": hp.value, "table_bytes": tb.value}
 
+    def autotune(self, scratch_ptr: int, stream: int = 0) -> list[tuple[list[int], float]]:
+        """efft_plan_autotune on a caller buffer of n elements (overwritten):
+        [(log2 radices, median ms)] per candidate; the plan keeps the fastest."""
+        cap = 16
+        r = (ctypes.c_int * (4 * cap))()
+        ms = (ctypes.c_double * cap)()
+        nc = ctypes.c_int()
+        _check(_lib().efft_plan_autotune(self._h, _vp(scratch_ptr), _vp(stream), r, ms, cap, ctypes.byref(nc)),
+               "efft_plan_autotune")
+        return [([v for v in r[4 * c:4 * c + 4] if v], ms[c]) for c in range(min(nc.value, cap))]
+
     def profile(self, enable: bool = True) -> None:
         """Start (clearing old records) or stop per-launch CUDA-event timing."""
         _check(_lib().efft_plan_profile(self._h, 1 if enable else 0), "efft_plan_profile")
@@ -149,6 +180,42 @@ class Plan:
         try:
             if self._h and _LIB is not None:
                 _LIB.efft_plan_destroy(self._h)
+        except Exception:
+            pass
+
+
+class Batch:
+    """Owning wrapper of an efft_batch_t: `len(sizes)` in-place transforms of
+    mixed power-of-two sizes, one CUDA graph launch per execute."""
+
+    def __init__(self, sizes, dtype: int = EFFT_C64, sign: int = -1, flags: int = 0):
+        self.sizes = [int(v) for v in sizes]
+        self.dtype, self.sign, self.flags = int(dtype), int(sign), int(flags)
+        arr = (ctypes.c_uint64 * max(len(self.sizes), 1))(*self.sizes)
+        self._h = _vp()
+        _check(_lib().efft_batch_create(ctypes.byref(self._h), arr, len(self.sizes), self.dtype, self.sign,
+                                        self.flags), "efft_batch_create")
+
+    def execute(self, data_ptrs, stream: int = 0) -> None:
+        if len(data_ptrs) != len(self.sizes):
+            raise ValueError(f"efft batch of {len(self.sizes)} transforms got {len(data_ptrs)} buffers")
+        arr = (_vp * len(data_ptrs))(*[_vp(int(v)) for v in data_ptrs])
+        _check(_lib().efft_batch_execute(self._h, arr, _vp(stream)), "efft_batch_execute")
+
+    def info(self) -> dict:
+        g, k = ctypes.c_int(), ctypes.c_int()
+        _check(_lib().efft_batch_info(self._h, ctypes.byref(g), ctypes.byref(k)), "efft_batch_info")
+        return {"groups": g.value, "kernels": k.value}
+
+    def destroy(self) -> None:
+        if self._h:
+            _check(_lib().efft_batch_destroy(self._h), "efft_batch_destroy")
+            self._h = _vp()
+
+    def __del__(self):
+        try:
+            if self._h and _LIB is not None:
+                _LIB.efft_batch_destroy(self._h)
         except Exception:
             pass
 
@@ -183,11 +250,29 @@ def get_plan(n: int, dtype: int, sign: int = -1, flags: int = 0) -> Plan:
     return p
 
 
+_BATCHES: dict = {}
+
+
+def get_batch(sizes, dtype: int, sign: int = -1, flags: int = 0) -> Batch:
+    """Cached batch for (device, sizes, dtype, sign, flags)."""
+    import torch
+    key = (torch.cuda.current_device(), tuple(int(v) for v in sizes), int(dtype), int(sign), int(flags))
+    with _PLANS_LOCK:
+        b = _BATCHES.get(key)
+        if b is None:
+            b = Batch(sizes, dtype, sign, flags)
+            _BATCHES[key] = b
+    return b
+
+
 def clear_plans() -> None:
     with _PLANS_LOCK:
         for p in _PLANS.values():
             p.destroy()
         _PLANS.clear()
+        for b in _BATCHES.values():
+            b.destroy()
+        _BATCHES.clear()
 
 
 def _dtype_code(t) -> int:
@@ -214,6 +299,29 @@ def fft_(t, sign: int = -1, flags: int = 0, stream=None):
     return t
 
 
+def fft_batch_(tensors, sign: int = -1, flags: int = 0, stream=None):
+    """In-place DFTs of a list of contiguous 1-D CUDA complex tensors of one
+    dtype and device (power-of-two lengths, not overlapping) by one batch
+    execute; returns the list."""
+    import torch
+    if not tensors:
+        return tensors
+    code = _dtype_code(tensors[0])
+    dev = tensors[0].device
+    for t in tensors:
+        if not t.is_cuda or t.device != dev:
+            raise ValueError("efft.fft_batch_: tensors must be on one CUDA device")
+        if not t.is_contiguous():
+            raise ValueError("efft.fft_batch_: tensors must be contiguous")
+        if _dtype_code(t) != code:
+            raise ValueError("efft.fft_batch_: tensors must share one dtype")
+    with torch.cuda.device(dev):
+        b = get_batch([t.numel() for t in tensors], code, sign, flags)
+        s = stream if stream is not None else torch.cuda.current_stream(dev)
+        b.execute([t.data_ptr() for t in tensors], s.cuda_stream)
+    return tensors
+
+
 def fft(t, sign: int = -1):
     """Out-of-place convenience: clone then fft_."""
     return fft_(t.clone(), sign)
@@ -223,5 +331,6 @@ def version() -> int:
     return _lib().efft_version()
 
 
-__all__ = ["Plan", "EfftError", "fft_", "fft", "get_plan", "clear_plans", "version", "lib_path", "execute_host_stream",
-           "EFFT_C64", "EFFT_C128", "EFFT_FLAG_DIGIT_REVERSED_OUT", "EFFT_FLAG_NORMALIZE"]
+__all__ = ["Plan", "Batch", "EfftError", "fft_", "fft", "fft_batch_", "get_plan", "get_batch", "clear_plans", "version",
+           "lib_path", "execute_host_stream", "EFFT_C64", "EFFT_C128", "EFFT_FLAG_DIGIT_REVERSED_OUT",
+           "EFFT_FLAG_NORMALIZE", "EFFT_FLAG_AUTOTUNE"]

@@ -11,7 +11,7 @@ from __future__ import annotations
 
 import torch
 
-from . import EFFT_FLAG_NORMALIZE, fft_
+from . import EFFT_FLAG_NORMALIZE, fft_, fft_batch_
 
 
 class _DFT(torch.autograd.Function):
@@ -31,9 +31,36 @@ class _DFT(torch.autograd.Function):
         return gx, None, None
 
 
+class _BatchDFT(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, sign: int, normalize: bool, *xs):
+        ctx.sign = sign
+        ctx.normalize = normalize
+        ctx.like = [torch.empty(0, dtype=x.dtype, device=x.device) for x in xs]
+        ctx.shapes = [x.shape for x in xs]
+        ys = [x.contiguous().clone() for x in xs]
+        fft_batch_(ys, sign, EFFT_FLAG_NORMALIZE if normalize else 0)
+        return tuple(ys)
+
+    @staticmethod
+    def backward(ctx, *gs):
+        # an output that did not reach the loss has no gradient: zeros
+        gx = [g.contiguous().clone() if g is not None else l.new_zeros(sh)
+              for g, l, sh in zip(gs, ctx.like, ctx.shapes)]
+        fft_batch_(gx, -ctx.sign, EFFT_FLAG_NORMALIZE if ctx.normalize else 0)
+        return (None, None, *gx)
+
+
 def dft(x: torch.Tensor, sign: int = -1, normalize: bool = False) -> torch.Tensor:
     """Out-of-place, differentiable X = F x (1-D contiguous CUDA complex tensor)."""
     return _DFT.apply(x, sign, normalize)
 
 
-__all__ = ["dft"]
+def dft_batch(xs, sign: int = -1, normalize: bool = False) -> list:
+    """Differentiable DFTs of a list of 1-D CUDA complex tensors (mixed
+    power-of-two lengths, one dtype) by one batch execute forward and one
+    (opposite sign) backward."""
+    return list(_BatchDFT.apply(sign, normalize, *xs))
+
+
+__all__ = ["dft", "dft_batch"]

@@ -7,13 +7,16 @@
 // word; an execute enqueues the pass kernels on the caller's stream.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <atomic>
 #include <cstdint>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <new>
 #include <set>
+#include <tuple>
 #include <vector>
 
 #include "../../include/efft.h"
@@ -26,7 +29,11 @@ namespace efft {
 // Range scan: largest biased binary64 exponent among all re/im parts.
 // ----------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) efft_range_scan(const uint4* __restrict__ x, uint64_t n,
-                                                        uint32_t* __restrict__ state) {
+                                                        uint32_t* __restrict__ state, void* const* ptrs) {
+  if (ptrs) {  // batched launch: transform blockIdx.y
+    x = reinterpret_cast<const uint4*>(ptrs[blockIdx.y]);
+    state += 4u * blockIdx.y;
+  }
   uint32_t mx = 0;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -155,6 +162,97 @@ int choose_radices(int e, int* r) {
   return 3;
 }
 
+// A radix list the kernels accept: none for N <= 8; one pass of 2^4..2^11;
+// two or three passes of 2^4..2^11 each, symmetric (R_0 = R_{p-1}).
+bool valid_schedule(int e, const int* r, int np) {
+  if (e <= 3) return np == 0;
+  if (np < 1 || np > 3 || !r) return false;
+  int sum = 0;
+  for (int j = 0; j < np; ++j) {
+    if (r[j] < 4 || r[j] > 11) return false;
+    sum += r[j];
+  }
+  return sum == e && r[0] == r[np - 1];
+}
+
+// Every accepted schedule for N = 2^e (at most 1 + 1 + 8 of them).
+int schedule_candidates(int e, int (*r)[kMaxPasses], int* np) {
+  int k = 0;
+  if (e <= 3) {
+    np[k++] = 0;
+    return k;
+  }
+  if (e <= 11) {
+    r[k][0] = e;
+    np[k++] = 1;
+  }
+  if (e % 2 == 0 && e / 2 >= 4 && e / 2 <= 11) {
+    r[k][0] = r[k][1] = e / 2;
+    np[k++] = 2;
+  }
+  for (int a = 4; a <= 11; ++a) {
+    const int b = e - 2 * a;
+    if (b < 4 || b > 11) continue;
+    r[k][0] = r[k][2] = a;
+    r[k][1] = b;
+    np[k++] = 3;
+  }
+  return k;
+}
+
+// Fills the pass table of p (log2n, dtype and flags already set) for the
+// radix list r[0..np).
+void apply_schedule(efft_plan_s* p, const int* r, int np) {
+  const int e = p->log2n;
+  p->npasses = np;
+  p->small = (e >= 1 && e <= 3);
+  const int log2cta = (p->dtype == EFFT_C128) ? kLog2CtaC128 : kLog2CtaC64;
+  const size_t eb = (p->dtype == EFFT_C128) ? 16 : 8;
+  int rest = e;
+  for (int j = 0; j < kMaxPasses; ++j) p->pass[j] = Pass();
+  for (int j = 0; j < np; ++j) {
+    Pass& ps = p->pass[j];
+    ps.log2R = r[j];
+    rest -= r[j];
+    ps.log2s = rest;
+    ps.log2L = r[j] + rest;
+    int log2C = log2cta - r[j];
+    if (log2C > e - r[j]) log2C = e - r[j];
+    ps.log2C = log2C;
+    ps.grid = 1ull << (e - r[j] - log2C);
+    ps.threads = 1 << (r[j] + log2C - 4);
+    const size_t elems = 1ull << (r[j] + log2C);
+    ps.smem = (elems + elems / 16 + 1) * eb;
+    if (np == 1) ps.kind = SINGLE;
+    else if (j == 0) ps.kind = FIRST;
+    else if (j == np - 1) ps.kind = LAST;
+    else ps.kind = MID;
+  }
+  p->permute = (np >= 2) && !(p->flags & EFFT_FLAG_DIGIT_REVERSED_OUT);
+  p->perm_log2A = (np >= 2) ? r[0] : 0;
+  p->perm_log2B = (np == 3) ? r[1] : 0;
+}
+
+// Autotuned schedules per (device, log2 N, dtype).
+struct Tuned { int np; int r[kMaxPasses]; };
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int>, Tuned>* g_tuned = nullptr;  // leaked on purpose
+
+bool tuned_lookup(int dev, int e, int dtype, Tuned* t) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  if (!g_tuned) return false;
+  auto it = g_tuned->find(std::make_tuple(dev, e, dtype));
+  if (it == g_tuned->end()) return false;
+  *t = it->second;
+  return true;
+}
+
+void tuned_store(int dev, int e, int dtype, const Tuned& t) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  if (!g_tuned) g_tuned = new std::map<std::tuple<int, int, int>, Tuned>();
+  (*g_tuned)[std::make_tuple(dev, e, dtype)] = t;
+}
+
 template <class P, int KIND, int CTA>
 void set_smem_attr() {
   cudaFuncSetAttribute(efft_pass<P, KIND, CTA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -256,8 +354,16 @@ void prof_end(efft_plan_s* p, int rec, cudaStream_t st) {
 }
 
 // P: policy of the generic kernel; PFX: policy of the specialised kernels
+// Batch: ptrs (device array of `count` data pointers, or NULL for one
+// transform at `data`) and state words (16 bytes per transform).
+struct Batch {
+  void* const* ptrs;
+  unsigned count;
+  uint32_t* state;
+};
+
 template <class P, class PFX, int CTA>
-cudaError_t launch_pass(const efft_plan_s* p, const Pass& ps, void* data, cudaStream_t st) {
+cudaError_t launch_pass(const efft_plan_s* p, const Pass& ps, void* data, const Batch& bt, cudaStream_t st) {
   PassArgs a;
   a.log2R = ps.log2R;
   a.log2C = ps.log2C;
@@ -268,12 +374,13 @@ cudaError_t launch_pass(const efft_plan_s* p, const Pass& ps, void* data, cudaSt
   a.w2048 = p->w2048;
   a.tw_lo = p->tw_lo;
   a.tw_hi = p->tw_hi;
-  a.state = p->state;
+  a.state = bt.state;
+  a.ptrs = bt.ptrs;
   const uint32_t conj = (p->sign > 0) ? 1u : 0u;
   a.conj_in = (ps.kind == FIRST || ps.kind == SINGLE) ? conj : 0u;
   a.conj_out = (ps.kind == LAST || ps.kind == SINGLE) ? conj : 0u;
   a.out_shift = ((p->flags & EFFT_FLAG_NORMALIZE) && (ps.kind == LAST || ps.kind == SINGLE)) ? p->log2n : 0;
-  dim3 grid((unsigned)ps.grid), block(ps.threads);
+  dim3 grid((unsigned)ps.grid, bt.count), block(ps.threads);
   constexpr int LOG2CTA = (P::kElemBytes == 16) ? kLog2CtaC128 : kLog2CtaC64;
   if (ps.kind != SINGLE && ps.log2R >= 8 && ps.log2R <= 11 && ps.log2R + ps.log2C == LOG2CTA) {
     const bool ok = (P::kElemBytes == 16) ? fx_launch_df2(ps.kind, ps.log2R, grid, block, ps.smem, st, data, a)
@@ -317,14 +424,16 @@ const char* efft_strerror(int s) {
   }
 }
 
-int efft_plan_create(efft_plan_t* out, uint64_t n, int dtype, int sign, uint32_t flags) {
-  if (!out) return EFFT_ERR_INVALID_PTR;
-  *out = nullptr;
-  if (n == 0 || (n & (n - 1)) != 0 || n > (1ull << EFFT_MAX_LOG2N)) return EFFT_ERR_INVALID_SIZE;
-  if (dtype != EFFT_C64 && dtype != EFFT_C128) return EFFT_ERR_INVALID_DTYPE;
-  if (sign != -1 && sign != 1) return EFFT_ERR_INVALID_SIGN;
-  if (flags & ~EFFT_FLAG_ALL) return EFFT_ERR_INVALID_FLAGS;
+}  // extern "C"
 
+namespace {
+
+int autotune_impl(efft_plan_s* p, void* scratch, cudaStream_t st, int* cand_log2r, double* cand_ms, int cap,
+                  int* ncand);
+
+// Plan creation; r_explicit != NULL: the caller's schedule (already checked).
+int plan_create_impl(efft_plan_t* out, uint64_t n, int dtype, int sign, uint32_t flags, const int* r_explicit,
+                     int np_explicit) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) {
     cudaGetLastError();
@@ -343,34 +452,20 @@ int efft_plan_create(efft_plan_t* out, uint64_t n, int dtype, int sign, uint32_t
   p->flags = flags;
 
   const int e = p->log2n;
-  int r[kMaxPasses] = {0, 0, 0, 0};
-  p->npasses = choose_radices(e, r);
-  p->small = (e >= 1 && e <= 3);
-  const int log2cta = (dtype == EFFT_C128) ? kLog2CtaC128 : kLog2CtaC64;
   const size_t eb = (dtype == EFFT_C128) ? 16 : 8;
-  int rest = e;
-  for (int j = 0; j < p->npasses; ++j) {
-    Pass& ps = p->pass[j];
-    ps.log2R = r[j];
-    rest -= r[j];
-    ps.log2s = rest;
-    ps.log2L = r[j] + rest;
-    int log2C = log2cta - r[j];
-    if (log2C > e - r[j]) log2C = e - r[j];
-    ps.log2C = log2C;
-    ps.grid = 1ull << (e - r[j] - log2C);
-    ps.threads = 1 << (r[j] + log2C - 4);
-    const size_t elems = 1ull << (r[j] + log2C);
-    ps.smem = (elems + elems / 16 + 1) * eb;
-    if (p->npasses == 1) ps.kind = SINGLE;
-    else if (j == 0) ps.kind = FIRST;
-    else if (j == p->npasses - 1) ps.kind = LAST;
-    else ps.kind = MID;
-  }
-  p->permute = (p->npasses >= 2) && !(flags & EFFT_FLAG_DIGIT_REVERSED_OUT);
-  if (p->npasses >= 2) {
-    p->perm_log2A = r[0];
-    p->perm_log2B = (p->npasses == 3) ? r[1] : 0;
+  bool tune = false;
+  if (r_explicit) {
+    apply_schedule(p, r_explicit, np_explicit);
+  } else {
+    Tuned t;
+    if ((flags & EFFT_FLAG_AUTOTUNE) && tuned_lookup(dev, e, dtype, &t)) {
+      apply_schedule(p, t.r, t.np);
+    } else {
+      int r[kMaxPasses] = {0, 0, 0, 0};
+      const int np = choose_radices(e, r);
+      apply_schedule(p, r, np);
+      tune = (flags & EFFT_FLAG_AUTOTUNE) && e >= 4 && n * eb <= EFFT_AUTOTUNE_MAX_BYTES;
+    }
   }
   p->twB = (e + 1) / 2;
 
@@ -393,6 +488,19 @@ int efft_plan_create(efft_plan_t* out, uint64_t n, int dtype, int sign, uint32_t
   if (rc == EFFT_OK) rc = gen_table(p->tw_hi, nhi, nlo, e, st);
   if (rc == EFFT_OK && cudaMemsetAsync(p->state, 0, 16, st) != cudaSuccess) rc = EFFT_ERR_CUDA;
   if (rc == EFFT_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = EFFT_ERR_CUDA;
+  p->recs = new (std::nothrow) std::vector<efft_plan_s::Rec>();
+  p->pool = new (std::nothrow) std::vector<cudaEvent_t>();
+  if (rc == EFFT_OK && (!p->recs || !p->pool)) rc = EFFT_ERR_ALLOC;
+  if (rc == EFFT_OK && tune) {
+    // a temporary buffer; without room the table's schedule stays
+    void* scratch = nullptr;
+    if (cudaMalloc(&scratch, n * eb) == cudaSuccess) {
+      rc = autotune_impl(p, scratch, st, nullptr, nullptr, 0, nullptr);
+      cudaFree(scratch);
+    } else {
+      cudaGetLastError();
+    }
+  }
   if (st) cudaStreamDestroy(st);
   if (rc != EFFT_OK) {
     cudaGetLastError();
@@ -401,13 +509,6 @@ int efft_plan_create(efft_plan_t* out, uint64_t n, int dtype, int sign, uint32_t
     return rc;
   }
   p->table_bytes = (2048 + nlo + nhi) * sizeof(float4) + 16;
-  p->recs = new (std::nothrow) std::vector<efft_plan_s::Rec>();
-  p->pool = new (std::nothrow) std::vector<cudaEvent_t>();
-  if (!p->recs || !p->pool) {
-    free_plan_memory(p);
-    delete p;
-    return EFFT_ERR_ALLOC;
-  }
   p->magic = kMagic;
   {
     std::lock_guard<std::mutex> lk(g_mu);
@@ -416,6 +517,36 @@ int efft_plan_create(efft_plan_t* out, uint64_t n, int dtype, int sign, uint32_t
   }
   *out = p;
   return EFFT_OK;
+}
+
+int check_create_args(efft_plan_t* out, uint64_t n, int dtype, int sign) {
+  if (!out) return EFFT_ERR_INVALID_PTR;
+  *out = nullptr;
+  if (n == 0 || (n & (n - 1)) != 0 || n > (1ull << EFFT_MAX_LOG2N)) return EFFT_ERR_INVALID_SIZE;
+  if (dtype != EFFT_C64 && dtype != EFFT_C128) return EFFT_ERR_INVALID_DTYPE;
+  if (sign != -1 && sign != 1) return EFFT_ERR_INVALID_SIGN;
+  return EFFT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int efft_plan_create(efft_plan_t* out, uint64_t n, int dtype, int sign, uint32_t flags) {
+  int rc = check_create_args(out, n, dtype, sign);
+  if (rc != EFFT_OK) return rc;
+  if (flags & ~EFFT_FLAG_ALL) return EFFT_ERR_INVALID_FLAGS;
+  return plan_create_impl(out, n, dtype, sign, flags, nullptr, 0);
+}
+
+int efft_plan_create_with_radices(efft_plan_t* out, uint64_t n, int dtype, int sign, uint32_t flags,
+                                  const int* log2_radices, int npasses) {
+  int rc = check_create_args(out, n, dtype, sign);
+  if (rc != EFFT_OK) return rc;
+  if (flags & ~(EFFT_FLAG_ALL & ~EFFT_FLAG_AUTOTUNE)) return EFFT_ERR_INVALID_FLAGS;
+  if (!valid_schedule(ilog2_u64(n), log2_radices, npasses)) return EFFT_ERR_UNSUPPORTED;
+  static const int kNone[1] = {0};
+  return plan_create_impl(out, n, dtype, sign, flags, log2_radices ? log2_radices : kNone, npasses);
 }
 
 int efft_plan_destroy(efft_plan_t plan) {
@@ -468,16 +599,20 @@ static int check_buffer(const efft_plan_s* p, const void* data) {
   return EFFT_OK;
 }
 
-static int enqueue(efft_plan_s* p, void* data, cudaStream_t st) {
+// One transform at `data`, or bt.count transforms (bt.ptrs) of the plan's
+// size in the same launches.
+static int enqueue_batch(efft_plan_s* p, void* data, const Batch& bt, cudaStream_t st) {
   if (fault_injected("launch")) return EFFT_ERR_LAUNCH;
-  if (p->log2n == 0) return EFFT_OK;  // N = 1: the DFT is the identity
+  if (p->log2n == 0 || bt.count == 0) return EFFT_OK;  // N = 1: the DFT is the identity
   const bool c128 = (p->dtype == EFFT_C128);
   if (c128) {
-    if (cudaMemsetAsync(p->state, 0, 4, st) != cudaSuccess) return EFFT_ERR_LAUNCH;
+    if (cudaMemsetAsync(bt.state, 0, 16 * (size_t)bt.count, st) != cudaSuccess) return EFFT_ERR_LAUNCH;
     uint64_t blocks = (p->n + 1023) / 1024;
     if (blocks > 152 * 8) blocks = 152 * 8;
+    if (bt.ptrs && blocks * bt.count > 152 * 16) blocks = (152 * 16 + bt.count - 1) / bt.count;
     int rec = prof_begin(p, 0, st);
-    efft_range_scan<<<(unsigned)blocks, 256, 0, st>>>(reinterpret_cast<const uint4*>(data), p->n, p->state);
+    efft_range_scan<<<dim3((unsigned)blocks, bt.count), 256, 0, st>>>(reinterpret_cast<const uint4*>(data), p->n,
+                                                                   bt.state, bt.ptrs);
     prof_end(p, rec, st);
     if (cudaGetLastError() != cudaSuccess) return EFFT_ERR_LAUNCH;
   }
@@ -486,19 +621,20 @@ static int enqueue(efft_plan_s* p, void* data, cudaStream_t st) {
     std::memset(&a, 0, sizeof(a));
     a.log2N = p->log2n;
     a.w2048 = p->w2048;
-    a.state = p->state;
+    a.state = bt.state;
+    a.ptrs = bt.ptrs;
     a.conj_in = a.conj_out = (p->sign > 0) ? 1u : 0u;
     a.out_shift = (p->flags & EFFT_FLAG_NORMALIZE) ? p->log2n : 0;
     int rec = prof_begin(p, 6, st);
-    if (c128) efft_small<PolicyDF><<<1, 32, 0, st>>>(data, a);
-    else efft_small<PolicyF32><<<1, 32, 0, st>>>(data, a);
+    if (c128) efft_small<PolicyDF><<<dim3(1, bt.count), 32, 0, st>>>(data, a);
+    else efft_small<PolicyF32><<<dim3(1, bt.count), 32, 0, st>>>(data, a);
     prof_end(p, rec, st);
     return cudaGetLastError() == cudaSuccess ? EFFT_OK : EFFT_ERR_LAUNCH;
   }
   for (int j = 0; j < p->npasses; ++j) {
     int rec = prof_begin(p, 1 + j, st);
-    cudaError_t err = c128 ? launch_pass<PolicyDF, PolicyDF2, 1 << kLog2CtaC128>(p, p->pass[j], data, st)
-                           : launch_pass<PolicyF32, PolicyF32, 1 << kLog2CtaC64>(p, p->pass[j], data, st);
+    cudaError_t err = c128 ? launch_pass<PolicyDF, PolicyDF2, 1 << kLog2CtaC128>(p, p->pass[j], data, bt, st)
+                           : launch_pass<PolicyF32, PolicyF32, 1 << kLog2CtaC64>(p, p->pass[j], data, bt, st);
     prof_end(p, rec, st);
     if (err != cudaSuccess) return EFFT_ERR_LAUNCH;
   }
@@ -506,14 +642,23 @@ static int enqueue(efft_plan_s* p, void* data, cudaStream_t st) {
     const int la = p->perm_log2A, lb = p->perm_log2B;
     const int lt = la < 5 ? la : 5;
     const uint64_t nt = 1ull << (la - lt);
-    dim3 grid((unsigned)(nt * (nt + 1) / 2), 1u << lb);
+    dim3 grid((unsigned)(nt * (nt + 1) / 2), 1u << lb, bt.count);
     int rec = prof_begin(p, 5, st);
-    if (c128) efft_digit_swap<uint4><<<grid, 256, 0, st>>>(reinterpret_cast<uint4*>(data), la, lb, lt);
-    else efft_digit_swap<uint2><<<grid, 256, 0, st>>>(reinterpret_cast<uint2*>(data), la, lb, lt);
+    if (c128)
+      efft_digit_swap<uint4><<<grid, 256, 0, st>>>(reinterpret_cast<uint4*>(data), la, lb, lt,
+                                                    reinterpret_cast<uint4* const*>(bt.ptrs));
+    else
+      efft_digit_swap<uint2><<<grid, 256, 0, st>>>(reinterpret_cast<uint2*>(data), la, lb, lt,
+                                                    reinterpret_cast<uint2* const*>(bt.ptrs));
     prof_end(p, rec, st);
     if (cudaGetLastError() != cudaSuccess) return EFFT_ERR_LAUNCH;
   }
   return EFFT_OK;
+}
+
+static int enqueue(efft_plan_s* p, void* data, cudaStream_t st) {
+  const Batch one{nullptr, 1u, p->state};
+  return enqueue_batch(p, data, one, st);
 }
 
 int efft_execute(efft_plan_t plan, void* data, void* stream) {
@@ -673,6 +818,328 @@ int efft_plan_profile_read(efft_plan_t plan, double* ms, int* count, int cap, in
 }  // extern "C"
 
 // ---------------------------------------------------------------------------
+// Autotuner: the schedule scan of the paper's Sec. 5.2 (Figs. 6-7), over the
+// radix lists the kernels accept instead of (split depth, worker count).
+// ---------------------------------------------------------------------------
+namespace {
+
+int autotune_impl(efft_plan_s* p, void* scratch, cudaStream_t st, int* cand_log2r, double* cand_ms, int cap,
+                  int* ncand) {
+  int cr[16][kMaxPasses] = {};
+  int cnp[16] = {};
+  const int nc = schedule_candidates(p->log2n, cr, cnp);
+  if (ncand) *ncand = nc;
+  int prev_r[kMaxPasses] = {0, 0, 0, 0};
+  const int prev_np = p->npasses;
+  for (int j = 0; j < prev_np; ++j) prev_r[j] = p->pass[j].log2R;
+  const size_t bytes = p->n * ((p->dtype == EFFT_C128) ? 16 : 8);
+  const int reps = (p->n <= (1ull << 20)) ? 21 : (p->n <= (1ull << 26) ? 9 : 5);
+  const bool prof = p->profiling;
+  p->profiling = false;
+  std::vector<cudaEvent_t> ev(2 * reps, nullptr);
+  std::vector<float> t(reps, 0.f);
+  int rc = EFFT_OK;
+  for (auto& x : ev)
+    if (cudaEventCreate(&x) != cudaSuccess) {
+      rc = EFFT_ERR_CUDA;
+      break;
+    }
+  int best = -1;
+  double best_ms = 0.0;
+  for (int c = 0; rc == EFFT_OK && c < nc; ++c) {
+    apply_schedule(p, cr[c], cnp[c]);
+    for (int k = -2; rc == EFFT_OK && k < reps; ++k) {
+      // a fresh finite input each time (repeated unnormalised transforms
+      // would overflow); the fill is outside the timed interval
+      if (cudaMemsetAsync(scratch, 0x3F, bytes, st) != cudaSuccess) {
+        rc = EFFT_ERR_LAUNCH;
+        break;
+      }
+      if (k >= 0) cudaEventRecord(ev[2 * k], st);
+      rc = enqueue(p, scratch, st);
+      if (k >= 0) cudaEventRecord(ev[2 * k + 1], st);
+    }
+    if (rc != EFFT_OK) break;
+    if (cudaStreamSynchronize(st) != cudaSuccess) {
+      rc = EFFT_ERR_CUDA;
+      break;
+    }
+    for (int k = 0; k < reps; ++k)
+      if (cudaEventElapsedTime(&t[k], ev[2 * k], ev[2 * k + 1]) != cudaSuccess) rc = EFFT_ERR_CUDA;
+    if (rc != EFFT_OK) break;
+    std::nth_element(t.begin(), t.begin() + reps / 2, t.end());
+    const double ms = t[reps / 2];
+    if (cand_log2r && c < cap)
+      for (int j = 0; j < kMaxPasses; ++j) cand_log2r[kMaxPasses * c + j] = (j < cnp[c]) ? cr[c][j] : 0;
+    if (cand_ms && c < cap) cand_ms[c] = ms;
+    if (best < 0 || ms < best_ms) {
+      best = c;
+      best_ms = ms;
+    }
+  }
+  for (auto x : ev)
+    if (x) cudaEventDestroy(x);
+  p->profiling = prof;
+  if (rc != EFFT_OK || best < 0) {
+    cudaGetLastError();
+    apply_schedule(p, prev_r, prev_np);
+    return rc == EFFT_OK ? EFFT_ERR_CUDA : rc;
+  }
+  apply_schedule(p, cr[best], cnp[best]);
+  Tuned tu;
+  tu.np = cnp[best];
+  for (int j = 0; j < kMaxPasses; ++j) tu.r[j] = cr[best][j];
+  tuned_store(p->device, p->log2n, p->dtype, tu);
+  return EFFT_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Batches of mixed sizes behind one CUDA graph.
+// ---------------------------------------------------------------------------
+struct efft_batch_s {
+  uint32_t magic = 0;
+  int device = 0;
+  int count = 0;
+  std::vector<efft_plan_s*> plans;  // one per distinct size, largest first
+  std::vector<int> gstart;          // group g owns pointer slots [gstart[g], gstart[g+1])
+  std::vector<int> slot;            // transform i -> its pointer slot
+  std::vector<int> group;           // transform i -> its group
+  void** dptrs = nullptr;           // device: count pointers, by slot
+  uint32_t* state = nullptr;        // device: 16 bytes per slot
+  void** stage = nullptr;           // pinned host: EFFT_BATCH_INFLIGHT * count pointers
+  cudaEvent_t done[EFFT_BATCH_INFLIGHT] = {};
+  int next = 0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int kernels = 0;
+};
+
+namespace {
+
+constexpr uint32_t kBatchMagic = 0xEFF7BA7Cu;
+std::set<efft_batch_s*>* g_live_batches = nullptr;  // leaked on purpose, guarded by g_mu
+
+bool batch_is_live(efft_batch_s* b) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  return g_live_batches && g_live_batches->count(b) && b->magic == kBatchMagic;
+}
+
+void batch_free(efft_batch_s* b) {
+  for (int k = 0; k < EFFT_BATCH_INFLIGHT; ++k)
+    if (b->done[k]) cudaEventSynchronize(b->done[k]);
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  for (int k = 0; k < EFFT_BATCH_INFLIGHT; ++k)
+    if (b->done[k]) cudaEventDestroy(b->done[k]);
+  if (b->dptrs) cudaFree(b->dptrs);
+  if (b->state) cudaFree(b->state);
+  if (b->stage) cudaFreeHost(b->stage);
+  for (efft_plan_s* p : b->plans) efft_plan_destroy(p);
+  cudaGetLastError();
+  delete b;
+}
+
+// Records every group's launches into one graph: group 0 on the capture
+// stream, the others on forked side streams joined back at the end.
+int batch_capture(efft_batch_s* b) {
+  const int G = (int)b->plans.size();
+  cudaStream_t cs = nullptr;
+  std::vector<cudaStream_t> side(G, nullptr);
+  std::vector<cudaEvent_t> join(G, nullptr);
+  cudaEvent_t fork = nullptr;
+  int rc = EFFT_OK;
+  if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) != cudaSuccess)
+    rc = EFFT_ERR_CUDA;
+  for (int g = 1; rc == EFFT_OK && g < G; ++g)
+    if (cudaStreamCreateWithFlags(&side[g], cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&join[g], cudaEventDisableTiming) != cudaSuccess)
+      rc = EFFT_ERR_CUDA;
+  if (rc == EFFT_OK) {
+    if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      rc = EFFT_ERR_CUDA;
+    } else {
+      bool forked = (G == 1) || cudaEventRecord(fork, cs) == cudaSuccess;
+      if (!forked) rc = EFFT_ERR_CUDA;
+      for (int g = 1; g < G && forked; ++g)
+        if (cudaStreamWaitEvent(side[g], fork, 0) != cudaSuccess) rc = EFFT_ERR_CUDA;
+      for (int g = 0; g < G && rc == EFFT_OK && forked; ++g) {
+        const int s0 = b->gstart[g], cnt = b->gstart[g + 1] - s0;
+        const Batch bt{reinterpret_cast<void* const*>(b->dptrs + s0), (unsigned)cnt, b->state + 4 * (size_t)s0};
+        rc = enqueue_batch(b->plans[g], nullptr, bt, g == 0 ? cs : side[g]);
+      }
+      // join every forked stream, also after an error, so the capture ends cleanly
+      for (int g = 1; g < G && forked; ++g)
+        if (cudaEventRecord(join[g], side[g]) != cudaSuccess || cudaStreamWaitEvent(cs, join[g], 0) != cudaSuccess)
+          if (rc == EFFT_OK) rc = EFFT_ERR_CUDA;
+      cudaGraph_t graph = nullptr;
+      if (cudaStreamEndCapture(cs, &graph) != cudaSuccess && rc == EFFT_OK) rc = EFFT_ERR_CUDA;
+      b->graph = graph;
+    }
+  }
+  if (rc == EFFT_OK && cudaGraphInstantiate(&b->exec, b->graph, 0) != cudaSuccess) rc = EFFT_ERR_CUDA;
+  if (rc == EFFT_OK) {
+    size_t num = 0;
+    if (cudaGraphGetNodes(b->graph, nullptr, &num) == cudaSuccess && num > 0) {
+      std::vector<cudaGraphNode_t> nodes(num);
+      if (cudaGraphGetNodes(b->graph, nodes.data(), &num) == cudaSuccess)
+        for (size_t k = 0; k < num; ++k) {
+          cudaGraphNodeType ty;
+          if (cudaGraphNodeGetType(nodes[k], &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel) ++b->kernels;
+        }
+    }
+  }
+  for (int g = 1; g < G; ++g) {
+    if (side[g]) cudaStreamDestroy(side[g]);
+    if (join[g]) cudaEventDestroy(join[g]);
+  }
+  if (fork) cudaEventDestroy(fork);
+  if (cs) cudaStreamDestroy(cs);
+  if (rc != EFFT_OK) cudaGetLastError();
+  return rc;
+}
+
+}  // namespace
+
+extern "C" {
+
+int efft_plan_autotune(efft_plan_t plan, void* scratch, void* stream, int* cand_log2r, double* cand_ms, int cap,
+                       int* ncand) {
+  if (!plan_is_live(plan)) return EFFT_ERR_INVALID_PLAN;
+  DeviceGuard g(plan->device);
+  if (!g.ok) return EFFT_ERR_CUDA;
+  int rc = check_buffer(plan, scratch);
+  if (rc != EFFT_OK) return rc;
+  return autotune_impl(plan, scratch, reinterpret_cast<cudaStream_t>(stream), cand_log2r, cand_ms,
+                       cap < 0 ? 0 : cap, ncand);
+}
+
+int efft_batch_create(efft_batch_t* out, const uint64_t* sizes, int count, int dtype, int sign, uint32_t flags) {
+  if (!out) return EFFT_ERR_INVALID_PTR;
+  *out = nullptr;
+  if (!sizes) return EFFT_ERR_INVALID_PTR;
+  if (count < 1) return EFFT_ERR_INVALID_SIZE;
+  if (dtype != EFFT_C64 && dtype != EFFT_C128) return EFFT_ERR_INVALID_DTYPE;
+  if (sign != -1 && sign != 1) return EFFT_ERR_INVALID_SIGN;
+  if (flags & ~EFFT_FLAG_ALL) return EFFT_ERR_INVALID_FLAGS;
+  std::map<uint64_t, std::vector<int>, std::greater<uint64_t>> by_size;
+  for (int i = 0; i < count; ++i) {
+    const uint64_t n = sizes[i];
+    if (n == 0 || (n & (n - 1)) != 0 || n > (1ull << EFFT_MAX_LOG2N)) return EFFT_ERR_INVALID_SIZE;
+    by_size[n].push_back(i);
+  }
+  for (auto& kv : by_size)
+    if (kv.second.size() > 65535) return EFFT_ERR_INVALID_SIZE;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return EFFT_ERR_CUDA;
+  }
+  efft_batch_s* b = new (std::nothrow) efft_batch_s();
+  if (!b) return EFFT_ERR_ALLOC;
+  b->device = dev;
+  b->count = count;
+  b->slot.assign(count, 0);
+  b->group.assign(count, 0);
+  int rc = EFFT_OK;
+  int pos = 0;
+  for (auto& kv : by_size) {
+    const int g = (int)b->plans.size();
+    b->gstart.push_back(pos);
+    for (int i : kv.second) {
+      b->slot[i] = pos++;
+      b->group[i] = g;
+    }
+    efft_plan_t pl = nullptr;
+    rc = efft_plan_create(&pl, kv.first, dtype, sign, flags);
+    if (rc != EFFT_OK) break;
+    b->plans.push_back(pl);
+  }
+  b->gstart.push_back(count);
+  if (rc == EFFT_OK && (cudaMalloc(&b->dptrs, sizeof(void*) * count) != cudaSuccess ||
+                        cudaMalloc(&b->state, 16 * (size_t)count) != cudaSuccess ||
+                        cudaHostAlloc(&b->stage, sizeof(void*) * count * EFFT_BATCH_INFLIGHT,
+                                      cudaHostAllocDefault) != cudaSuccess))
+    rc = EFFT_ERR_ALLOC;
+  for (int k = 0; rc == EFFT_OK && k < EFFT_BATCH_INFLIGHT; ++k)
+    if (cudaEventCreateWithFlags(&b->done[k], cudaEventDisableTiming) != cudaSuccess) rc = EFFT_ERR_CUDA;
+  if (rc == EFFT_OK && cudaMemset(b->dptrs, 0, sizeof(void*) * count) != cudaSuccess) rc = EFFT_ERR_CUDA;
+  if (rc == EFFT_OK) rc = batch_capture(b);
+  if (rc != EFFT_OK) {
+    cudaGetLastError();
+    batch_free(b);
+    return rc;
+  }
+  b->magic = kBatchMagic;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_live_batches) g_live_batches = new std::set<efft_batch_s*>();
+    g_live_batches->insert(b);
+  }
+  *out = b;
+  return EFFT_OK;
+}
+
+int efft_batch_execute(efft_batch_t b, void* const* data, void* stream) {
+  if (!batch_is_live(b)) return EFFT_ERR_INVALID_PLAN;
+  if (!data) return EFFT_ERR_INVALID_PTR;
+  DeviceGuard g(b->device);
+  if (!g.ok) return EFFT_ERR_CUDA;
+  // every buffer valid, and no two overlapping (they are transformed concurrently)
+  std::vector<std::pair<uintptr_t, uintptr_t>> spans(b->count);
+  for (int i = 0; i < b->count; ++i) {
+    const efft_plan_s* p = b->plans[b->group[i]];
+    int rc = check_buffer(p, data[i]);
+    if (rc != EFFT_OK) return rc;
+    const uintptr_t a = reinterpret_cast<uintptr_t>(data[i]);
+    spans[i] = {a, a + p->n * ((p->dtype == EFFT_C128) ? 16 : 8)};
+  }
+  std::sort(spans.begin(), spans.end());
+  for (int i = 1; i < b->count; ++i)
+    if (spans[i].first < spans[i - 1].second) return EFFT_ERR_INVALID_PTR;
+  if (fault_injected("launch")) return EFFT_ERR_LAUNCH;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const int k = b->next;
+  if (cudaEventSynchronize(b->done[k]) != cudaSuccess) {  // staging slot k free again
+    cudaGetLastError();
+    return EFFT_ERR_CUDA;
+  }
+  void** stage = b->stage + (size_t)k * b->count;
+  for (int i = 0; i < b->count; ++i) stage[b->slot[i]] = data[i];
+  if (cudaMemcpyAsync(b->dptrs, stage, sizeof(void*) * b->count, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaGraphLaunch(b->exec, st) != cudaSuccess || cudaEventRecord(b->done[k], st) != cudaSuccess) {
+    cudaGetLastError();
+    return EFFT_ERR_LAUNCH;
+  }
+  b->next = (k + 1) % EFFT_BATCH_INFLIGHT;
+  return EFFT_OK;
+}
+
+int efft_batch_info(efft_batch_t b, int* ngroups, int* kernels) {
+  if (!batch_is_live(b)) return EFFT_ERR_INVALID_PLAN;
+  if (ngroups) *ngroups = (int)b->plans.size();
+  if (kernels) *kernels = b->kernels;
+  return EFFT_OK;
+}
+
+int efft_batch_destroy(efft_batch_t b) {
+  if (!b) return EFFT_OK;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_live_batches || !g_live_batches->count(b) || b->magic != kBatchMagic) return EFFT_ERR_INVALID_PLAN;
+    g_live_batches->erase(b);
+  }
+  b->magic = 0;
+  DeviceGuard g(b->device);
+  batch_free(b);
+  return EFFT_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
 // Internal helper for efft_execute_noalloc (efft_noalloc.cu): the same launch
 // sequence as efft_execute, for a plan description built on the stack whose
 // twiddle tables and state word live in caller-provided device memory.
@@ -694,34 +1161,7 @@ int efft_internal_run_in_scratch(void* scratch, size_t scratch_bytes, bool regen
   p.flags = flags;
   const int e = p.log2n;
   int r[kMaxPasses] = {0, 0, 0, 0};
-  p.npasses = choose_radices(e, r);
-  p.small = (e >= 1 && e <= 3);
-  const int log2cta = (dtype == EFFT_C128) ? kLog2CtaC128 : kLog2CtaC64;
-  const size_t eb = (dtype == EFFT_C128) ? 16 : 8;
-  int rest = e;
-  for (int j = 0; j < p.npasses; ++j) {
-    Pass& ps = p.pass[j];
-    ps.log2R = r[j];
-    rest -= r[j];
-    ps.log2s = rest;
-    ps.log2L = r[j] + rest;
-    int log2C = log2cta - r[j];
-    if (log2C > e - r[j]) log2C = e - r[j];
-    ps.log2C = log2C;
-    ps.grid = 1ull << (e - r[j] - log2C);
-    ps.threads = 1 << (r[j] + log2C - 4);
-    const size_t elems = 1ull << (r[j] + log2C);
-    ps.smem = (elems + elems / 16 + 1) * eb;
-    if (p.npasses == 1) ps.kind = SINGLE;
-    else if (j == 0) ps.kind = FIRST;
-    else if (j == p.npasses - 1) ps.kind = LAST;
-    else ps.kind = MID;
-  }
-  p.permute = (p.npasses >= 2) && !(flags & EFFT_FLAG_DIGIT_REVERSED_OUT);
-  if (p.npasses >= 2) {
-    p.perm_log2A = r[0];
-    p.perm_log2B = (p.npasses == 3) ? r[1] : 0;
-  }
+  apply_schedule(&p, r, choose_radices(e, r));
   p.twB = (e + 1) / 2;
   const uint64_t nlo = 1ull << p.twB, nhi = 1ull << (e - p.twB);
   const size_t state_off = (2048 + nlo + nhi) * sizeof(float4);

@@ -37,6 +37,8 @@ struct PassArgs {
   const float4* tw_lo;   // exp(-2*pi*i*t/N), t < 2^twB
   const float4* tw_hi;   // exp(-2*pi*i*(t << twB)/N), t < N >> twB
   const uint32_t* state; // state[0] = max biased binary64 exponent of the input
+  void* const* ptrs;     // non-null: batched launch, transform blockIdx.y has data
+                         // ptrs[blockIdx.y] and state word state + 4*blockIdx.y
   uint32_t conj_in;      // 1: conjugate the input (sign = +1 transforms)
   uint32_t conj_out;     // 1: conjugate the output
   int out_shift;         // output multiplied by 2^-out_shift (1/N normalisation)
@@ -231,6 +233,8 @@ template <class P, int KIND, int CTA_ELEMS>
 __global__ void __launch_bounds__(CTA_ELEMS / 16, 2)
 efft_pass(void* __restrict__ data, const PassArgs a) {
   typedef typename P::V V;
+  if (a.ptrs) data = a.ptrs[blockIdx.y];
+  const uint32_t* state = a.state + (a.ptrs ? 4u * blockIdx.y : 0u);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V* sm = reinterpret_cast<V*>(smem_raw);
 
@@ -251,7 +255,7 @@ efft_pass(void* __restrict__ data, const PassArgs a) {
   int D = 0, Dout = a.out_shift;
   bool nonfinite = false;
   if (P::kElemBytes == 16) {
-    uint32_t emax = __ldg(a.state);
+    uint32_t emax = __ldg(state);
     D = (int)emax - 127;
     Dout = D - a.out_shift;
     nonfinite = (emax >= 0x7FFu);
@@ -398,6 +402,8 @@ template <class P, int KIND, int LR, int LC>
 __global__ void __launch_bounds__(1 << (LR + LC - 4), 2)
 efft_pass_fx(void* __restrict__ data, const PassArgs a) {
   typedef typename P::V V;
+  if (a.ptrs) data = a.ptrs[blockIdx.y];
+  const uint32_t* state = a.state + (a.ptrs ? 4u * blockIdx.y : 0u);
   constexpr int R = 1 << LR, C = 1 << LC, TPC = R >> 4;
   constexpr int NFULL = LR / 4, REM = LR % 4, NST = NFULL + (REM ? 1 : 0);
   constexpr int NMID = NST - 2;  // radix-16 stages between the first and the last
@@ -424,7 +430,7 @@ efft_pass_fx(void* __restrict__ data, const PassArgs a) {
   int D = 0, Dout = a.out_shift;
   bool nonfinite = false;
   if (P::kElemBytes == 16) {
-    uint32_t emax = __ldg(a.state);
+    uint32_t emax = __ldg(state);
     D = (int)emax - 127;
     Dout = D - a.out_shift;
     nonfinite = (emax >= 0x7FFu);
@@ -523,11 +529,13 @@ template <class P>
 __global__ void efft_small(void* __restrict__ data, const PassArgs a) {
   typedef typename P::V V;
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  if (a.ptrs) data = a.ptrs[blockIdx.y];
+  const uint32_t* state = a.state + (a.ptrs ? 4u * blockIdx.y : 0u);
   const int N = 1 << a.log2N;
   int D = 0, Dout = a.out_shift;
   bool nonfinite = false;
   if (P::kElemBytes == 16) {
-    uint32_t emax = __ldg(a.state);
+    uint32_t emax = __ldg(state);
     D = (int)emax - 127;
     Dout = D - a.out_shift;
     nonfinite = (emax >= 0x7FFu);
@@ -553,7 +561,9 @@ __global__ void efft_small(void* __restrict__ data, const PassArgs a) {
 // T x T tiles, T = min(32, A); 256 threads.
 // ----------------------------------------------------------------------------
 template <typename E>
-__global__ void __launch_bounds__(256) efft_digit_swap(E* __restrict__ data, int log2A, int log2B, int log2T) {
+__global__ void __launch_bounds__(256) efft_digit_swap(E* __restrict__ data, int log2A, int log2B, int log2T,
+                                                       E* const* ptrs) {
+  if (ptrs) data = ptrs[blockIdx.z];  // batched launch: transform blockIdx.z
   __shared__ E t0[32][33];
   __shared__ E t1[32][33];
   const int T = 1 << log2T;

@@ -43,7 +43,7 @@ extern "C" int efft_execute_noalloc(void* data, uint64_t n, int dtype, int sign,
   if (n == 0 || (n & (n - 1)) != 0 || n > (1ull << EFFT_NOALLOC_MAX_LOG2N)) return EFFT_ERR_INVALID_SIZE;
   if (dtype != EFFT_C64 && dtype != EFFT_C128) return EFFT_ERR_INVALID_DTYPE;
   if (sign != -1 && sign != 1) return EFFT_ERR_INVALID_SIGN;
-  if (flags & ~EFFT_FLAG_ALL) return EFFT_ERR_INVALID_FLAGS;
+  if (flags & ~(EFFT_FLAG_DIGIT_REVERSED_OUT | EFFT_FLAG_NORMALIZE)) return EFFT_ERR_INVALID_FLAGS;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) {
     cudaGetLastError();

@@ -94,10 +94,9 @@ def test_missing_library_fails_loudly(tmp_path, monkeypatch):
         efft._lib()
 
 
-def test_radix_schedule_is_symmetric():
-    """The planner's three-pass table (read from the source) gives symmetric
-    radices, so the digit reversal is an involution; all radices 16..2048,
-    and at most 2^10 rows in the first pass below 2^32."""
+def _planner_choice():
+    """The planner's default schedule, with its three-pass table read from
+    the source."""
     src = open(os.path.join(ROOT, "paper_1409_5757_gb300", "csrc", "efft.cu")).read()
     body = src[src.index("static const int kA[34] = {") + len("static const int kA[34] = {"):]
     body = body[:body.index("};")]
@@ -112,6 +111,14 @@ def test_radix_schedule_is_symmetric():
         if e <= 22 and e % 2 == 0:
             return [e // 2, e // 2]
         return [kA[e], e - 2 * kA[e], kA[e]]
+    return choose
+
+
+def test_radix_schedule_is_symmetric():
+    """The planner's three-pass table gives symmetric radices, so the digit
+    reversal is an involution; all radices 16..2048, and at most 2^10 rows in
+    the first pass below 2^32."""
+    choose = _planner_choice()
     for e in range(4, 34):
         r = choose(e)
         assert sum(r) == e and r == r[::-1] and all(4 <= x <= 11 for x in r), (e, r)
@@ -133,3 +140,73 @@ def test_arith_constants_match_mpmath():
         hi, lo = np.float32(float(m.group(1))), np.float32(float(m.group(2)))
         assert hi == np.float32(float(v))
         assert lo == np.float32(float(v - mpmath.mpf(float(hi))))
+
+
+def test_schedule_and_batch_argument_errors_before_cuda(libs):
+    import paper_1409_5757_gb300 as efft
+    L = efft._lib()
+    h = ctypes.c_void_p()
+
+    def radices(*r):
+        return (ctypes.c_int * max(len(r), 1))(*r), len(r)
+
+    def create(n, r, flags=0):
+        arr, np_ = radices(*r)
+        return L.efft_plan_create_with_radices(ctypes.byref(h), n, 1, -1, flags, arr, np_)
+    assert create(1 << 12, [6, 5]) == 9             # sum != log2 N
+    assert create(1 << 11, [6, 5]) == 9             # not symmetric
+    assert create(1 << 12, [12]) == 9               # radix above 2^11
+    assert create(1 << 12, [3, 6, 3]) == 9          # radix below 2^4
+    assert create(1 << 16, [4, 4, 4, 4]) == 9       # four passes
+    assert create(1 << 4, []) == 9                  # N > 8 needs a pass
+    assert create(1 << 3, [3]) == 9                 # N <= 8: direct sums only
+    assert create(1 << 12, [6, 6], flags=0x4) == 12  # autotune with an explicit schedule
+    assert create(12, [6, 6]) == 1
+    assert L.efft_plan_create_with_radices(None, 1 << 12, 1, -1, 0, radices(6, 6)[0], 2) == 4
+    assert h.value is None
+
+    sizes = (ctypes.c_uint64 * 3)(1 << 10, 1 << 12, 1 << 10)
+    assert L.efft_batch_create(None, sizes, 3, 0, -1, 0) == 4
+    assert L.efft_batch_create(ctypes.byref(h), None, 3, 0, -1, 0) == 4
+    assert L.efft_batch_create(ctypes.byref(h), sizes, 0, 0, -1, 0) == 1
+    assert L.efft_batch_create(ctypes.byref(h), sizes, 3, 2, -1, 0) == 2
+    assert L.efft_batch_create(ctypes.byref(h), sizes, 3, 0, 0, 0) == 3
+    assert L.efft_batch_create(ctypes.byref(h), sizes, 3, 0, -1, 0x80) == 12
+    bad = (ctypes.c_uint64 * 2)(1 << 10, 3 << 10)
+    assert L.efft_batch_create(ctypes.byref(h), bad, 2, 0, -1, 0) == 1
+    big = (ctypes.c_uint64 * 1)(1 << 34)
+    assert L.efft_batch_create(ctypes.byref(h), big, 1, 0, -1, 0) == 1
+    assert h.value is None
+
+
+def test_batch_and_autotune_handle_checks(libs):
+    import paper_1409_5757_gb300 as efft
+    L = efft._lib()
+    bogus = ctypes.create_string_buffer(256)
+    bp = ctypes.cast(bogus, ctypes.c_void_p)
+    assert L.efft_batch_destroy(None) == 0
+    assert L.efft_batch_destroy(bp) == 10
+    assert L.efft_batch_execute(None, None, None) == 10
+    assert L.efft_batch_execute(bp, None, None) == 10
+    assert L.efft_batch_info(None, None, None) == 10
+    assert L.efft_plan_autotune(None, None, None, None, None, 0, None) == 10
+    assert L.efft_plan_autotune(bp, None, None, None, None, 0, None) == 10
+
+
+def test_schedule_candidates_are_valid():
+    """The accepted schedules of every size: the planner's own choice is one
+    of them, and every one sums to log2 N, is symmetric and uses radices
+    2^4..2^11."""
+    import sys
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from parity_util import schedule_candidates
+    for e in range(0, 34):
+        cands = schedule_candidates(e)
+        if e <= 3:
+            assert cands == [[]]
+            continue
+        assert cands, e
+        for r in cands:
+            assert sum(r) == e and r == r[::-1] and all(4 <= v <= 11 for v in r), (e, r)
+        assert len(cands) <= 10
+        assert _planner_choice()(e) in cands, e

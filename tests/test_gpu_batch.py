@@ -1,0 +1,258 @@
+"""Explicit radix schedules, the autotuner and batched transforms of mixed
+sizes (one CUDA graph launch) against the CPU oracle.
+
+A batch runs the same kernels with the same schedule as single plans, so
+its results must be bit-identical to theirs; the single-plan path is in turn
+checked against the oracle here and in test_gpu_parity.py."""
+import numpy as np
+import pytest
+
+import oracle
+from parity_util import TOL, check, host_input, schedule_candidates
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def _code(name):
+    import paper_1409_5757_gb300 as efft
+    return efft.EFFT_C128 if name == "c128" else efft.EFFT_C64
+
+
+def _np(name):
+    return np.complex128 if name == "c128" else np.complex64
+
+
+@pytest.mark.parametrize("name", ["c128", "c64"])
+@pytest.mark.parametrize("e", list(range(0, 25)))
+def test_every_schedule_matches_oracle(orc, name, e):
+    """Every accepted radix schedule, through efft_plan_create_with_radices."""
+    import paper_1409_5757_gb300 as efft
+    N = 1 << e
+    x = host_input(orc, name, N, seed=3000 + e)
+    X = orc.dft(x, -1)
+    for r in schedule_candidates(e):
+        plan = efft.Plan(N, _code(name), -1, 0, radices=r)
+        assert plan.radices() == r
+        t = torch.from_numpy(x.astype(_np(name))).cuda()
+        plan.execute(t.data_ptr(), torch.cuda.current_stream().cuda_stream)
+        check(t.cpu().numpy().astype(np.complex128), X, name, N, f"radices {r}")
+        plan.destroy()
+
+
+@pytest.mark.parametrize("name", ["c128", "c64"])
+@pytest.mark.parametrize("e", [13, 20])
+def test_every_schedule_inverse_normalised(orc, name, e):
+    import paper_1409_5757_gb300 as efft
+    N = 1 << e
+    x = host_input(orc, name, N, seed=17)
+    X = orc.dft(x, +1) / N
+    for r in schedule_candidates(e):
+        t = torch.from_numpy(x.astype(_np(name))).cuda()
+        efft.Plan(N, _code(name), 1, efft.EFFT_FLAG_NORMALIZE, radices=r).execute(
+            t.data_ptr(), torch.cuda.current_stream().cuda_stream)
+        check(t.cpu().numpy().astype(np.complex128), X, name, N, f"radices {r}")
+
+
+@pytest.mark.parametrize("name", ["c128", "c64"])
+@pytest.mark.parametrize("e", [4, 12, 19, 24])
+def test_autotune_scans_every_candidate(orc, name, e):
+    import paper_1409_5757_gb300 as efft
+    N = 1 << e
+    plan = efft.Plan(N, _code(name), -1)
+    scratch = torch.empty(N, dtype=torch.complex128 if name == "c128" else torch.complex64, device="cuda")
+    res = plan.autotune(scratch.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    assert [r for r, _ in res] == schedule_candidates(e)
+    assert all(ms > 0 for _, ms in res)
+    best = min(res, key=lambda t: t[1])[0]
+    assert plan.radices() == best
+    # the tuned plan still computes the DFT
+    x = host_input(orc, name, N, seed=55)
+    t = torch.from_numpy(x.astype(_np(name))).cuda()
+    plan.execute(t.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    check(t.cpu().numpy().astype(np.complex128), orc.dft(x, -1), name, N, "autotuned")
+    # later plans with the flag reuse the cached choice
+    assert efft.Plan(N, _code(name), 1, efft.EFFT_FLAG_AUTOTUNE).radices() == best
+
+
+@pytest.mark.parametrize("name", ["c128", "c64"])
+def test_autotune_flag_at_creation(orc, name):
+    import paper_1409_5757_gb300 as efft
+    N = 1 << 18
+    plan = efft.Plan(N, _code(name), -1, efft.EFFT_FLAG_AUTOTUNE)
+    assert plan.radices() in schedule_candidates(18)
+    x = host_input(orc, name, N, seed=8)
+    t = torch.from_numpy(x.astype(_np(name))).cuda()
+    plan.execute(t.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    check(t.cpu().numpy().astype(np.complex128), orc.dft(x, -1), name, N, "autotune flag")
+
+
+def _batch_inputs(orc, name, es, seed):
+    xs = [host_input(orc, name, 1 << e, seed + i) for i, e in enumerate(es)]
+    ts = [torch.from_numpy(x.astype(_np(name))).cuda() for x in xs]
+    return xs, ts
+
+
+@pytest.mark.parametrize("name", ["c128", "c64"])
+@pytest.mark.parametrize("sign,flags", [(-1, 0), (1, 0x2), (-1, 0x1)])
+def test_batch_mixed_sizes(orc, name, sign, flags):
+    """Sizes 2^0..2^20 with repeats, in shuffled order: each result equals the
+    single-plan result bit for bit, and the oracle within tolerance."""
+    import paper_1409_5757_gb300 as efft
+    rng = np.random.default_rng(21)
+    es = list(range(0, 21)) + [12, 12, 3, 16, 16, 16, 20, 7, 0]
+    rng.shuffle(es)
+    xs, ts = _batch_inputs(orc, name, es, 400)
+    refs = [t.clone() for t in ts]
+    b = efft.Batch([t.numel() for t in ts], _code(name), sign, flags)
+    info = b.info()
+    assert info["groups"] == len(set(es))
+    assert info["kernels"] > 0
+    b.execute([t.data_ptr() for t in ts], torch.cuda.current_stream().cuda_stream)
+    for r in refs:
+        efft.fft_(r, sign, flags)
+    torch.cuda.synchronize()
+    for e, x, t, r in zip(es, xs, ts, refs):
+        assert torch.equal(t, r), f"batch differs from the single plan at N=2^{e}"
+        if not (flags & 0x1):
+            want = orc.dft(x, sign) / ((1 << e) if flags & 0x2 else 1)
+            check(t.cpu().numpy().astype(np.complex128), want, name, 1 << e, "batch")
+    b.destroy()
+
+
+@pytest.mark.parametrize("name", ["c128", "c64"])
+def test_batch_reexecute_new_buffers(orc, name):
+    """More executes back to back than the staging ring holds, each on other
+    buffers: the device pointer array follows every call."""
+    import paper_1409_5757_gb300 as efft
+    es = [14, 9, 14, 17, 3, 12]
+    b = efft.Batch([1 << e for e in es], _code(name), -1)
+    rounds = []
+    for k in range(2 * efft.EFFT_BATCH_INFLIGHT + 1):
+        xs, ts = _batch_inputs(orc, name, es, 1000 + 10 * k)
+        b.execute([t.data_ptr() for t in ts], torch.cuda.current_stream().cuda_stream)
+        rounds.append((xs, ts))
+    torch.cuda.synchronize()
+    for xs, ts in rounds:
+        for e, x, t in zip(es, xs, ts):
+            check(t.cpu().numpy().astype(np.complex128), orc.dft(x, -1), name, 1 << e, "re-execute")
+
+
+def test_batch_argument_errors():
+    import paper_1409_5757_gb300 as efft
+    base = torch.zeros(3 << 12, dtype=torch.complex64, device="cuda")
+    b = efft.Batch([1 << 12, 1 << 12], efft.EFFT_C64, -1)
+    s = torch.cuda.current_stream().cuda_stream
+    with pytest.raises(ValueError):
+        b.execute([base.data_ptr()], s)
+    with pytest.raises(efft.EfftError) as ei:  # overlapping buffers
+        b.execute([base.data_ptr(), base.data_ptr() + 8 * 100], s)
+    assert ei.value.status == 4
+    with pytest.raises(efft.EfftError) as ei:  # misaligned
+        b.execute([base.data_ptr(), base.data_ptr() + (1 << 15) + 4], s)
+    assert ei.value.status == 5
+    with pytest.raises(efft.EfftError) as ei:  # host memory
+        h = torch.zeros(1 << 12, dtype=torch.complex64)
+        b.execute([base.data_ptr(), h.data_ptr()], s)
+    assert ei.value.status == 4
+    b.execute([base.data_ptr(), base.data_ptr() + (1 << 15)], s)  # adjacent is fine
+    torch.cuda.synchronize()
+    h = b._h
+    b.destroy()
+    assert efft._lib().efft_batch_destroy(h) == 10
+
+
+@pytest.mark.parametrize("name", ["c128", "c64"])
+def test_batch_fault_injection(monkeypatch, name):
+    import paper_1409_5757_gb300 as efft
+    t = torch.zeros(1 << 10, dtype=torch.complex128 if name == "c128" else torch.complex64, device="cuda")
+    b = efft.Batch([1 << 10], _code(name), -1)
+    monkeypatch.setenv("EFFT_FAULT_INJECT", "launch")
+    with pytest.raises(efft.EfftError) as ei:
+        b.execute([t.data_ptr()], 0)
+    assert ei.value.status == 7
+    with pytest.raises(efft.EfftError) as ei:
+        efft.Batch([1 << 11, 1 << 10], _code(name), -1)
+    assert ei.value.status == 7
+    monkeypatch.setenv("EFFT_FAULT_INJECT", "alloc")
+    with pytest.raises(efft.EfftError) as ei:
+        efft.Batch([1 << 9], _code(name), -1)
+    assert ei.value.status == 6
+    monkeypatch.delenv("EFFT_FAULT_INJECT")
+    b.execute([t.data_ptr()], 0)
+    torch.cuda.synchronize()
+
+
+def test_batch_of_256_uneven_c64(orc):
+    """256 complex64 transforms, N = 2^e with e uniform in {12..24} (seed 5):
+    bit-identical to single plans for all, the oracle for the smallest and
+    largest of each size class sampled."""
+    import paper_1409_5757_gb300 as efft
+    from paper_1409_5757_gb300 import inputs
+    es = np.random.default_rng(5).integers(12, 25, 256)
+    ts = [torch.empty(1 << int(e), dtype=torch.complex64, device="cuda") for e in es]
+    for i, t in enumerate(ts):
+        inputs.fill_uniform(t, 5000 + i)
+    refs = [t.clone() for t in ts]
+    efft.fft_batch_(ts)
+    for r in refs:
+        efft.fft_(r)
+    torch.cuda.synchronize()
+    for e, t, r in zip(es, ts, refs):
+        assert torch.equal(t, r), f"N=2^{e}"
+    for i in (int(np.argmin(es)), int(np.argmax(es))):
+        N = 1 << int(es[i])
+        x = orc.gen_uniform(5000 + i, N).astype(np.complex64).astype(np.complex128)
+        check(ts[i].cpu().numpy().astype(np.complex128), orc.dft(x, -1), "c64", N, "256-batch")
+
+
+@pytest.mark.parametrize("name", ["c128", "c64"])
+def test_batch_grad_matches_closed_form(orc, name):
+    """L = sum_t sum_k |w_tk X_tk|^2 over a batch of sizes 2^4..2^14:
+    grad x_t = 2 F^H(|w_t|^2 X_t) per transform."""
+    from paper_1409_5757_gb300.autograd import dft_batch
+    es = [4, 9, 14, 9, 11]
+    g = np.random.default_rng(99)
+    xs = [host_input(orc, name, 1 << e, 70 + i) for i, e in enumerate(es)]
+    ws = [g.uniform(0, 1, 1 << e) for e in es]
+    rdt = torch.float64 if name == "c128" else torch.float32
+    xt = [torch.from_numpy(x.astype(_np(name))).cuda().requires_grad_(True) for x in xs]
+    Xs = dft_batch(xt, -1)
+    L = sum(torch.sum(torch.from_numpy(w ** 2).to(rdt).cuda() * (X.real ** 2 + X.imag ** 2)) for w, X in zip(ws, Xs))
+    L.backward()
+    for e, x, w, t in zip(es, xs, ws, xt):
+        ref = 2 * orc.dft(w ** 2 * orc.dft(x, -1), +1)
+        assert oracle.rel_l2(t.grad.cpu().numpy().astype(np.complex128), ref) <= TOL[name] * 2 * e
+
+
+def test_batch_grad_finite_differences(orc):
+    from paper_1409_5757_gb300.autograd import dft_batch
+    es = [6, 10]
+    xs = [orc.gen_uniform(90 + i, 1 << e) for i, e in enumerate(es)]
+    w2 = [torch.from_numpy(np.random.default_rng(e).uniform(0, 1, 1 << e) ** 2).cuda() for e in es]
+
+    def loss(ts):
+        return sum(torch.sum(w * (X.real ** 2 + X.imag ** 2)) for w, X in zip(w2, dft_batch(ts, 1)))
+
+    xt = [torch.from_numpy(x.copy()).cuda().requires_grad_(True) for x in xs]
+    loss(xt).backward()
+    h = 1e-3
+    for ti, j in ((0, 0), (0, 63), (1, 5), (1, 1023)):
+        for unit in (1.0, 1j):
+            xp = [torch.from_numpy(x.copy()).cuda() for x in xs]
+            xm = [torch.from_numpy(x.copy()).cuda() for x in xs]
+            xp[ti][j] += unit * h
+            xm[ti][j] -= unit * h
+            with torch.no_grad():
+                d = (loss(xp) - loss(xm)).item() / (2 * h)
+            gj = xt[ti].grad[j].item()
+            want = gj.real if unit == 1.0 else gj.imag
+            assert abs(d - want) <= 1e-7 * max(1.0, abs(want)), (ti, j, unit, d, want)
