@@ -83,10 +83,12 @@ constexpr uint32_t kMagic = 0xEFF71409u;
 constexpr int kLog2CtaC128 = 12;  // 4096 complex128 elements per CTA (64 KiB)
 constexpr int kLog2CtaC64 = 13;   // 8192 complex64 elements per CTA (64 KiB)
 constexpr int kMaxPasses = 4;
+constexpr int kWideMinLog2N = 28;  // complex128 first passes on 8192-element tiles from 2^28
 constexpr size_t kCopyChunk = size_t(1) << 30;  // host copies of the streaming entry point
 
 struct Pass {
   int log2R, log2s, log2L, log2C, kind;
+  bool wide;  // complex128 first pass on 8192-element tiles
   uint64_t grid;
   int threads;
   size_t smem;
@@ -216,17 +218,20 @@ void apply_schedule(efft_plan_s* p, const int* r, int np) {
     rest -= r[j];
     ps.log2s = rest;
     ps.log2L = r[j] + rest;
-    int log2C = log2cta - r[j];
+    if (np == 1) ps.kind = SINGLE;
+    else if (j == 0) ps.kind = FIRST;
+    else if (j == np - 1) ps.kind = LAST;
+    else ps.kind = MID;
+    // the first pass of a large complex128 array reads rows 2^(e-R) elements
+    // apart, each in its own page; wider tiles move twice the bytes per row
+    ps.wide = (p->dtype == EFFT_C128 && ps.kind == FIRST && (r[j] == 10 || r[j] == 11) && e >= kWideMinLog2N);
+    int log2C = (ps.wide ? kLog2CtaWide : log2cta) - r[j];
     if (log2C > e - r[j]) log2C = e - r[j];
     ps.log2C = log2C;
     ps.grid = 1ull << (e - r[j] - log2C);
     ps.threads = 1 << (r[j] + log2C - 4);
     const size_t elems = 1ull << (r[j] + log2C);
     ps.smem = (elems + elems / 16 + 1) * eb;
-    if (np == 1) ps.kind = SINGLE;
-    else if (j == 0) ps.kind = FIRST;
-    else if (j == np - 1) ps.kind = LAST;
-    else ps.kind = MID;
   }
   p->permute = (np >= 2) && !(p->flags & EFFT_FLAG_DIGIT_REVERSED_OUT);
   p->perm_log2A = (np >= 2) ? r[0] : 0;
@@ -365,6 +370,7 @@ struct Batch {
 template <class P, class PFX, int CTA>
 cudaError_t launch_pass(const efft_plan_s* p, const Pass& ps, void* data, const Batch& bt, cudaStream_t st) {
   PassArgs a;
+  std::memset(&a, 0, sizeof(a));
   a.log2R = ps.log2R;
   a.log2C = ps.log2C;
   a.log2s = ps.log2s;
@@ -382,6 +388,10 @@ cudaError_t launch_pass(const efft_plan_s* p, const Pass& ps, void* data, const 
   a.out_shift = ((p->flags & EFFT_FLAG_NORMALIZE) && (ps.kind == LAST || ps.kind == SINGLE)) ? p->log2n : 0;
   dim3 grid((unsigned)ps.grid, bt.count), block(ps.threads);
   constexpr int LOG2CTA = (P::kElemBytes == 16) ? kLog2CtaC128 : kLog2CtaC64;
+  if (ps.wide) {
+    if (fx_launch_df2_wide(ps.log2R, grid, block, ps.smem, st, data, a)) return cudaGetLastError();
+    return cudaErrorInvalidConfiguration;
+  }
   if (ps.kind != SINGLE && ps.log2R >= 8 && ps.log2R <= 11 && ps.log2R + ps.log2C == LOG2CTA) {
     const bool ok = (P::kElemBytes == 16) ? fx_launch_df2(ps.kind, ps.log2R, grid, block, ps.smem, st, data, a)
                                           : fx_launch_f32(ps.kind, ps.log2R, grid, block, ps.smem, st, data, a);

@@ -33,6 +33,17 @@ bool launch(int log2R, dim3 grid, dim3 block, size_t smem, cudaStream_t st, void
   }
 }
 
+void attrs_wide(cudaError_t& err) {
+  const int bytes = (int)(((1 << kLog2CtaWide) + (1 << kLog2CtaWide) / 16 + 1) * PolicyDF2::kElemBytes);
+  cudaError_t e[2] = {
+      cudaFuncSetAttribute(efft_pass_fx<PolicyDF2, FIRST, 10, kLog2CtaWide - 10, 1>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, bytes),
+      cudaFuncSetAttribute(efft_pass_fx<PolicyDF2, FIRST, 11, kLog2CtaWide - 11, 1>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)};
+  for (cudaError_t x : e)
+    if (x != cudaSuccess && err == cudaSuccess) err = x;
+}
+
 }  // namespace
 
 cudaError_t fx_set_attrs_df2() {
@@ -40,7 +51,21 @@ cudaError_t fx_set_attrs_df2() {
   attrs<FIRST>(err);
   attrs<MID>(err);
   attrs<LAST>(err);
+  attrs_wide(err);
   return err;
+}
+
+bool fx_launch_df2_wide(int log2R, dim3 grid, dim3 block, size_t smem, cudaStream_t st, void* data,
+                        const PassArgs& a) {
+  switch (log2R) {
+    case 10:
+      efft_pass_fx<PolicyDF2, FIRST, 10, kLog2CtaWide - 10, 1><<<grid, block, smem, st>>>(data, a);
+      return true;
+    case 11:
+      efft_pass_fx<PolicyDF2, FIRST, 11, kLog2CtaWide - 11, 1><<<grid, block, smem, st>>>(data, a);
+      return true;
+    default: return false;
+  }
 }
 
 bool fx_launch_df2(int kind, int log2R, dim3 grid, dim3 block, size_t smem, cudaStream_t st, void* data,

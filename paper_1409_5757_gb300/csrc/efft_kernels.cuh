@@ -398,24 +398,37 @@ __device__ __forceinline__ void dif_groups(typename P::V* v) {
   for (int g = 0; g < 16; g += (1 << LOG)) dif_regs<P, LOG>(v + g);
 }
 
-template <class P, int KIND, int LR, int LC>
-__global__ void __launch_bounds__(1 << (LR + LC - 4), 2)
+// The specialised pass kernel (R = 2^LR rows, C = 2^LC columns per CTA,
+// MINB CTAs per SM); grid.y selects the transform of a batched launch.
+template <class P, int KIND, int LR, int LC, int MINB = 2>
+__global__ void __launch_bounds__(1 << (LR + LC - 4), MINB)
 efft_pass_fx(void* __restrict__ data, const PassArgs a) {
   typedef typename P::V V;
   if (a.ptrs) data = a.ptrs[blockIdx.y];
   const uint32_t* state = a.state + (a.ptrs ? 4u * blockIdx.y : 0u);
-  constexpr int R = 1 << LR, C = 1 << LC, TPC = R >> 4;
+  constexpr int R = 1 << LR, C = 1 << LC, TPC = R >> 4, NT = (R * C) / 16;
   constexpr int NFULL = LR / 4, REM = LR % 4, NST = NFULL + (REM ? 1 : 0);
   constexpr int NMID = NST - 2;  // radix-16 stages between the first and the last
   constexpr bool STRIDED = (KIND == FIRST || KIND == MID);
+  // The last pass reads whole columns (C blocks of R contiguous elements):
+  // there t runs fastest across the threads so that global loads coalesce,
+  // and shared memory is column-major, raw index c*R + p.  The strided
+  // passes read C adjacent columns per row: c runs fastest, raw index
+  // p*C + c.  Either way slot = raw + raw/16 (one pad slot per 16).
+  constexpr bool CM = (KIND == LAST);
+  constexpr int PS = CM ? 1 : C;  // raw step of one position p
   static_assert(LR >= 5 && LR <= 12, "radix range");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V* sm = reinterpret_cast<V*>(smem_raw);
   __shared__ typename P::TW vtw[STRIDED ? 16 * C : 1];
+  auto slot = [](int p, int col) {
+    const int raw = CM ? (col << LR) + p : (p << LC) + col;
+    return raw + (raw >> 4);
+  };
 
   const int tid = threadIdx.x;
-  const int c = tid & (C - 1);
-  const int t = tid >> LC;
+  const int c = CM ? (tid >> (LR - 4)) : (tid & (C - 1));
+  const int t = CM ? (tid & (TPC - 1)) : (tid >> LC);
   const uint64_t jcol = (uint64_t)blockIdx.x * C + c;
   uint64_t m = 0, colbase, step;
   if (STRIDED) {
@@ -463,9 +476,9 @@ efft_pass_fx(void* __restrict__ data, const PassArgs a) {
 #pragma unroll
     for (int u = 1; u < 16; ++u)
       v[u] = P::mul_tw(v[u], P::int_tw(a.w2048, nullptr, (uint32_t)(t * bitrev_c(u, 4)) << (11 - LR)));
-    const int sb = smem_slot(t, c, LC);
+    const int sb = slot(t, c);
 #pragma unroll
-    for (int u = 0; u < 16; ++u) sm[sb + pad_off(bitrev_c(u, 4) * TPC * C)] = v[u];
+    for (int u = 0; u < 16; ++u) sm[sb + pad_off(bitrev_c(u, 4) * TPC * PS)] = v[u];
   }
   __syncthreads();
 
@@ -475,8 +488,8 @@ efft_pass_fx(void* __restrict__ data, const PassArgs a) {
     const int log2l = LR - 4 * st;      // sub-block length
     const int log2g = log2l - 4;        // groups per sub-block
     const int b = t >> log2g, i = t & ((1 << log2g) - 1);
-    const int sb = smem_slot((b << log2l) + i, c, LC);
-    const int gstep = (1 << log2g) * C;  // raw step between group members
+    const int sb = slot((b << log2l) + i, c);
+    const int gstep = (1 << log2g) * PS;  // raw step between group members
 #pragma unroll
     for (int j = 0; j < 16; ++j) v[j] = sm[sb + pad_off(j * gstep)];
     dif_regs<P, 4>(v);
@@ -491,9 +504,9 @@ efft_pass_fx(void* __restrict__ data, const PassArgs a) {
 
   // ---- last stage: the thread's 16 contiguous positions 16t .. 16t+15 ----
   {
-    const int sb = smem_slot(t << 4, c, LC);
+    const int sb = slot(t << 4, c);
 #pragma unroll
-    for (int j = 0; j < 16; ++j) v[j] = sm[sb + pad_off(j * C)];
+    for (int j = 0; j < 16; ++j) v[j] = sm[sb + pad_off(j * PS)];
     if (REM == 0) dif_regs<P, 4>(v);
     else dif_groups<P, (REM == 0 ? 4 : REM)>(v);
   }
@@ -510,14 +523,14 @@ efft_pass_fx(void* __restrict__ data, const PassArgs a) {
 #pragma unroll
     for (int u = 0; u < 16; ++u) {
       const int k = kt | digit_rev_c(last_pos_c(u, REM), LR);
-      sm[smem_slot(k, c, LC)] = v[u];
+      sm[slot(k, c)] = v[u];
     }
     __syncthreads();
     const uint64_t tile0 = (uint64_t)blockIdx.x * (R * C);
 #pragma unroll 4
-    for (int e = tid; e < R * C; e += (R * C) / 16) {
+    for (int e = tid; e < R * C; e += NT) {
       const int cc = e >> LR, k = e & (R - 1);
-      Mem<P, KIND>::store(data, tile0 + (uint64_t)e, sm[smem_slot(k, cc, LC)], Dout, a.conj_out, nonfinite);
+      Mem<P, KIND>::store(data, tile0 + (uint64_t)e, sm[slot(k, cc)], Dout, a.conj_out, nonfinite);
     }
   }
 }
@@ -598,6 +611,12 @@ __global__ void __launch_bounds__(256) efft_digit_swap(E* __restrict__ data, int
 cudaError_t fx_set_attrs_df2();
 bool fx_launch_df2(int kind, int log2R, dim3 grid, dim3 block, size_t smem, cudaStream_t st, void* data,
                    const PassArgs& a);
+// complex128 first pass with 8192-element tiles (R = 2^10 or 2^11), one CTA
+// of 512 threads per SM: twice the bytes per row segment of the 4096-element
+// tile, for first passes whose rows lie in different pages.
+constexpr int kLog2CtaWide = 13;
+bool fx_launch_df2_wide(int log2R, dim3 grid, dim3 block, size_t smem, cudaStream_t st, void* data,
+                        const PassArgs& a);
 cudaError_t fx_set_attrs_f32();
 bool fx_launch_f32(int kind, int log2R, dim3 grid, dim3 block, size_t smem, cudaStream_t st, void* data,
                    const PassArgs& a);

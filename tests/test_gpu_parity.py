@@ -175,6 +175,18 @@ def test_parity_large_full_oracle(orc, name, e):
     check(got, orc.fft_radix2(x, -1), name, N)
 
 
+@pytest.mark.parametrize("sign", [-1, 1])
+def test_parity_2p28_wide_first_pass(orc, sign):
+    """complex128 2^28 = 2^10 * 2^8 * 2^10: the first pass runs on
+    8192-element tiles (from 2^28 on); against the full oracle."""
+    import paper_1409_5757_gb300 as efft
+    N = 1 << 28
+    assert efft.Plan(N, efft.EFFT_C128, sign).radices() == [10, 8, 10]
+    x = host_input(orc, "c128", N, seed=2828)
+    got = gpu_fft(x, "c128", sign)
+    check(got, orc.fft_radix2(x, sign), "c128", N)
+
+
 def test_execute_host_entry_point(orc):
     import paper_1409_5757_gb300 as efft
     N = 1 << 18
