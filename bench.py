@@ -52,9 +52,10 @@ WORKLOADS = {
     "c4": dict(log2n=31, dtype="c64", seed=4, tones=0, fwd_inv=False, gauss=True,
                desc="complex64 N=2^31 in place, one transform per step; Gaussian(0,1) re/im"),
     "c5": dict(batch=256, emin=12, emax=24, log2n=24, dtype="c64", seed=5, tones=0, fwd_inv=True, gauss=False,
+               autotune=True,
                desc="256 complex64 transforms in place, N_i = 2^e_i with e_i uniform in {12..24} (seed 5), "
                     "one graph launch per direction: forward, then the normalised conjugate-sign transform; "
-                    "uniform[-1,1) re/im"),
+                    "radix schedules from the autotuner; uniform[-1,1) re/im"),
 }
 DTYPE_NAME = {"c128": "df32 (double-float f32 pairs; complex128 in/out)", "c64": "f32 (complex64)"}
 
@@ -187,6 +188,40 @@ def oracle_time(log2n: int, seed: int, reps: int = 1):
         dt = time.perf_counter() - t0
         best = dt if best is None else min(best, dt)
     return best, o.threads
+
+
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part")):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def oracle_single_core(log2n: int, seed: int):
+    """GFLOP/s of one forward oracle transform of 2^log2n points on one core
+    (a fresh interpreter with OMP_NUM_THREADS=1)."""
+    code = ("import sys, time; sys.path.insert(0, %r); import oracle; o = oracle.get(); "
+            "x = o.gen_uniform(%d, 1 << %d); t = time.perf_counter(); o.fft_radix2(x, -1); "
+            "print(time.perf_counter() - t, o.threads)") % (ROOT, seed, log2n)
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    try:
+        r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=600)
+        dt, th = r.stdout.split()[-2:]
+        return {"value": flops(1 << log2n) / float(dt) / 1e9, "unit": "GFLOP/s", "cores": int(th),
+                "sample": f"one forward FP64 radix-2 oracle transform of N=2^{log2n}, {float(dt):.2f} s"}
+    except Exception as ex:  # report, do not fail the benchmark line
+        return {"value": None, "error": str(ex)[:200]}
 
 
 def oracle_sample_log2n(target_s: float, cap: int) -> int:
@@ -338,11 +373,12 @@ def run_ours(args, wl):
     torch.cuda.synchronize(dev)
     ref_norm = None
     keep = None
-    if N <= (1 << 30):
+    if N * S <= (32 << 30):
         keep = x.clone()  # for the round-trip accuracy check after timing
 
-    fwd = efft.Plan(N, code, -1)
-    inv = efft.Plan(N, code, +1, efft.EFFT_FLAG_NORMALIZE)
+    tune = efft.EFFT_FLAG_AUTOTUNE if args.autotune else 0
+    fwd = efft.Plan(N, code, -1, tune)
+    inv = efft.Plan(N, code, +1, efft.EFFT_FLAG_NORMALIZE | tune)
     stream = torch.cuda.current_stream(dev)
     sp = stream.cuda_stream
     tps = 2 if wl["fwd_inv"] else 1
@@ -371,11 +407,13 @@ def run_ours(args, wl):
     inv.profile(True)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.profiler.start()  # a profiler run with --profile-from-start off sees the timed region only
     e0.record(stream)
     for i in range(K):
         step(W + i)
     e1.record(stream)
     torch.cuda.synchronize(dev)
+    torch.cuda.profiler.stop()
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize(dev)
@@ -398,9 +436,15 @@ def run_ours(args, wl):
 
     # accuracy: after W+K round trips the buffer should equal the input
     accuracy = None
-    if keep is not None and wl["fwd_inv"]:
+    done = W + K
+    if not wl["fwd_inv"] and done % 2 == 1:
+        step(done)  # untimed: complete the last forward / inverse pair
+        done += 1
+    round_trips = done if wl["fwd_inv"] else done // 2
+    if keep is not None:
+        # forward then normalised inverse, round_trips times: x should return
         num, den = inputs.diff_norms(x, keep, 1.0)
-        accuracy = {"roundtrip_rel_l2_after_all_steps": math.sqrt(num / den), "round_trips": W + K,
+        accuracy = {"roundtrip_rel_l2_after_all_steps": math.sqrt(num / den), "round_trips": round_trips,
                     "tolerance_per_round_trip": 2e-14 * wl["log2n"] if c128 else 4e-6 * wl["log2n"]}
 
     # roofline of the dominant kernel
@@ -423,6 +467,33 @@ def run_ours(args, wl):
                     "per_launch_ms": tot_ms / nl, "algorithmic_bytes_per_launch": alg_bytes,
                     "kernels_ms_per_step": {k: v[0] / K for k, v in prof.items()}}
     launches = sum(v[1] for v in prof.values())
+    floor_gbs = world * tps * 2 * N * S / (ms_per_step * 1e-3) / 1e9
+
+    # the FP32 form against the FP64 form at the same N (complex64 workloads)
+    same_n_c128 = None
+    if not c128 and N * 16 <= (64 << 30) and not args.no_compare:
+        del keep
+        keep = None
+        y = torch.empty(N, dtype=torch.complex128, device=dev)
+        inputs.fill_gaussian(y, wl["seed"]) if wl["gauss"] else inputs.fill_uniform(y, wl["seed"])
+        p128f = efft.Plan(N, efft.EFFT_C128, -1)
+        p128i = efft.Plan(N, efft.EFFT_C128, +1, efft.EFFT_FLAG_NORMALIZE)
+        for i in range(3):
+            (p128f if i % 2 == 0 else p128i).execute(y.data_ptr(), sp)
+        Kc = 4
+        c0 = torch.cuda.Event(enable_timing=True)
+        c1 = torch.cuda.Event(enable_timing=True)
+        c0.record(stream)
+        for i in range(Kc):
+            (p128i if i % 2 == 0 else p128f).execute(y.data_ptr(), sp)
+        c1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms128 = c0.elapsed_time(c1) / Kc
+        same_n_c128 = {"value": flops(N) / (ms128 * 1e-3) / 1e9, "unit": "GFLOP/s", "ms_per_transform": ms128,
+                       "speedup_of_complex64": ms128 / (ms_per_step / tps)}
+        for q in (p128f, p128i):
+            q.destroy()
+        del y
 
     # end to end: host buffers through efft_execute_host_stream (each step copies
     # its input from pinned host memory, transforms, copies the result back;
@@ -461,14 +532,18 @@ def run_ours(args, wl):
         dt, cores = oracle_time(e, wl["seed"])
         cpu = {"value": flops(1 << e) / dt / 1e9, "unit": "GFLOP/s", "cores": cores, "kind": "oracle",
                "sample": f"one forward FP64 radix-2 oracle transform of N=2^{e} (same seeded uniform input "
-                         f"family) on the host cores, {dt:.1f} s"}
+                         f"family) on the host cores, {dt:.1f} s",
+               "nproc": os.cpu_count(), "cpu_model": cpu_model(),
+               "single_core": oracle_single_core(min(e, 24), wl["seed"])}
 
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": K, "warmup": W,
             "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": DTYPE_NAME[wl["dtype"]], "data": "synthetic", "config": config_of(wl),
-            "hbm_gbs": hbm_gbs, "hbm_passes_per_transform": hbm_passes,
+            "hbm_gbs": hbm_gbs, "hbm_passes_per_transform": hbm_passes, "floor_equivalent_gbs": floor_gbs,
+            "radices_log2": fwd.radices(),
+            "fp64_form_same_n": same_n_c128,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "clocks": clocks, "accuracy": accuracy, "impl": "ours",
         }
@@ -517,8 +592,10 @@ def run_batch(args, wl):
     keep = arena.clone()
     ptrs = [arena.data_ptr() + o * S for o in offs[:-1]]
     sizes = [1 << e for e in es]
-    fwd = efft.Batch(sizes, code, -1)
-    inv = efft.Batch(sizes, code, +1, efft.EFFT_FLAG_NORMALIZE)
+    tune = efft.EFFT_FLAG_AUTOTUNE if (wl.get("autotune") or args.autotune) else 0
+    fwd = efft.Batch(sizes, code, -1, tune)
+    inv = efft.Batch(sizes, code, +1, efft.EFFT_FLAG_NORMALIZE | tune)
+    schedules = {e: efft.Plan(1 << e, code, -1, tune).radices() for e in sorted(set(es))}
     kernels = fwd.info()["kernels"] + inv.info()["kernels"]
     stream = torch.cuda.current_stream(dev)
     sp = stream.cuda_stream
@@ -538,6 +615,7 @@ def run_batch(args, wl):
     sampler.start()
     time.sleep(0.3)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * K + 1)]
+    torch.cuda.profiler.start()  # a profiler run with --profile-from-start off sees the timed region only
     ev[0].record(stream)
     for i in range(K):
         fwd.execute(ptrs, sp)
@@ -545,6 +623,7 @@ def run_batch(args, wl):
         inv.execute(ptrs, sp)
         ev[2 * i + 2].record(stream)
     torch.cuda.synchronize(dev)
+    torch.cuda.profiler.stop()
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize(dev)
@@ -558,7 +637,7 @@ def run_batch(args, wl):
     value = world * step_flop / (ms_per_step * 1e-3) / 1e9
     passes = {}
     for e in sorted(set(es)):
-        passes[e] = efft.Plan(1 << e, code, -1).info()["hbm_passes"]
+        passes[e] = efft.Plan(1 << e, code, -1, tune).info()["hbm_passes"]
     step_bytes = 2 * sum(passes[e] * 2 * (1 << e) * S for e in es)
     hbm_gbs = world * step_bytes / (ms_per_step * 1e-3) / 1e9
 
@@ -610,6 +689,7 @@ def run_batch(args, wl):
             "dtype": DTYPE_NAME[wl["dtype"]], "data": "synthetic", "config": config_of(wl),
             "hbm_gbs": hbm_gbs, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": K * kernels, "clocks": clocks, "accuracy": accuracy, "impl": "ours",
+            "schedules_log2": {str(e): r for e, r in schedules.items()},
         }
         print(json.dumps(line), flush=True)
     fwd.destroy()
@@ -629,6 +709,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg")
+    ap.add_argument("--autotune", action="store_true",
+                    help="plans with EFFT_FLAG_AUTOTUNE (measured radix schedules; c5 always tunes)")
+    ap.add_argument("--no-compare", action="store_true",
+                    help="complex64 workloads: skip the complex128 run at the same N")
     ap.add_argument("--log2n", type=int, default=None,
                     help="override the workload's size (profiling captures on a smaller case)")
     args = ap.parse_args()

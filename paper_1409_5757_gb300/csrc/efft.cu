@@ -7,22 +7,20 @@
 // word; an execute enqueues the pass kernels on the caller's stream.
 #include <cuda_runtime.h>
 
-#include <algorithm>
-#include <atomic>
 #include <cstdint>
 #include <cstdlib>
 #include <cstring>
-#include <map>
 #include <mutex>
 #include <new>
 #include <set>
-#include <tuple>
 #include <vector>
 
 #include "../../include/efft.h"
+#include "efft_host.h"
 #include "efft_kernels.cuh"
 
 using namespace efft;
+using namespace efft::host;
 
 namespace efft {
 // ----------------------------------------------------------------------------
@@ -78,53 +76,15 @@ __global__ void efft_twiddles(float4* __restrict__ out, uint64_t count, uint64_t
 }  // namespace efft
 
 namespace {
-
-constexpr uint32_t kMagic = 0xEFF71409u;
-constexpr int kLog2CtaC128 = 12;  // 4096 complex128 elements per CTA (64 KiB)
-constexpr int kLog2CtaC64 = 13;   // 8192 complex64 elements per CTA (64 KiB)
-constexpr int kMaxPasses = 4;
-constexpr int kWideMinLog2N = 28;  // complex128 first passes on 8192-element tiles from 2^28
 constexpr size_t kCopyChunk = size_t(1) << 30;  // host copies of the streaming entry point
-
-struct Pass {
-  int log2R, log2s, log2L, log2C, kind;
-  bool wide;  // complex128 first pass on 8192-element tiles
-  uint64_t grid;
-  int threads;
-  size_t smem;
-};
-
+std::mutex g_mu;
 }  // namespace
 
-struct efft_plan_s {
-  uint32_t magic;
-  int device;
-  uint64_t n;
-  int log2n;
-  int dtype;
-  int sign;
-  uint32_t flags;
-  int npasses;
-  Pass pass[kMaxPasses];
-  bool small;             // N <= 8: direct-sum kernel
-  bool permute;           // final digit swap enabled
-  int perm_log2A, perm_log2B;
-  int twB;
-  float4* w2048;
-  float4* tw_lo;
-  float4* tw_hi;
-  uint32_t* state;
-  uint64_t table_bytes;
-  // profiling: CUDA event pairs recorded around each launch
-  bool profiling;
-  struct Rec { int slot; cudaEvent_t a, b; };
-  std::vector<Rec>* recs;
-  std::vector<cudaEvent_t>* pool;
-};
+namespace efft {
+namespace host {
 
-namespace {
+std::mutex& registry_mutex() { return g_mu; }
 
-std::mutex g_mu;
 std::set<efft_plan_s*>* g_live = nullptr;  // leaked on purpose: safe at exit
 
 bool plan_is_live(efft_plan_s* p) {
@@ -177,31 +137,6 @@ bool valid_schedule(int e, const int* r, int np) {
   return sum == e && r[0] == r[np - 1];
 }
 
-// Every accepted schedule for N = 2^e (at most 1 + 1 + 8 of them).
-int schedule_candidates(int e, int (*r)[kMaxPasses], int* np) {
-  int k = 0;
-  if (e <= 3) {
-    np[k++] = 0;
-    return k;
-  }
-  if (e <= 11) {
-    r[k][0] = e;
-    np[k++] = 1;
-  }
-  if (e % 2 == 0 && e / 2 >= 4 && e / 2 <= 11) {
-    r[k][0] = r[k][1] = e / 2;
-    np[k++] = 2;
-  }
-  for (int a = 4; a <= 11; ++a) {
-    const int b = e - 2 * a;
-    if (b < 4 || b > 11) continue;
-    r[k][0] = r[k][2] = a;
-    r[k][1] = b;
-    np[k++] = 3;
-  }
-  return k;
-}
-
 // Fills the pass table of p (log2n, dtype and flags already set) for the
 // radix list r[0..np).
 void apply_schedule(efft_plan_s* p, const int* r, int np) {
@@ -238,26 +173,6 @@ void apply_schedule(efft_plan_s* p, const int* r, int np) {
   p->perm_log2B = (np == 3) ? r[1] : 0;
 }
 
-// Autotuned schedules per (device, log2 N, dtype).
-struct Tuned { int np; int r[kMaxPasses]; };
-std::mutex g_tune_mu;
-std::map<std::tuple<int, int, int>, Tuned>* g_tuned = nullptr;  // leaked on purpose
-
-bool tuned_lookup(int dev, int e, int dtype, Tuned* t) {
-  std::lock_guard<std::mutex> lk(g_tune_mu);
-  if (!g_tuned) return false;
-  auto it = g_tuned->find(std::make_tuple(dev, e, dtype));
-  if (it == g_tuned->end()) return false;
-  *t = it->second;
-  return true;
-}
-
-void tuned_store(int dev, int e, int dtype, const Tuned& t) {
-  std::lock_guard<std::mutex> lk(g_tune_mu);
-  if (!g_tuned) g_tuned = new std::map<std::tuple<int, int, int>, Tuned>();
-  (*g_tuned)[std::make_tuple(dev, e, dtype)] = t;
-}
-
 template <class P, int KIND, int CTA>
 void set_smem_attr() {
   cudaFuncSetAttribute(efft_pass<P, KIND, CTA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -283,19 +198,6 @@ int init_kernels() {
   });
   return err == cudaSuccess ? EFFT_OK : EFFT_ERR_CUDA;
 }
-
-struct DeviceGuard {
-  int prev = -1;
-  bool ok = false;
-  explicit DeviceGuard(int dev) {
-    if (cudaGetDevice(&prev) != cudaSuccess) return;
-    ok = (prev == dev) || (cudaSetDevice(dev) == cudaSuccess);
-  }
-  ~DeviceGuard() {
-    int cur = -1;
-    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
-  }
-};
 
 int gen_table(float4* out, uint64_t count, uint64_t stride, int log2N, cudaStream_t st) {
   const int bs = 256;
@@ -359,14 +261,6 @@ void prof_end(efft_plan_s* p, int rec, cudaStream_t st) {
 }
 
 // P: policy of the generic kernel; PFX: policy of the specialised kernels
-// Batch: ptrs (device array of `count` data pointers, or NULL for one
-// transform at `data`) and state words (16 bytes per transform).
-struct Batch {
-  void* const* ptrs;
-  unsigned count;
-  uint32_t* state;
-};
-
 template <class P, class PFX, int CTA>
 cudaError_t launch_pass(const efft_plan_s* p, const Pass& ps, void* data, const Batch& bt, cudaStream_t st) {
   PassArgs a;
@@ -406,7 +300,8 @@ cudaError_t launch_pass(const efft_plan_s* p, const Pass& ps, void* data, const 
   return cudaGetLastError();
 }
 
-}  // namespace
+}  // namespace host
+}  // namespace efft
 
 // ---------------------------------------------------------------------------
 // C ABI
@@ -436,10 +331,8 @@ const char* efft_strerror(int s) {
 
 }  // extern "C"
 
-namespace {
-
-int autotune_impl(efft_plan_s* p, void* scratch, cudaStream_t st, int* cand_log2r, double* cand_ms, int cap,
-                  int* ncand);
+namespace efft {
+namespace host {
 
 // Plan creation; r_explicit != NULL: the caller's schedule (already checked).
 int plan_create_impl(efft_plan_t* out, uint64_t n, int dtype, int sign, uint32_t flags, const int* r_explicit,
@@ -538,7 +431,8 @@ int check_create_args(efft_plan_t* out, uint64_t n, int dtype, int sign) {
   return EFFT_OK;
 }
 
-}  // namespace
+}  // namespace host
+}  // namespace efft
 
 extern "C" {
 
@@ -595,7 +489,12 @@ int efft_plan_info(efft_plan_t plan, double* hbm_passes, uint64_t* table_bytes) 
   return EFFT_OK;
 }
 
-static int check_buffer(const efft_plan_s* p, const void* data) {
+}  // extern "C"
+
+namespace efft {
+namespace host {
+
+int check_buffer(const efft_plan_s* p, const void* data) {
   if (!data) return EFFT_ERR_INVALID_PTR;
   const uintptr_t align = (p->dtype == EFFT_C128) ? 16 : 8;
   if (reinterpret_cast<uintptr_t>(data) % align) return EFFT_ERR_MISALIGNED;
@@ -611,7 +510,7 @@ static int check_buffer(const efft_plan_s* p, const void* data) {
 
 // One transform at `data`, or bt.count transforms (bt.ptrs) of the plan's
 // size in the same launches.
-static int enqueue_batch(efft_plan_s* p, void* data, const Batch& bt, cudaStream_t st) {
+int enqueue_batch(efft_plan_s* p, void* data, const Batch& bt, cudaStream_t st) {
   if (fault_injected("launch")) return EFFT_ERR_LAUNCH;
   if (p->log2n == 0 || bt.count == 0) return EFFT_OK;  // N = 1: the DFT is the identity
   const bool c128 = (p->dtype == EFFT_C128);
@@ -666,10 +565,15 @@ static int enqueue_batch(efft_plan_s* p, void* data, const Batch& bt, cudaStream
   return EFFT_OK;
 }
 
-static int enqueue(efft_plan_s* p, void* data, cudaStream_t st) {
+int enqueue(efft_plan_s* p, void* data, cudaStream_t st) {
   const Batch one{nullptr, 1u, p->state};
   return enqueue_batch(p, data, one, st);
 }
+
+}  // namespace host
+}  // namespace efft
+
+extern "C" {
 
 int efft_execute(efft_plan_t plan, void* data, void* stream) {
   if (!plan_is_live(plan)) return EFFT_ERR_INVALID_PLAN;
@@ -823,328 +727,6 @@ int efft_plan_profile_read(efft_plan_t plan, double* ms, int* count, int cap, in
   }
   if (nslots) *nslots = EFFT_PROFILE_SLOTS;
   return rc;
-}
-
-}  // extern "C"
-
-// ---------------------------------------------------------------------------
-// Autotuner: the schedule scan of the paper's Sec. 5.2 (Figs. 6-7), over the
-// radix lists the kernels accept instead of (split depth, worker count).
-// ---------------------------------------------------------------------------
-namespace {
-
-int autotune_impl(efft_plan_s* p, void* scratch, cudaStream_t st, int* cand_log2r, double* cand_ms, int cap,
-                  int* ncand) {
-  int cr[16][kMaxPasses] = {};
-  int cnp[16] = {};
-  const int nc = schedule_candidates(p->log2n, cr, cnp);
-  if (ncand) *ncand = nc;
-  int prev_r[kMaxPasses] = {0, 0, 0, 0};
-  const int prev_np = p->npasses;
-  for (int j = 0; j < prev_np; ++j) prev_r[j] = p->pass[j].log2R;
-  const size_t bytes = p->n * ((p->dtype == EFFT_C128) ? 16 : 8);
-  const int reps = (p->n <= (1ull << 20)) ? 21 : (p->n <= (1ull << 26) ? 9 : 5);
-  const bool prof = p->profiling;
-  p->profiling = false;
-  std::vector<cudaEvent_t> ev(2 * reps, nullptr);
-  std::vector<float> t(reps, 0.f);
-  int rc = EFFT_OK;
-  for (auto& x : ev)
-    if (cudaEventCreate(&x) != cudaSuccess) {
-      rc = EFFT_ERR_CUDA;
-      break;
-    }
-  int best = -1;
-  double best_ms = 0.0;
-  for (int c = 0; rc == EFFT_OK && c < nc; ++c) {
-    apply_schedule(p, cr[c], cnp[c]);
-    for (int k = -2; rc == EFFT_OK && k < reps; ++k) {
-      // a fresh finite input each time (repeated unnormalised transforms
-      // would overflow); the fill is outside the timed interval
-      if (cudaMemsetAsync(scratch, 0x3F, bytes, st) != cudaSuccess) {
-        rc = EFFT_ERR_LAUNCH;
-        break;
-      }
-      if (k >= 0) cudaEventRecord(ev[2 * k], st);
-      rc = enqueue(p, scratch, st);
-      if (k >= 0) cudaEventRecord(ev[2 * k + 1], st);
-    }
-    if (rc != EFFT_OK) break;
-    if (cudaStreamSynchronize(st) != cudaSuccess) {
-      rc = EFFT_ERR_CUDA;
-      break;
-    }
-    for (int k = 0; k < reps; ++k)
-      if (cudaEventElapsedTime(&t[k], ev[2 * k], ev[2 * k + 1]) != cudaSuccess) rc = EFFT_ERR_CUDA;
-    if (rc != EFFT_OK) break;
-    std::nth_element(t.begin(), t.begin() + reps / 2, t.end());
-    const double ms = t[reps / 2];
-    if (cand_log2r && c < cap)
-      for (int j = 0; j < kMaxPasses; ++j) cand_log2r[kMaxPasses * c + j] = (j < cnp[c]) ? cr[c][j] : 0;
-    if (cand_ms && c < cap) cand_ms[c] = ms;
-    if (best < 0 || ms < best_ms) {
-      best = c;
-      best_ms = ms;
-    }
-  }
-  for (auto x : ev)
-    if (x) cudaEventDestroy(x);
-  p->profiling = prof;
-  if (rc != EFFT_OK || best < 0) {
-    cudaGetLastError();
-    apply_schedule(p, prev_r, prev_np);
-    return rc == EFFT_OK ? EFFT_ERR_CUDA : rc;
-  }
-  apply_schedule(p, cr[best], cnp[best]);
-  Tuned tu;
-  tu.np = cnp[best];
-  for (int j = 0; j < kMaxPasses; ++j) tu.r[j] = cr[best][j];
-  tuned_store(p->device, p->log2n, p->dtype, tu);
-  return EFFT_OK;
-}
-
-}  // namespace
-
-// ---------------------------------------------------------------------------
-// Batches of mixed sizes behind one CUDA graph.
-// ---------------------------------------------------------------------------
-struct efft_batch_s {
-  uint32_t magic = 0;
-  int device = 0;
-  int count = 0;
-  std::vector<efft_plan_s*> plans;  // one per distinct size, largest first
-  std::vector<int> gstart;          // group g owns pointer slots [gstart[g], gstart[g+1])
-  std::vector<int> slot;            // transform i -> its pointer slot
-  std::vector<int> group;           // transform i -> its group
-  void** dptrs = nullptr;           // device: count pointers, by slot
-  uint32_t* state = nullptr;        // device: 16 bytes per slot
-  void** stage = nullptr;           // pinned host: EFFT_BATCH_INFLIGHT * count pointers
-  cudaEvent_t done[EFFT_BATCH_INFLIGHT] = {};
-  int next = 0;
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t exec = nullptr;
-  int kernels = 0;
-};
-
-namespace {
-
-constexpr uint32_t kBatchMagic = 0xEFF7BA7Cu;
-std::set<efft_batch_s*>* g_live_batches = nullptr;  // leaked on purpose, guarded by g_mu
-
-bool batch_is_live(efft_batch_s* b) {
-  std::lock_guard<std::mutex> lk(g_mu);
-  return g_live_batches && g_live_batches->count(b) && b->magic == kBatchMagic;
-}
-
-void batch_free(efft_batch_s* b) {
-  for (int k = 0; k < EFFT_BATCH_INFLIGHT; ++k)
-    if (b->done[k]) cudaEventSynchronize(b->done[k]);
-  if (b->exec) cudaGraphExecDestroy(b->exec);
-  if (b->graph) cudaGraphDestroy(b->graph);
-  for (int k = 0; k < EFFT_BATCH_INFLIGHT; ++k)
-    if (b->done[k]) cudaEventDestroy(b->done[k]);
-  if (b->dptrs) cudaFree(b->dptrs);
-  if (b->state) cudaFree(b->state);
-  if (b->stage) cudaFreeHost(b->stage);
-  for (efft_plan_s* p : b->plans) efft_plan_destroy(p);
-  cudaGetLastError();
-  delete b;
-}
-
-// Records every group's launches into one graph: group 0 on the capture
-// stream, the others on forked side streams joined back at the end.
-int batch_capture(efft_batch_s* b) {
-  const int G = (int)b->plans.size();
-  cudaStream_t cs = nullptr;
-  std::vector<cudaStream_t> side(G, nullptr);
-  std::vector<cudaEvent_t> join(G, nullptr);
-  cudaEvent_t fork = nullptr;
-  int rc = EFFT_OK;
-  if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) != cudaSuccess)
-    rc = EFFT_ERR_CUDA;
-  for (int g = 1; rc == EFFT_OK && g < G; ++g)
-    if (cudaStreamCreateWithFlags(&side[g], cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreateWithFlags(&join[g], cudaEventDisableTiming) != cudaSuccess)
-      rc = EFFT_ERR_CUDA;
-  if (rc == EFFT_OK) {
-    if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
-      rc = EFFT_ERR_CUDA;
-    } else {
-      bool forked = (G == 1) || cudaEventRecord(fork, cs) == cudaSuccess;
-      if (!forked) rc = EFFT_ERR_CUDA;
-      for (int g = 1; g < G && forked; ++g)
-        if (cudaStreamWaitEvent(side[g], fork, 0) != cudaSuccess) rc = EFFT_ERR_CUDA;
-      for (int g = 0; g < G && rc == EFFT_OK && forked; ++g) {
-        const int s0 = b->gstart[g], cnt = b->gstart[g + 1] - s0;
-        const Batch bt{reinterpret_cast<void* const*>(b->dptrs + s0), (unsigned)cnt, b->state + 4 * (size_t)s0};
-        rc = enqueue_batch(b->plans[g], nullptr, bt, g == 0 ? cs : side[g]);
-      }
-      // join every forked stream, also after an error, so the capture ends cleanly
-      for (int g = 1; g < G && forked; ++g)
-        if (cudaEventRecord(join[g], side[g]) != cudaSuccess || cudaStreamWaitEvent(cs, join[g], 0) != cudaSuccess)
-          if (rc == EFFT_OK) rc = EFFT_ERR_CUDA;
-      cudaGraph_t graph = nullptr;
-      if (cudaStreamEndCapture(cs, &graph) != cudaSuccess && rc == EFFT_OK) rc = EFFT_ERR_CUDA;
-      b->graph = graph;
-    }
-  }
-  if (rc == EFFT_OK && cudaGraphInstantiate(&b->exec, b->graph, 0) != cudaSuccess) rc = EFFT_ERR_CUDA;
-  if (rc == EFFT_OK) {
-    size_t num = 0;
-    if (cudaGraphGetNodes(b->graph, nullptr, &num) == cudaSuccess && num > 0) {
-      std::vector<cudaGraphNode_t> nodes(num);
-      if (cudaGraphGetNodes(b->graph, nodes.data(), &num) == cudaSuccess)
-        for (size_t k = 0; k < num; ++k) {
-          cudaGraphNodeType ty;
-          if (cudaGraphNodeGetType(nodes[k], &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel) ++b->kernels;
-        }
-    }
-  }
-  for (int g = 1; g < G; ++g) {
-    if (side[g]) cudaStreamDestroy(side[g]);
-    if (join[g]) cudaEventDestroy(join[g]);
-  }
-  if (fork) cudaEventDestroy(fork);
-  if (cs) cudaStreamDestroy(cs);
-  if (rc != EFFT_OK) cudaGetLastError();
-  return rc;
-}
-
-}  // namespace
-
-extern "C" {
-
-int efft_plan_autotune(efft_plan_t plan, void* scratch, void* stream, int* cand_log2r, double* cand_ms, int cap,
-                       int* ncand) {
-  if (!plan_is_live(plan)) return EFFT_ERR_INVALID_PLAN;
-  DeviceGuard g(plan->device);
-  if (!g.ok) return EFFT_ERR_CUDA;
-  int rc = check_buffer(plan, scratch);
-  if (rc != EFFT_OK) return rc;
-  return autotune_impl(plan, scratch, reinterpret_cast<cudaStream_t>(stream), cand_log2r, cand_ms,
-                       cap < 0 ? 0 : cap, ncand);
-}
-
-int efft_batch_create(efft_batch_t* out, const uint64_t* sizes, int count, int dtype, int sign, uint32_t flags) {
-  if (!out) return EFFT_ERR_INVALID_PTR;
-  *out = nullptr;
-  if (!sizes) return EFFT_ERR_INVALID_PTR;
-  if (count < 1) return EFFT_ERR_INVALID_SIZE;
-  if (dtype != EFFT_C64 && dtype != EFFT_C128) return EFFT_ERR_INVALID_DTYPE;
-  if (sign != -1 && sign != 1) return EFFT_ERR_INVALID_SIGN;
-  if (flags & ~EFFT_FLAG_ALL) return EFFT_ERR_INVALID_FLAGS;
-  std::map<uint64_t, std::vector<int>, std::greater<uint64_t>> by_size;
-  for (int i = 0; i < count; ++i) {
-    const uint64_t n = sizes[i];
-    if (n == 0 || (n & (n - 1)) != 0 || n > (1ull << EFFT_MAX_LOG2N)) return EFFT_ERR_INVALID_SIZE;
-    by_size[n].push_back(i);
-  }
-  for (auto& kv : by_size)
-    if (kv.second.size() > 65535) return EFFT_ERR_INVALID_SIZE;
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) {
-    cudaGetLastError();
-    return EFFT_ERR_CUDA;
-  }
-  efft_batch_s* b = new (std::nothrow) efft_batch_s();
-  if (!b) return EFFT_ERR_ALLOC;
-  b->device = dev;
-  b->count = count;
-  b->slot.assign(count, 0);
-  b->group.assign(count, 0);
-  int rc = EFFT_OK;
-  int pos = 0;
-  for (auto& kv : by_size) {
-    const int g = (int)b->plans.size();
-    b->gstart.push_back(pos);
-    for (int i : kv.second) {
-      b->slot[i] = pos++;
-      b->group[i] = g;
-    }
-    efft_plan_t pl = nullptr;
-    rc = efft_plan_create(&pl, kv.first, dtype, sign, flags);
-    if (rc != EFFT_OK) break;
-    b->plans.push_back(pl);
-  }
-  b->gstart.push_back(count);
-  if (rc == EFFT_OK && (cudaMalloc(&b->dptrs, sizeof(void*) * count) != cudaSuccess ||
-                        cudaMalloc(&b->state, 16 * (size_t)count) != cudaSuccess ||
-                        cudaHostAlloc(&b->stage, sizeof(void*) * count * EFFT_BATCH_INFLIGHT,
-                                      cudaHostAllocDefault) != cudaSuccess))
-    rc = EFFT_ERR_ALLOC;
-  for (int k = 0; rc == EFFT_OK && k < EFFT_BATCH_INFLIGHT; ++k)
-    if (cudaEventCreateWithFlags(&b->done[k], cudaEventDisableTiming) != cudaSuccess) rc = EFFT_ERR_CUDA;
-  if (rc == EFFT_OK && cudaMemset(b->dptrs, 0, sizeof(void*) * count) != cudaSuccess) rc = EFFT_ERR_CUDA;
-  if (rc == EFFT_OK) rc = batch_capture(b);
-  if (rc != EFFT_OK) {
-    cudaGetLastError();
-    batch_free(b);
-    return rc;
-  }
-  b->magic = kBatchMagic;
-  {
-    std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_live_batches) g_live_batches = new std::set<efft_batch_s*>();
-    g_live_batches->insert(b);
-  }
-  *out = b;
-  return EFFT_OK;
-}
-
-int efft_batch_execute(efft_batch_t b, void* const* data, void* stream) {
-  if (!batch_is_live(b)) return EFFT_ERR_INVALID_PLAN;
-  if (!data) return EFFT_ERR_INVALID_PTR;
-  DeviceGuard g(b->device);
-  if (!g.ok) return EFFT_ERR_CUDA;
-  // every buffer valid, and no two overlapping (they are transformed concurrently)
-  std::vector<std::pair<uintptr_t, uintptr_t>> spans(b->count);
-  for (int i = 0; i < b->count; ++i) {
-    const efft_plan_s* p = b->plans[b->group[i]];
-    int rc = check_buffer(p, data[i]);
-    if (rc != EFFT_OK) return rc;
-    const uintptr_t a = reinterpret_cast<uintptr_t>(data[i]);
-    spans[i] = {a, a + p->n * ((p->dtype == EFFT_C128) ? 16 : 8)};
-  }
-  std::sort(spans.begin(), spans.end());
-  for (int i = 1; i < b->count; ++i)
-    if (spans[i].first < spans[i - 1].second) return EFFT_ERR_INVALID_PTR;
-  if (fault_injected("launch")) return EFFT_ERR_LAUNCH;
-  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  const int k = b->next;
-  if (cudaEventSynchronize(b->done[k]) != cudaSuccess) {  // staging slot k free again
-    cudaGetLastError();
-    return EFFT_ERR_CUDA;
-  }
-  void** stage = b->stage + (size_t)k * b->count;
-  for (int i = 0; i < b->count; ++i) stage[b->slot[i]] = data[i];
-  if (cudaMemcpyAsync(b->dptrs, stage, sizeof(void*) * b->count, cudaMemcpyHostToDevice, st) != cudaSuccess ||
-      cudaGraphLaunch(b->exec, st) != cudaSuccess || cudaEventRecord(b->done[k], st) != cudaSuccess) {
-    cudaGetLastError();
-    return EFFT_ERR_LAUNCH;
-  }
-  b->next = (k + 1) % EFFT_BATCH_INFLIGHT;
-  return EFFT_OK;
-}
-
-int efft_batch_info(efft_batch_t b, int* ngroups, int* kernels) {
-  if (!batch_is_live(b)) return EFFT_ERR_INVALID_PLAN;
-  if (ngroups) *ngroups = (int)b->plans.size();
-  if (kernels) *kernels = b->kernels;
-  return EFFT_OK;
-}
-
-int efft_batch_destroy(efft_batch_t b) {
-  if (!b) return EFFT_OK;
-  {
-    std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_live_batches || !g_live_batches->count(b) || b->magic != kBatchMagic) return EFFT_ERR_INVALID_PLAN;
-    g_live_batches->erase(b);
-  }
-  b->magic = 0;
-  DeviceGuard g(b->device);
-  batch_free(b);
-  return EFFT_OK;
 }
 
 }  // extern "C"

@@ -1,0 +1,129 @@
+// efft_host.h -- host-side internals shared by the translation units of
+// libefft.so: efft.cu (plans, execution, the C ABI of plans), efft_tune.cu
+// (schedule autotuner) and efft_batch.cu (mixed-size batches).  Not part of
+// the public interface (include/efft.h).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <mutex>
+#include <vector>
+
+#include "../../include/efft.h"
+#include "efft_kernels.cuh"
+
+namespace efft {
+namespace host {
+
+constexpr uint32_t kMagic = 0xEFF71409u;
+constexpr int kLog2CtaC128 = 12;   // 4096 complex128 elements per CTA (64 KiB)
+constexpr int kLog2CtaC64 = 13;    // 8192 complex64 elements per CTA (64 KiB)
+constexpr int kMaxPasses = 4;
+constexpr int kWideMinLog2N = 28;  // complex128 first passes on 8192-element tiles from 2^28
+
+// One pass of the schedule and its launch shape.
+struct Pass {
+  int log2R, log2s, log2L, log2C, kind;
+  bool wide;  // complex128 first pass on 8192-element tiles
+  uint64_t grid;
+  int threads;
+  size_t smem;
+};
+
+// The transforms one enqueue covers: ptrs (device array of `count` data
+// pointers, or NULL for one transform at the enqueue's `data`) and their
+// state words (16 bytes per transform).
+struct Batch {
+  void* const* ptrs;
+  unsigned count;
+  uint32_t* state;
+};
+
+// A radix schedule (log2 R_0 .. log2 R_{np-1}).
+struct Tuned {
+  int np;
+  int r[kMaxPasses];
+};
+
+// Makes `dev` current for the guard's lifetime.
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = false;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) return;
+    ok = (prev == dev) || (cudaSetDevice(dev) == cudaSuccess);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+}  // namespace host
+}  // namespace efft
+
+struct efft_plan_s {
+  uint32_t magic;
+  int device;
+  uint64_t n;
+  int log2n;
+  int dtype;
+  int sign;
+  uint32_t flags;
+  int npasses;
+  efft::host::Pass pass[efft::host::kMaxPasses];
+  bool small;    // N <= 8: direct-sum kernel
+  bool permute;  // final digit swap enabled
+  int perm_log2A, perm_log2B;
+  int twB;
+  float4* w2048;
+  float4* tw_lo;
+  float4* tw_hi;
+  uint32_t* state;
+  uint64_t table_bytes;
+  // profiling: CUDA event pairs recorded around each launch
+  bool profiling;
+  struct Rec {
+    int slot;
+    cudaEvent_t a, b;
+  };
+  std::vector<Rec>* recs;
+  std::vector<cudaEvent_t>* pool;
+};
+
+namespace efft {
+namespace host {
+
+// Registry of live handles (plans here, batches in efft_batch.cu).
+std::mutex& registry_mutex();
+bool plan_is_live(efft_plan_s* p);
+// EFFT_FAULT_INJECT=<what>: host-side failure injection for tests.
+bool fault_injected(const char* what);
+int ilog2_u64(uint64_t n);
+
+// Schedules: the planner's table, the accepted set, and filling a plan's
+// pass table from a radix list.
+int choose_radices(int e, int* r);
+bool valid_schedule(int e, const int* r, int np);
+int schedule_candidates(int e, int (*r)[kMaxPasses], int* np);
+void apply_schedule(efft_plan_s* p, const int* r, int np);
+bool tuned_lookup(int dev, int e, int dtype, Tuned* t);
+void tuned_store(int dev, int e, int dtype, const Tuned& t);
+
+// A plan whose create arguments have been checked; r_explicit != NULL: the
+// caller's (validated) schedule.
+int plan_create_impl(efft_plan_t* out, uint64_t n, int dtype, int sign, uint32_t flags, const int* r_explicit,
+                     int np_explicit);
+// Times every accepted schedule on `scratch` and keeps the fastest.
+int autotune_impl(efft_plan_s* p, void* scratch, cudaStream_t st, int* cand_log2r, double* cand_ms, int cap,
+                  int* ncand);
+
+// Execution: buffer checks and the launch sequence of one transform or of a
+// batch of same-size transforms.
+int check_buffer(const efft_plan_s* p, const void* data);
+int enqueue_batch(efft_plan_s* p, void* data, const Batch& bt, cudaStream_t st);
+int enqueue(efft_plan_s* p, void* data, cudaStream_t st);
+
+}  // namespace host
+}  // namespace efft

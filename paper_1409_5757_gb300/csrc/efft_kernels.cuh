@@ -410,17 +410,23 @@ efft_pass_fx(void* __restrict__ data, const PassArgs a) {
   constexpr int NFULL = LR / 4, REM = LR % 4, NST = NFULL + (REM ? 1 : 0);
   constexpr int NMID = NST - 2;  // radix-16 stages between the first and the last
   constexpr bool STRIDED = (KIND == FIRST || KIND == MID);
-  // The last pass reads whole columns (C blocks of R contiguous elements):
-  // there t runs fastest across the threads so that global loads coalesce,
-  // and shared memory is column-major, raw index c*R + p.  The strided
-  // passes read C adjacent columns per row: c runs fastest, raw index
-  // p*C + c.  Either way slot = raw + raw/16 (one pad slot per 16).
-  constexpr bool CM = (KIND == LAST);
+  // Thread mapping: c runs fastest (a warp covers C columns x 32/C rows) and
+  // shared memory is row-major, raw index p*C + c.  The last pass reads C
+  // whole contiguous blocks: when a warp's run per column, 32/C elements,
+  // would fill less than a 32-byte sector, t runs fastest instead (coalesced
+  // loads) and shared memory is column-major, raw index c*R + p; its stage-0
+  // twiddles then differ per lane, so it is used only there.  Either way
+  // slot = raw + raw/16 (one pad slot per 16).
+  constexpr bool CM = (KIND == LAST) && ((32 / C) * P::kElemBytes < 32);
   constexpr int PS = CM ? 1 : C;  // raw step of one position p
   static_assert(LR >= 5 && LR <= 12, "radix range");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V* sm = reinterpret_cast<V*>(smem_raw);
   __shared__ typename P::TW vtw[STRIDED ? 16 * C : 1];
+  // column-major last pass: lanes hold different t, so the stage-0 twiddles
+  // exp(-2*pi*i*t*q/R) come from a shared copy of the R-th roots of unity
+  // (root k at k + k/8: lanes reading k = 8t or 4t stay on different banks)
+  __shared__ float4 wroot[CM ? R + R / 8 : 1];
   auto slot = [](int p, int col) {
     const int raw = CM ? (col << LR) + p : (p << LC) + col;
     return raw + (raw >> 4);
@@ -470,12 +476,17 @@ efft_pass_fx(void* __restrict__ data, const PassArgs a) {
 #pragma unroll
     for (int j = 0; j < 16; ++j) v[j] = Mem<P, KIND>::load(data, b0 + (uint64_t)j * sj, D, a.conj_in);
   }
+  if (CM) {
+    for (int k = tid; k < R; k += NT) wroot[k + (k >> 3)] = __ldg(a.w2048 + (k << (11 - LR)));
+    __syncthreads();
+  }
   dif_regs<P, 4>(v);
   {
     // exp(-2*pi*i * t*q / R), q = bitrev4(u), to positions t + TPC*q
 #pragma unroll
     for (int u = 1; u < 16; ++u)
-      v[u] = P::mul_tw(v[u], P::int_tw(a.w2048, nullptr, (uint32_t)(t * bitrev_c(u, 4)) << (11 - LR)));
+      v[u] = P::mul_tw(v[u], CM ? P::expand(wroot[t * bitrev_c(u, 4) + ((t * bitrev_c(u, 4)) >> 3)])
+                                : P::int_tw(a.w2048, nullptr, (uint32_t)(t * bitrev_c(u, 4)) << (11 - LR)));
     const int sb = slot(t, c);
 #pragma unroll
     for (int u = 0; u < 16; ++u) sm[sb + pad_off(bitrev_c(u, 4) * TPC * PS)] = v[u];
