@@ -4,8 +4,10 @@ TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and
 bench.py's cpu_baseline / reference legs import this package.  The product
 library (paper_1409_5757_gb300) never imports it and shares no code with it.
 
-All routines take and return numpy complex128 arrays (interleaved re, im),
-and compute X[k] = sum_n x[n] exp(sign*2*pi*i*n*k/N) with no normalisation.
+All complex routines take and return numpy complex128 arrays (interleaved
+re, im), and compute X[k] = sum_n x[n] exp(sign*2*pi*i*n*k/N) with no
+normalisation.  The real-data routines (rdft_perm, irdft_perm) apply the
+complex DFT to real data and pack / unpack the perm layout of Eq. 3.
 """
 from __future__ import annotations
 
@@ -124,6 +126,46 @@ class Oracle:
         if rc:
             raise ValueError(f"oracle_dft_bins failed ({rc})")
         return X
+
+
+    # -- real data (the perm layout of Eq. 3, Sec. 2.1) ----------------------
+    @staticmethod
+    def pack_perm(X) -> np.ndarray:
+        """The perm layout of Eq. 3 for the spectrum X[0..N) of real data:
+        {R_0, R_{N/2}, R_1, I_1, ..., R_{N/2-1}, I_{N/2-1}} (N reals);
+        X[k] for k > N/2 follows from the symmetry X[N-k] = conj(X[k])."""
+        X = np.asarray(X, dtype=np.complex128)
+        N = X.size
+        out = np.empty(N, dtype=np.float64)
+        out[0] = X[0].real
+        out[1] = X[N // 2].real
+        out[2::2] = X[1:N // 2].real
+        out[3::2] = X[1:N // 2].imag
+        return out
+
+    @staticmethod
+    def unpack_perm(p) -> np.ndarray:
+        """Inverse of pack_perm: the full Hermitian spectrum F[0..N) of a
+        perm array (F[N-k] = conj(F[k]); F[0], F[N/2] real)."""
+        p = np.asarray(p, dtype=np.float64)
+        N = p.size
+        F = np.empty(N, dtype=np.complex128)
+        F[0] = p[0]
+        F[N // 2] = p[1]
+        F[1:N // 2] = p[2::2] + 1j * p[3::2]
+        F[N // 2 + 1:] = np.conj(F[1:N // 2][::-1])
+        return F
+
+    def rdft_perm(self, x, sign: int = -1) -> np.ndarray:
+        """Eq. 1 for real x (N a power of two >= 2), packed by pack_perm."""
+        x = np.asarray(x, dtype=np.float64)
+        return self.pack_perm(self.dft(x.astype(np.complex128), sign))
+
+    def irdft_perm(self, p, sign: int = +1) -> np.ndarray:
+        """x[n] = sum_k F[k] exp(sign*2*pi*i*n*k/N) over the Hermitian
+        spectrum of the perm array p (a real result; unnormalised, so that
+        irdft_perm(rdft_perm(x)) = N x)."""
+        return self.dft(self.unpack_perm(p), sign).real.copy()
 
 
 def rel_l2(F, Fe) -> float:

@@ -290,4 +290,63 @@ def pin_bins_tone(o):
     assert np.max(np.abs(X[1:])) <= 1e-10 * N
 
 
+# --------------------------------------------------------------------------
+# Real data: the perm layout of Eq. 3 (Sec. 2.1)
+# --------------------------------------------------------------------------
+def pin_real_perm_closed_forms(o):
+    """Closed forms of Eq. 1 for real inputs, read through the perm layout
+    {R_0, R_{N/2}, R_1, I_1, ..., R_{N/2-1}, I_{N/2-1}}:
+    cos(2 pi f n / N) -> R_f = N/2; sin(2 pi f n / N) -> I_f = -N/2 (sign -1);
+    delta_0 -> every R_k = 1, I_k = 0; a constant c -> R_0 = N c;
+    (-1)^n -> R_{N/2} = N."""
+    for N in (2, 4, 8, 64, 1024, 8192):
+        n = np.arange(N)
+        tol = 1e-12 * N
+        for f in range(1, N // 2):
+            if f > 5 and f < N // 2 - 3:
+                continue
+            want = np.zeros(N)
+            want[2 * f] = N / 2
+            assert np.max(np.abs(o.rdft_perm(np.cos(2 * np.pi * f * n / N)) - want)) <= tol, (N, f, "cos")
+            want = np.zeros(N)
+            want[2 * f + 1] = -N / 2
+            assert np.max(np.abs(o.rdft_perm(np.sin(2 * np.pi * f * n / N)) - want)) <= tol, (N, f, "sin")
+        d = np.zeros(N)
+        d[0] = 1
+        want = np.zeros(N)
+        want[0] = want[1] = 1
+        want[2::2] = 1
+        assert np.max(np.abs(o.rdft_perm(d) - want)) <= tol, (N, "delta")
+        want = np.zeros(N)
+        want[0] = 0.75 * N
+        assert np.max(np.abs(o.rdft_perm(np.full(N, 0.75)) - want)) <= tol, (N, "constant")
+        want = np.zeros(N)
+        want[1] = N
+        assert np.max(np.abs(o.rdft_perm((-1.0) ** n) - want)) <= tol, (N, "alternating")
+
+
+def pin_real_perm_brute_force(o):
+    """mpmath's Eq. 1 on random real inputs, packed by hand into Eq. 3."""
+    for N, seed in ((2, 1), (4, 2), (8, 3), (16, 4), (32, 5)):
+        x = _rng(seed).uniform(-1, 1, N)
+        X = _mp_dft(x, -1)
+        want = [X[0].real, X[N // 2].real]
+        for k in range(1, N // 2):
+            want += [X[k].real, X[k].imag]
+        assert np.max(np.abs(o.rdft_perm(x) - np.array(want))) <= 1e-14 * N, N
+
+
+def pin_real_perm_round_trip(o):
+    """irdft_perm(rdft_perm(x)) = N x, and the conjugate-sign inverse of a
+    perm spectrum equals numpy's irfft of the same spectrum times N."""
+    for N in (2, 4, 16, 256, 4096, 1 << 14):
+        x = _rng(N).uniform(-1, 1, N)
+        assert _rel(o.irdft_perm(o.rdft_perm(x)), N * x) <= 1e-14 * np.log2(N) + 1e-16, N
+        p = _rng(N + 1).uniform(-1, 1, N)
+        F = np.empty(N // 2 + 1, np.complex128)
+        F[0], F[N // 2] = p[0], p[1]
+        F[1:N // 2] = p[2::2] + 1j * p[3::2]
+        assert _rel(o.irdft_perm(p), N * np.fft.irfft(F, n=N)) <= 1e-13, N
+
+
 ALL_PINS = [v for k, v in sorted(globals().items()) if k.startswith("pin_")]

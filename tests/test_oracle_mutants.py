@@ -8,6 +8,7 @@ or truncated sampled-mode twiddle, a mis-reduced octant or quadrant).
 The mutants are built into a temporary directory; the shipped library is
 always built with ORACLE_MUTANT=0.
 """
+import numpy as np
 import pytest
 
 import oracle
@@ -32,3 +33,48 @@ def test_mutant_is_caught(mutant, tmp_path):
 
 def test_real_oracle_is_not_a_mutant(orc):
     assert orc._lib.oracle_mutant() == 0
+
+
+# Planted mistakes in the oracle's perm packing (Eq. 3), on the CPU: each
+# replaces the packing or unpacking routine of a fresh oracle object.
+def _pack_swapped_ends(X):
+    out = oracle.Oracle.pack_perm(X)
+    out[[0, 1]] = out[[1, 0]]          # R_{N/2} first
+    return out
+
+
+def _pack_conjugated(X):
+    out = oracle.Oracle.pack_perm(X)
+    out[3::2] = -out[3::2]             # I_k of the conjugate spectrum
+    return out
+
+
+def _pack_shifted(X):
+    X = np.asarray(X, np.complex128)
+    return oracle.Oracle.pack_perm(np.roll(X, -1))  # off by one bin
+
+
+def _unpack_mirror_off_by_one(p):
+    F = oracle.Oracle.unpack_perm(p)
+    N = F.size
+    F[N // 2 + 1:] = np.conj(F[:N // 2 - 1][::-1])  # F[N-k] from F[k-1]
+    return F
+
+
+@pytest.mark.parametrize("mistake", [("pack_perm", _pack_swapped_ends), ("pack_perm", _pack_conjugated),
+                                     ("pack_perm", _pack_shifted), ("unpack_perm", _unpack_mirror_off_by_one)],
+                         ids=["swapped-ends", "conjugated", "shifted", "mirror-off-by-one"])
+def test_perm_mistake_is_caught(orc, mistake):
+    name, fn = mistake
+    o = oracle.Oracle()
+    setattr(o, name, fn)
+    caught = False
+    for pin in ALL_PINS:
+        if "real" not in pin.__name__:
+            continue
+        try:
+            pin(o)
+        except AssertionError:
+            caught = True
+            break
+    assert caught, f"perm mistake {fn.__name__} passed every real-data pin"
