@@ -1,7 +1,7 @@
 #!/usr/bin/env python3
 """Throughput of the in-place 1-D complex DFT on GB300.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload c2|c3|c1|c4|c5]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload c2|c3|c1|c4|c5|r1]
                     [--impl ours|reference]
 
 Default workload (the headline configuration): one step = a forward DFT
@@ -51,6 +51,9 @@ WORKLOADS = {
                desc="complex128 N=2^20 in place, one transform per step; uniform[-1,1) re/im"),
     "c4": dict(log2n=31, dtype="c64", seed=4, tones=0, fwd_inv=False, gauss=True,
                desc="complex64 N=2^31 in place, one transform per step; Gaussian(0,1) re/im"),
+    "r1": dict(log2n=31, real=True, dtype="c64", seed=6, tones=0, fwd_inv=True, gauss=False,
+               desc="real float32 N=2^32 reals (16 GiB) in place, forward to the perm layout (Eq. 3) then the "
+                    "normalised inverse; uniform[-1,1); GFLOP/s by the real-data count (5/2) N log2 N (Eq. 7)"),
     "c5": dict(batch=256, emin=12, emax=24, log2n=24, dtype="c64", seed=5, tones=0, fwd_inv=True, gauss=False,
                autotune=True,
                desc="256 complex64 transforms in place, N_i = 2^e_i with e_i uniform in {12..24} (seed 5), "
@@ -58,10 +61,16 @@ WORKLOADS = {
                     "radix schedules from the autotuner; uniform[-1,1) re/im"),
 }
 DTYPE_NAME = {"c128": "df32 (double-float f32 pairs; complex128 in/out)", "c64": "f32 (complex64)"}
+DTYPE_NAME_REAL = {"c128": "df32 (double-float f32 pairs; float64 in/out)", "c64": "f32 (float32 reals)"}
 
 
 def flops(n: int) -> float:
     return 5.0 * n * math.log2(n)
+
+
+def flops_real(n: int) -> float:
+    """The paper's count for n real points (Eq. 7)."""
+    return 2.5 * n * math.log2(n)
 
 
 def max_over_ranks(value: float, device=None) -> float:
@@ -75,9 +84,11 @@ def max_over_ranks(value: float, device=None) -> float:
     return float(t.item())
 
 
-def job_rate(world: int, transforms_per_step: int, n: int, ms_per_step: float) -> float:
-    """Whole-job GFLOP/s: every rank transforms its own array (replicas)."""
-    return world * transforms_per_step * flops(n) / (ms_per_step * 1e-3) / 1e9
+def job_rate(world: int, transforms_per_step: int, n: int, ms_per_step: float, real: bool = False) -> float:
+    """Whole-job GFLOP/s: every rank transforms its own array (replicas);
+    n complex points, or for real data 2n reals."""
+    f = flops_real(2 * n) if real else flops(n)
+    return world * transforms_per_step * f / (ms_per_step * 1e-3) / 1e9
 
 
 def kernel_fingerprint() -> str:
@@ -324,6 +335,12 @@ def config_of(wl):
                 else "complex128", "transforms_per_step": 2 * len(es), "in_place": True,
                 "l2_between_steps": "inputs larger than L2 (no flush needed)", "seed": wl["seed"],
                 "parallelism": "replicas only (one batch per GPU)"}
+    if wl.get("real"):
+        return {"workload": wl["desc"], "N_reals": 2 << wl["log2n"], "log2N": wl["log2n"] + 1,
+                "element": "float32" if wl["dtype"] == "c64" else "float64", "layout": "perm (Eq. 3)",
+                "transforms_per_step": 2 if wl["fwd_inv"] else 1, "in_place": True,
+                "l2_between_steps": "inputs larger than L2 (no flush needed)",
+                "seed": wl["seed"], "parallelism": "replicas only (one transform per GPU)"}
     return {"workload": wl["desc"], "N": 1 << wl["log2n"], "log2N": wl["log2n"],
             "element": "complex128" if wl["dtype"] == "c128" else "complex64",
             "transforms_per_step": 2 if wl["fwd_inv"] else 1, "in_place": True,
@@ -377,8 +394,15 @@ def run_ours(args, wl):
         keep = x.clone()  # for the round-trip accuracy check after timing
 
     tune = efft.EFFT_FLAG_AUTOTUNE if args.autotune else 0
-    fwd = efft.Plan(N, code, -1, tune)
-    inv = efft.Plan(N, code, +1, efft.EFFT_FLAG_NORMALIZE | tune)
+    real = bool(wl.get("real"))
+    if real:
+        # x holds 2N reals (the same bytes as N complex values)
+        fwd = efft.Plan.real(2 * N, code, efft.EFFT_REAL_FORWARD, tune)
+        inv = efft.Plan.real(2 * N, code, efft.EFFT_REAL_INVERSE, efft.EFFT_FLAG_NORMALIZE | tune)
+    else:
+        fwd = efft.Plan(N, code, -1, tune)
+        inv = efft.Plan(N, code, +1, efft.EFFT_FLAG_NORMALIZE | tune)
+    fpt = flops_real(2 * N) if real else flops(N)  # flop per transform
     stream = torch.cuda.current_stream(dev)
     sp = stream.cuda_stream
     tps = 2 if wl["fwd_inv"] else 1
@@ -430,7 +454,7 @@ def run_ours(args, wl):
 
     elapsed_ms = max_over_ranks(elapsed_ms, dev)
     ms_per_step = elapsed_ms / K
-    value = job_rate(world, tps, N, ms_per_step)
+    value = job_rate(world, tps, N, ms_per_step, real)
     hbm_passes = fwd.info()["hbm_passes"]
     hbm_gbs = world * tps * hbm_passes * 2 * N * S / (ms_per_step * 1e-3) / 1e9
 
@@ -471,7 +495,7 @@ def run_ours(args, wl):
 
     # the FP32 form against the FP64 form at the same N (complex64 workloads)
     same_n_c128 = None
-    if not c128 and N * 16 <= (64 << 30) and not args.no_compare:
+    if not c128 and not real and N * 16 <= (64 << 30) and not args.no_compare:
         del keep
         keep = None
         y = torch.empty(N, dtype=torch.complex128, device=dev)
@@ -515,7 +539,7 @@ def run_ours(args, wl):
         hin.free()
         hout.free()
         tps_e2e = len(chain)
-        e2e = {"value": world * tps_e2e * flops(N) / dt / 1e9, "unit": "GFLOP/s",
+        e2e = {"value": world * tps_e2e * fpt / dt / 1e9, "unit": "GFLOP/s",
                "h2d_bytes_per_step": N * S, "d2h_bytes_per_step": N * S,
                "ms_per_step": dt * 1e3, "steps": Ke,
                "api": "efft_execute_host_stream (cudaHostAlloc host buffers, 3 device buffers, "
@@ -530,7 +554,10 @@ def run_ours(args, wl):
         e = wl["log2n"] if wl["log2n"] <= 30 else 30
         e = min(e, oracle_sample_log2n(25.0, e))
         dt, cores = oracle_time(e, wl["seed"])
-        cpu = {"value": flops(1 << e) / dt / 1e9, "unit": "GFLOP/s", "cores": cores, "kind": "oracle",
+        # real data: the oracle transforms 2^e reals by a 2^e-point complex FFT,
+        # i.e. the same time as this complex sample, counted by Eq. 7
+        cval = (flops_real(1 << e) if real else flops(1 << e)) / dt / 1e9
+        cpu = {"value": cval, "unit": "GFLOP/s", "cores": cores, "kind": "oracle",
                "sample": f"one forward FP64 radix-2 oracle transform of N=2^{e} (same seeded uniform input "
                          f"family) on the host cores, {dt:.1f} s",
                "nproc": os.cpu_count(), "cpu_model": cpu_model(),
@@ -540,7 +567,8 @@ def run_ours(args, wl):
         line = {
             "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": K, "warmup": W,
             "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": DTYPE_NAME[wl["dtype"]], "data": "synthetic", "config": config_of(wl),
+            "dtype": (DTYPE_NAME_REAL if real else DTYPE_NAME)[wl["dtype"]], "data": "synthetic",
+            "config": config_of(wl),
             "hbm_gbs": hbm_gbs, "hbm_passes_per_transform": hbm_passes, "floor_equivalent_gbs": floor_gbs,
             "radices_log2": fwd.radices(),
             "fp64_form_same_n": same_n_c128,
@@ -721,7 +749,7 @@ def main():
         wl["log2n"] = args.log2n
         wl["desc"] = wl["desc"].replace("2^30", f"2^{args.log2n}").replace("2^33", f"2^{args.log2n}")
     if args.steps is None:
-        args.steps = {"c2": 20, "c3": 6, "c1": 200, "c4": 40, "c5": 40}[args.workload]
+        args.steps = {"c2": 20, "c3": 6, "c1": 200, "c4": 40, "c5": 40, "r1": 20}[args.workload]
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
     if args.impl == "reference":

@@ -222,14 +222,45 @@ int efft_plan_info(efft_plan_t plan, double* hbm_passes, uint64_t* table_bytes);
  *  efft_plan_profile_read synchronises on the recorded events and writes, per
  *    launch slot s < cap, total milliseconds ms[s] and launch count count[s];
  *    *nslots receives EFFT_PROFILE_SLOTS.  Slots: 0 range scan (complex128),
- *    1 + j pass j (j < 4), 5 digit swap, 6 direct-sum kernel (N <= 8).
+ *    1 + j pass j (j < 4), 5 digit swap, 6 direct-sum kernel (N <= 8),
+ *    7 mirrored-pair kernel of a real-data plan.
  *    Records are consumed by the read.
  * Profiling mutates the plan: do not profile a plan that other host threads
  * execute concurrently.
  */
-#define EFFT_PROFILE_SLOTS 7
+#define EFFT_PROFILE_SLOTS 8
 int efft_plan_profile(efft_plan_t plan, int enable);
 int efft_plan_profile_read(efft_plan_t plan, double* ms, int* count, int cap, int* nslots);
+
+/*
+ * Real-data transforms: the paper's real-input form (Sec. 2.1, the packed
+ * "perm" layout of Eq. 3) with its in-place pairing of mirrored elements
+ * (Sec. 3.4).  The N reals are viewed as N/2 complex values
+ * z[m] = x[2m] + i x[2m+1]; a complex plan of N/2 points transforms them and
+ * one more in-place sweep combines each mirrored pair (k, N/2 - k), so that
+ * a real transform costs about half a complex one of the same N.
+ *  direction  EFFT_REAL_FORWARD: x[0..N) real in place -> the perm layout
+ *               {R_0, R_{N/2}, R_1, I_1, ..., R_{N/2-1}, I_{N/2-1}} of
+ *               F[k] = R_k + i I_k = sum_n x[n] exp(-2*pi*i*n*k/N), 0 <= k <= N/2
+ *               (F[k] for k > N/2 is conj(F[N-k]));
+ *             EFFT_REAL_INVERSE: a perm array in place ->
+ *               x[n] = sum_{k<N} F[k] exp(+2*pi*i*n*k/N) over the Hermitian
+ *               spectrum (F[N-k] = conj F[k]), a real result: N times the
+ *               original data, or the original data with EFFT_FLAG_NORMALIZE.
+ *  precision  EFFT_C64: float32 reals (4 bytes each); EFFT_C128: float64.
+ *  n          number of reals, a power of two, 2 <= n <= 2^(EFFT_MAX_LOG2N+1).
+ *  flags      EFFT_FLAG_NORMALIZE (multiply by 1/N), EFFT_FLAG_AUTOTUNE (for
+ *             the complex plan); EFFT_FLAG_DIGIT_REVERSED_OUT is rejected.
+ * The plan is executed with efft_execute / efft_execute_host /
+ * efft_execute_host_stream like a complex plan (data: n reals, aligned to
+ * two reals); efft_plan_radices reports the complex plan's radices and
+ * efft_plan_autotune tunes it; batches take complex plans only.
+ * Errors: as efft_plan_create (INVALID_SIZE for n < 2), INVALID_SIGN for
+ * another direction, INVALID_FLAGS.
+ */
+#define EFFT_REAL_FORWARD (-1)
+#define EFFT_REAL_INVERSE (+1)
+int efft_plan_create_real(efft_plan_t* out, uint64_t n, int precision, int direction, uint32_t flags);
 
 /*
  * One transform that allocates nothing (the paper has no counterpart; this

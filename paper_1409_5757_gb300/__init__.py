@@ -26,7 +26,9 @@ EFFT_FLAG_DIGIT_REVERSED_OUT = 0x1
 EFFT_FLAG_NORMALIZE = 0x2
 EFFT_FLAG_AUTOTUNE = 0x4
 EFFT_BATCH_INFLIGHT = 4
-PROFILE_SLOTS = ("range_scan", "pass0", "pass1", "pass2", "pass3", "digit_swap", "direct_small")
+EFFT_REAL_FORWARD = -1
+EFFT_REAL_INVERSE = +1
+PROFILE_SLOTS = ("range_scan", "pass0", "pass1", "pass2", "pass3", "digit_swap", "direct_small", "real_pair")
 EFFT_MAX_LOG2N = 33
 
 STATUS = {
@@ -65,6 +67,8 @@ _SIGNATURES = {
     "efft_batch_execute": (ctypes.c_int, [_vp, ctypes.POINTER(_vp), _vp]),
     "efft_batch_info": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     "efft_batch_destroy": (ctypes.c_int, [_vp]),
+    "efft_plan_create_real": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_uint64, ctypes.c_int, ctypes.c_int,
+                                             ctypes.c_uint32]),
 }
 
 
@@ -125,6 +129,18 @@ class Plan:
                                                         int(flags), r, len(radices)),
                    "efft_plan_create_with_radices")
         self.n, self.dtype, self.sign, self.flags = int(n), int(dtype), int(sign), int(flags)
+
+    @classmethod
+    def real(cls, n: int, precision: int = EFFT_C128, direction: int = EFFT_REAL_FORWARD, flags: int = 0):
+        """Real-data plan (efft_plan_create_real): n reals <-> the perm layout
+        {R_0, R_{N/2}, R_1, I_1, ...}; precision EFFT_C64 (float32 data) or
+        EFFT_C128 (float64)."""
+        self = cls.__new__(cls)
+        self._h = _vp()
+        _check(_lib().efft_plan_create_real(ctypes.byref(self._h), int(n), int(precision), int(direction),
+                                            int(flags)), "efft_plan_create_real")
+        self.n, self.dtype, self.sign, self.flags = int(n), int(precision), int(direction), int(flags)
+        return self
 
     @property
     def handle(self):
@@ -273,6 +289,9 @@ def clear_plans() -> None:
         for b in _BATCHES.values():
             b.destroy()
         _BATCHES.clear()
+        for p in _RPLANS.values():
+            p.destroy()
+        _RPLANS.clear()
 
 
 def _dtype_code(t) -> int:
@@ -322,6 +341,48 @@ def fft_batch_(tensors, sign: int = -1, flags: int = 0, stream=None):
     return tensors
 
 
+_RPLANS: dict = {}
+
+
+def _real_code(t) -> int:
+    import torch
+    if t.dtype == torch.float64:
+        return EFFT_C128
+    if t.dtype == torch.float32:
+        return EFFT_C64
+    raise TypeError(f"efft: unsupported real dtype {t.dtype} (float32 or float64)")
+
+
+def _real_execute(t, direction: int, flags: int, stream):
+    import torch
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("efft: real transforms take a contiguous CUDA tensor")
+    code = _real_code(t)
+    with torch.cuda.device(t.device):
+        key = (torch.cuda.current_device(), t.numel(), code, direction, int(flags))
+        with _PLANS_LOCK:
+            p = _RPLANS.get(key)
+            if p is None:
+                p = Plan.real(t.numel(), code, direction, flags)
+                _RPLANS[key] = p
+        s = stream if stream is not None else torch.cuda.current_stream(t.device)
+        p.execute(t.data_ptr(), s.cuda_stream)
+    return t
+
+
+def rfft_(t, flags: int = 0, stream=None):
+    """In-place real-data DFT of a contiguous 1-D CUDA float32/float64 tensor
+    of N = 2^e reals: afterwards t holds the perm layout
+    {R_0, R_{N/2}, R_1, I_1, ..., R_{N/2-1}, I_{N/2-1}} (Eq. 3)."""
+    return _real_execute(t, EFFT_REAL_FORWARD, flags, stream)
+
+
+def irfft_(t, normalize: bool = True, stream=None):
+    """In place, the inverse of rfft_: a perm array back to N reals
+    (divided by N when normalize, else N times the original data)."""
+    return _real_execute(t, EFFT_REAL_INVERSE, EFFT_FLAG_NORMALIZE if normalize else 0, stream)
+
+
 def fft(t, sign: int = -1):
     """Out-of-place convenience: clone then fft_."""
     return fft_(t.clone(), sign)
@@ -331,6 +392,7 @@ def version() -> int:
     return _lib().efft_version()
 
 
-__all__ = ["Plan", "Batch", "EfftError", "fft_", "fft", "fft_batch_", "get_plan", "get_batch", "clear_plans", "version",
+__all__ = ["Plan", "Batch", "EfftError", "fft_", "fft", "fft_batch_", "rfft_", "irfft_", "get_plan", "get_batch",
+           "clear_plans", "version", "EFFT_REAL_FORWARD", "EFFT_REAL_INVERSE",
            "lib_path", "execute_host_stream", "EFFT_C64", "EFFT_C128", "EFFT_FLAG_DIGIT_REVERSED_OUT",
            "EFFT_FLAG_NORMALIZE", "EFFT_FLAG_AUTOTUNE"]

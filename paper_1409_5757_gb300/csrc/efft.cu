@@ -92,6 +92,12 @@ bool plan_is_live(efft_plan_s* p) {
   return g_live && g_live->count(p) && p->magic == kMagic;
 }
 
+void register_plan(efft_plan_s* p) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (!g_live) g_live = new std::set<efft_plan_s*>();
+  g_live->insert(p);
+}
+
 bool fault_injected(const char* what) {
   const char* v = std::getenv("EFFT_FAULT_INJECT");
   return v && std::strcmp(v, what) == 0;
@@ -231,8 +237,12 @@ void free_plan_memory(efft_plan_s* p) {
   if (p->tw_lo) cudaFree(p->tw_lo);
   if (p->tw_hi) cudaFree(p->tw_hi);
   if (p->state) cudaFree(p->state);
-  p->w2048 = p->tw_lo = p->tw_hi = nullptr;
+  if (p->rtw_lo) cudaFree(p->rtw_lo);
+  if (p->rtw_hi) cudaFree(p->rtw_hi);
+  if (p->inner) efft_plan_destroy(p->inner);
+  p->w2048 = p->tw_lo = p->tw_hi = p->rtw_lo = p->rtw_hi = nullptr;
   p->state = nullptr;
+  p->inner = nullptr;
 }
 
 cudaEvent_t take_event(efft_plan_s* p) {
@@ -413,11 +423,7 @@ int plan_create_impl(efft_plan_t* out, uint64_t n, int dtype, int sign, uint32_t
   }
   p->table_bytes = (2048 + nlo + nhi) * sizeof(float4) + 16;
   p->magic = kMagic;
-  {
-    std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_live) g_live = new std::set<efft_plan_s*>();
-    g_live->insert(p);
-  }
+  register_plan(p);
   *out = p;
   return EFFT_OK;
 }
@@ -471,6 +477,7 @@ int efft_plan_destroy(efft_plan_t plan) {
 
 int efft_plan_radices(efft_plan_t plan, int* log2_radices, int cap, int* npasses) {
   if (!plan_is_live(plan)) return EFFT_ERR_INVALID_PLAN;
+  if (plan->real) plan = plan->inner;  // the complex plan of n/2 points
   if (npasses) *npasses = plan->npasses;
   if (log2_radices)
     for (int j = 0; j < plan->npasses && j < cap; ++j) log2_radices[j] = plan->pass[j].log2R;
@@ -479,6 +486,16 @@ int efft_plan_radices(efft_plan_t plan, int* log2_radices, int cap, int* npasses
 
 int efft_plan_info(efft_plan_t plan, double* hbm_passes, uint64_t* table_bytes) {
   if (!plan_is_live(plan)) return EFFT_ERR_INVALID_PLAN;
+  if (plan->real) {
+    // the complex plan's sweeps of the same bytes, the mirrored-pair sweep,
+    // and for an inverse complex128 plan the range scan ahead of it
+    double hp = 0.0;
+    uint64_t tb = 0;
+    efft_plan_info(plan->inner, &hp, &tb);
+    if (hbm_passes) *hbm_passes = hp + 1.0 + ((plan->dtype == EFFT_C128 && plan->real > 0) ? 0.5 : 0.0);
+    if (table_bytes) *table_bytes = tb + plan->table_bytes;
+    return EFFT_OK;
+  }
   if (hbm_passes) {
     double hp = plan->npasses + (plan->permute ? 1.0 : 0.0);
     if (plan->small) hp = 1.0;
@@ -493,6 +510,24 @@ int efft_plan_info(efft_plan_t plan, double* hbm_passes, uint64_t* table_bytes) 
 
 namespace efft {
 namespace host {
+
+size_t plan_bytes(const efft_plan_s* p) {
+  const size_t s = (p->dtype == EFFT_C128) ? 16 : 8;
+  return p->n * (p->real ? s / 2 : s);
+}
+
+// Clears the state words and enqueues the range scan of `count` arrays of
+// n_complex complex128 values (data, or ptrs[0..count) when ptrs != NULL).
+int launch_range_scan(const void* data, uint64_t n_complex, uint32_t* state, void* const* ptrs, unsigned count,
+                      cudaStream_t st) {
+  if (cudaMemsetAsync(state, 0, 16 * (size_t)count, st) != cudaSuccess) return EFFT_ERR_LAUNCH;
+  uint64_t blocks = (n_complex + 1023) / 1024;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  if (ptrs && blocks * count > 152 * 16) blocks = (152 * 16 + count - 1) / count;
+  efft_range_scan<<<dim3((unsigned)blocks, count), 256, 0, st>>>(reinterpret_cast<const uint4*>(data), n_complex,
+                                                                 state, ptrs);
+  return cudaGetLastError() == cudaSuccess ? EFFT_OK : EFFT_ERR_LAUNCH;
+}
 
 int check_buffer(const efft_plan_s* p, const void* data) {
   if (!data) return EFFT_ERR_INVALID_PTR;
@@ -515,15 +550,10 @@ int enqueue_batch(efft_plan_s* p, void* data, const Batch& bt, cudaStream_t st) 
   if (p->log2n == 0 || bt.count == 0) return EFFT_OK;  // N = 1: the DFT is the identity
   const bool c128 = (p->dtype == EFFT_C128);
   if (c128) {
-    if (cudaMemsetAsync(bt.state, 0, 16 * (size_t)bt.count, st) != cudaSuccess) return EFFT_ERR_LAUNCH;
-    uint64_t blocks = (p->n + 1023) / 1024;
-    if (blocks > 152 * 8) blocks = 152 * 8;
-    if (bt.ptrs && blocks * bt.count > 152 * 16) blocks = (152 * 16 + bt.count - 1) / bt.count;
     int rec = prof_begin(p, 0, st);
-    efft_range_scan<<<dim3((unsigned)blocks, bt.count), 256, 0, st>>>(reinterpret_cast<const uint4*>(data), p->n,
-                                                                   bt.state, bt.ptrs);
+    const int rc = launch_range_scan(data, p->n, bt.state, bt.ptrs, bt.count, st);
     prof_end(p, rec, st);
-    if (cudaGetLastError() != cudaSuccess) return EFFT_ERR_LAUNCH;
+    if (rc != EFFT_OK) return rc;
   }
   if (p->small) {
     PassArgs a;
@@ -566,6 +596,7 @@ int enqueue_batch(efft_plan_s* p, void* data, const Batch& bt, cudaStream_t st) 
 }
 
 int enqueue(efft_plan_s* p, void* data, cudaStream_t st) {
+  if (p->real) return enqueue_real(p, data, st);
   const Batch one{nullptr, 1u, p->state};
   return enqueue_batch(p, data, one, st);
 }
@@ -592,7 +623,7 @@ int efft_execute_host(efft_plan_t plan, void* host_data, void* dev_data, void* s
   int rc = check_buffer(plan, dev_data);
   if (rc != EFFT_OK) return rc;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  const size_t bytes = plan->n * ((plan->dtype == EFFT_C128) ? 16 : 8);
+  const size_t bytes = plan_bytes(plan);
   if (cudaMemcpyAsync(dev_data, host_data, bytes, cudaMemcpyHostToDevice, st) != cudaSuccess) {
     cudaGetLastError();
     return EFFT_ERR_CUDA;
@@ -616,7 +647,7 @@ int efft_execute_host_stream(const efft_plan_t* plans, int nplans, void* const* 
   if (!plans || nplans < 1 || nbufs < 1 || count < 0) return EFFT_ERR_INVALID_SIZE;
   for (int j = 0; j < nplans; ++j) {
     if (!plan_is_live(plans[j])) return EFFT_ERR_INVALID_PLAN;
-    if (plans[j]->n != plans[0]->n || plans[j]->dtype != plans[0]->dtype ||
+    if (plan_bytes(plans[j]) != plan_bytes(plans[0]) || plans[j]->dtype != plans[0]->dtype ||
         plans[j]->device != plans[0]->device)
       return EFFT_ERR_INVALID_SIZE;
   }
@@ -631,7 +662,7 @@ int efft_execute_host_stream(const efft_plan_t* plans, int nplans, void* const* 
     int rc = check_buffer(p0, dev_bufs[b]);
     if (rc != EFFT_OK) return rc;
   }
-  const size_t bytes = p0->n * ((p0->dtype == EFFT_C128) ? 16 : 8);
+  const size_t bytes = plan_bytes(p0);
   cudaStream_t sc = reinterpret_cast<cudaStream_t>(stream);
   cudaStream_t sin = nullptr, sout = nullptr;
   std::vector<cudaEvent_t> ev_in(nbufs, nullptr), ev_comp(nbufs, nullptr), ev_out(nbufs, nullptr);
@@ -693,6 +724,7 @@ int efft_execute_host_stream(const efft_plan_t* plans, int nplans, void* const* 
 
 int efft_plan_profile(efft_plan_t plan, int enable) {
   if (!plan_is_live(plan)) return EFFT_ERR_INVALID_PLAN;
+  if (plan->real) efft_plan_profile(plan->inner, enable);
   DeviceGuard g(plan->device);
   if (enable) {
     for (auto& r : *plan->recs) cudaEventSynchronize(r.b);
@@ -708,6 +740,15 @@ int efft_plan_profile_read(efft_plan_t plan, double* ms, int* count, int cap, in
   double tot[EFFT_PROFILE_SLOTS] = {0};
   int cnt[EFFT_PROFILE_SLOTS] = {0};
   int rc = EFFT_OK;
+  if (plan->real) {  // the complex plan's launches, then this plan's own
+    double ims[EFFT_PROFILE_SLOTS] = {0};
+    int icnt[EFFT_PROFILE_SLOTS] = {0};
+    rc = efft_plan_profile_read(plan->inner, ims, icnt, EFFT_PROFILE_SLOTS, nullptr);
+    for (int s = 0; s < EFFT_PROFILE_SLOTS; ++s) {
+      tot[s] += ims[s];
+      cnt[s] += icnt[s];
+    }
+  }
   for (auto& r : *plan->recs) {
     float t = 0.f;
     if (cudaEventSynchronize(r.b) != cudaSuccess || cudaEventElapsedTime(&t, r.a, r.b) != cudaSuccess) {

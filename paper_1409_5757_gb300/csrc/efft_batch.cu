@@ -205,7 +205,7 @@ int efft_batch_execute(efft_batch_t b, void* const* data, void* stream) {
     int rc = check_buffer(p, data[i]);
     if (rc != EFFT_OK) return rc;
     const uintptr_t a = reinterpret_cast<uintptr_t>(data[i]);
-    spans[i] = {a, a + p->n * ((p->dtype == EFFT_C128) ? 16 : 8)};
+    spans[i] = {a, a + plan_bytes(p)};
   }
   std::sort(spans.begin(), spans.end());
   for (int i = 1; i < b->count; ++i)

@@ -90,6 +90,13 @@ struct efft_plan_s {
   };
   std::vector<Rec>* recs;
   std::vector<cudaEvent_t>* pool;
+  // real-data plans (efft_plan_create_real): n reals; the complex work is
+  // done by `inner` (n/2 points), the mirrored pairs by efft_real_pairs
+  int real;              // 0 complex plan, EFFT_REAL_FORWARD or EFFT_REAL_INVERSE
+  efft_plan_s* inner;
+  float4* rtw_lo;        // exp(-2*pi*i*t/n), t < 2^rtwB
+  float4* rtw_hi;        // exp(-2*pi*i*(t << rtwB)/n), t < (n/2) >> rtwB
+  int rtwB;
 };
 
 namespace efft {
@@ -98,6 +105,7 @@ namespace host {
 // Registry of live handles (plans here, batches in efft_batch.cu).
 std::mutex& registry_mutex();
 bool plan_is_live(efft_plan_s* p);
+void register_plan(efft_plan_s* p);
 // EFFT_FAULT_INJECT=<what>: host-side failure injection for tests.
 bool fault_injected(const char* what);
 int ilog2_u64(uint64_t n);
@@ -122,6 +130,17 @@ int autotune_impl(efft_plan_s* p, void* scratch, cudaStream_t st, int* cand_log2
 // Execution: buffer checks and the launch sequence of one transform or of a
 // batch of same-size transforms.
 int check_buffer(const efft_plan_s* p, const void* data);
+// Bytes of the data array of a plan (n complex values, or n reals).
+size_t plan_bytes(const efft_plan_s* p);
+// Twiddle table generation and the range scan, shared with efft_real.cu.
+int gen_table(float4* out, uint64_t count, uint64_t stride, int log2N, cudaStream_t st);
+int launch_range_scan(const void* data, uint64_t n_complex, uint32_t* state, void* const* ptrs, unsigned count,
+                      cudaStream_t st);
+void free_plan_memory(efft_plan_s* p);
+int prof_begin(efft_plan_s* p, int slot, cudaStream_t st);
+void prof_end(efft_plan_s* p, int rec, cudaStream_t st);
+// The real-data launch sequence (efft_real.cu).
+int enqueue_real(efft_plan_s* p, void* data, cudaStream_t st);
 int enqueue_batch(efft_plan_s* p, void* data, const Batch& bt, cudaStream_t st);
 int enqueue(efft_plan_s* p, void* data, cudaStream_t st);
 

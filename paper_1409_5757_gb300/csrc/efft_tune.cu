@@ -76,7 +76,7 @@ int autotune_impl(efft_plan_s* p, void* scratch, cudaStream_t st, int* cand_log2
   int prev_r[kMaxPasses] = {0, 0, 0, 0};
   const int prev_np = p->npasses;
   for (int j = 0; j < prev_np; ++j) prev_r[j] = p->pass[j].log2R;
-  const size_t bytes = p->n * ((p->dtype == EFFT_C128) ? 16 : 8);
+  const size_t bytes = plan_bytes(p);
   const int reps = (p->n <= (1ull << 20)) ? 21 : (p->n <= (1ull << 26) ? 9 : 5);
   const bool prof = p->profiling;
   p->profiling = false;
@@ -149,6 +149,7 @@ int efft_plan_autotune(efft_plan_t plan, void* scratch, void* stream, int* cand_
   if (!g.ok) return EFFT_ERR_CUDA;
   int rc = check_buffer(plan, scratch);
   if (rc != EFFT_OK) return rc;
+  if (plan->real) plan = plan->inner;  // a real plan's schedule is its complex plan's
   return autotune_impl(plan, scratch, reinterpret_cast<cudaStream_t>(stream), cand_log2r, cand_ms,
                        cap < 0 ? 0 : cap, ncand);
 }

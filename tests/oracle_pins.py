@@ -294,23 +294,24 @@ def pin_bins_tone(o):
 # Real data: the perm layout of Eq. 3 (Sec. 2.1)
 # --------------------------------------------------------------------------
 def pin_real_perm_closed_forms(o):
-    """Closed forms of Eq. 1 for real inputs, read through the perm layout
+    """Closed forms of Eq. 1 for real inputs (phases reduced mod N in integers),
+    read through the perm layout
     {R_0, R_{N/2}, R_1, I_1, ..., R_{N/2-1}, I_{N/2-1}}:
     cos(2 pi f n / N) -> R_f = N/2; sin(2 pi f n / N) -> I_f = -N/2 (sign -1);
     delta_0 -> every R_k = 1, I_k = 0; a constant c -> R_0 = N c;
     (-1)^n -> R_{N/2} = N."""
     for N in (2, 4, 8, 64, 1024, 8192):
         n = np.arange(N)
-        tol = 1e-12 * N
+        tol = 1e-14 * N
         for f in range(1, N // 2):
             if f > 5 and f < N // 2 - 3:
                 continue
             want = np.zeros(N)
             want[2 * f] = N / 2
-            assert np.max(np.abs(o.rdft_perm(np.cos(2 * np.pi * f * n / N)) - want)) <= tol, (N, f, "cos")
+            assert np.max(np.abs(o.rdft_perm(np.cos(2 * np.pi * ((f * n) % N) / N)) - want)) <= tol, (N, f, "cos")
             want = np.zeros(N)
             want[2 * f + 1] = -N / 2
-            assert np.max(np.abs(o.rdft_perm(np.sin(2 * np.pi * f * n / N)) - want)) <= tol, (N, f, "sin")
+            assert np.max(np.abs(o.rdft_perm(np.sin(2 * np.pi * ((f * n) % N) / N)) - want)) <= tol, (N, f, "sin")
         d = np.zeros(N)
         d[0] = 1
         want = np.zeros(N)

@@ -210,3 +210,17 @@ def test_schedule_candidates_are_valid():
             assert sum(r) == e and r == r[::-1] and all(4 <= v <= 11 for v in r), (e, r)
         assert len(cands) <= 10
         assert _planner_choice()(e) in cands, e
+
+
+def test_real_plan_argument_errors_before_cuda(libs):
+    import paper_1409_5757_gb300 as efft
+    L = efft._lib()
+    h = ctypes.c_void_p()
+    assert L.efft_plan_create_real(None, 16, 1, -1, 0) == 4
+    assert L.efft_plan_create_real(ctypes.byref(h), 1, 1, -1, 0) == 1        # N < 2
+    assert L.efft_plan_create_real(ctypes.byref(h), 24, 1, -1, 0) == 1       # not a power of two
+    assert L.efft_plan_create_real(ctypes.byref(h), 1 << 35, 1, -1, 0) == 1  # above 2^34 reals
+    assert L.efft_plan_create_real(ctypes.byref(h), 16, 2, -1, 0) == 2       # precision
+    assert L.efft_plan_create_real(ctypes.byref(h), 16, 1, 0, 0) == 3        # direction
+    assert L.efft_plan_create_real(ctypes.byref(h), 16, 1, -1, 0x1) == 12    # digit-reversed output
+    assert h.value is None
