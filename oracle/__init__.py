@@ -91,11 +91,33 @@ class Oracle:
         return X
 
     def dft(self, x, sign: int = -1) -> np.ndarray:
-        """Naive DFT for N <= 4096, radix-2 FFT above (N a power of two)."""
+        """Naive DFT for N <= 4096; above, the radix-2 FFT for N a power of
+        two, dft_mixed for N = M * 2^e (M odd)."""
         x = self._c128(x)
         if x.size <= 4096:
             return self.dft_naive(x, sign)
-        return self.fft_radix2(x, sign)
+        if x.size & (x.size - 1) == 0:
+            return self.fft_radix2(x, sign)
+        return self.dft_mixed(x, sign)
+
+    def dft_mixed(self, x, sign: int = -1) -> np.ndarray:
+        """Eq. 1 for N = M * P, P = 2^e, M odd: the decimation identity of Eq. 4
+        taken M ways instead of two,
+            X[k] = sum_{r<M} exp(sign*2*pi*i*r*k/N) * Y_r[k mod P],
+            Y_r = the P-point DFT of x[r], x[r+M], x[r+2M], ...
+        with the Y_r from dft (radix-2 or naive) and the M-term sums
+        evaluated directly; the phase r*k is reduced mod N in integers."""
+        x = self._c128(x)
+        N = x.size
+        P = N & -N
+        M = N // P
+        Y = [self.dft(x[r::M], sign) for r in range(M)]
+        k = np.arange(N, dtype=np.int64)
+        X = np.zeros(N, dtype=np.complex128)
+        for r in range(M):
+            ang = 2.0 * np.pi * ((r * k) % N) / N
+            X += (np.cos(ang) + 1j * sign * np.sin(ang)) * Y[r][k % P]
+        return X
 
     def gen_uniform(self, seed: int, N: int, n0: int = 0) -> np.ndarray:
         """The oracle's own SplitMix64 uniform[-1,1) re/im input, elements n0..n0+N-1."""

@@ -350,4 +350,48 @@ def pin_real_perm_round_trip(o):
         assert _rel(o.irdft_perm(p), N * np.fft.irfft(F, n=N)) <= 1e-13, N
 
 
+# --------------------------------------------------------------------------
+# N = M * 2^e (the paper's size set, Sec. 2.1)
+# --------------------------------------------------------------------------
+MIXED_SMALL = (12, 20, 24, 40, 48, 96, 3 << 10, 5 << 9, 7 << 9, 9 << 8, 15 << 8)
+
+
+def pin_mixed_vs_naive(o):
+    """The M-way decimation equals the direct sum of Eq. 1 (itself pinned by
+    mpmath and closed forms) wherever both run."""
+    for N in MIXED_SMALL:
+        x = _rand_c(N, N)
+        for sign in (-1, 1):
+            assert _rel(o.dft_mixed(x, sign), o.dft_naive(x, sign)) <= 1e-14, (N, sign)
+
+
+def pin_mixed_vs_numpy(o):
+    """Against numpy's pocketfft (its own mixed-radix algorithm)."""
+    for N in (3 << 14, 5 << 13, 15 << 12, 7 << 14):
+        x = _rand_c(N, N + 1)
+        assert _rel(o.dft(x, -1), np.fft.fft(x)) <= 1e-13, N
+        assert _rel(o.dft(x, +1), np.fft.ifft(x) * N) <= 1e-13, N
+
+
+def pin_mixed_closed_forms(o):
+    """N = M * 2^e: an impulse at m gives exp(sign*2*pi*i*m*k/N); a tone at
+    f gives N at bin f; the round trip returns N x; Parseval."""
+    for N in (3 << 15, 5 << 13):
+        k = np.arange(N)
+        for m in (1, 7, N // 3 + 1):
+            x = np.zeros(N, np.complex128)
+            x[m] = 1
+            want = np.exp(-2j * np.pi * ((m * k) % N) / N)
+            assert np.max(np.abs(o.dft(x, -1) - want)) <= 1e-14, (N, m)
+        f = N // 5 + 3
+        x = np.exp(2j * np.pi * ((f * k) % N) / N)
+        want = np.zeros(N, np.complex128)
+        want[f] = N
+        assert np.max(np.abs(o.dft(x, -1) - want)) <= 1e-12 * np.log2(N) * N ** 0.5, N
+        y = _rand_c(N, 3)
+        Y = o.dft(y, -1)
+        assert _rel(o.dft(Y, +1), N * y) <= 1e-14 * np.log2(N), N
+        assert abs(np.sum(np.abs(Y) ** 2) / (N * np.sum(np.abs(y) ** 2)) - 1) <= 1e-13, N
+
+
 ALL_PINS = [v for k, v in sorted(globals().items()) if k.startswith("pin_")]

@@ -78,3 +78,42 @@ def test_perm_mistake_is_caught(orc, mistake):
             caught = True
             break
     assert caught, f"perm mistake {fn.__name__} passed every real-data pin"
+
+
+# Planted mistakes in the oracle's M-way decimation, on the CPU.
+def _mixed_variant(kind):
+    def dft_mixed(self, x, sign=-1):
+        x = np.ascontiguousarray(np.asarray(x, np.complex128))
+        N = x.size
+        P = N & -N
+        M = N // P
+        if kind == "blocks":      # contiguous blocks instead of every M-th sample
+            Y = [self.dft(x[r * P:(r + 1) * P], sign) for r in range(M)]
+        else:
+            Y = [self.dft(x[r::M], sign) for r in range(M)]
+        k = np.arange(N, dtype=np.int64)
+        X = np.zeros(N, np.complex128)
+        for r in range(M):
+            kk = (k % P) if kind == "phase-mod-P" else k
+            sg = -sign if kind == "sign" else sign
+            ang = 2.0 * np.pi * ((r * kk) % N) / N
+            X += (np.cos(ang) + 1j * sg * np.sin(ang)) * Y[r][k % P]
+        return X
+    return dft_mixed
+
+
+@pytest.mark.parametrize("kind", ["blocks", "phase-mod-P", "sign"])
+def test_mixed_mistake_is_caught(orc, kind):
+    import types
+    o = oracle.Oracle()
+    o.dft_mixed = types.MethodType(_mixed_variant(kind), o)
+    caught = False
+    for pin in ALL_PINS:
+        if "mixed" not in pin.__name__:
+            continue
+        try:
+            pin(o)
+        except AssertionError:
+            caught = True
+            break
+    assert caught, f"mixed-radix mistake {kind} passed every pin"
