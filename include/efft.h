@@ -49,7 +49,7 @@ enum efft_dtype {
 /* Status codes returned by every entry point. */
 enum efft_status {
   EFFT_OK = 0,
-  EFFT_ERR_INVALID_SIZE = 1,   /* N is not 2^e with 0 <= e <= EFFT_MAX_LOG2N   */
+  EFFT_ERR_INVALID_SIZE = 1,   /* N is not M * 2^e (M odd <= 15), or too large  */
   EFFT_ERR_INVALID_DTYPE = 2,  /* dtype is not EFFT_C64 / EFFT_C128             */
   EFFT_ERR_INVALID_SIGN = 3,   /* sign is not -1 or +1                          */
   EFFT_ERR_INVALID_PTR = 4,    /* NULL, or not device memory of this device     */
@@ -65,6 +65,9 @@ enum efft_status {
 
 /* Largest supported log2 N (2^33 complex128 = 128 GiB). */
 #define EFFT_MAX_LOG2N 33
+/* Supported lengths: N = M * 2^e with M odd, 1 <= M <= EFFT_MAX_ODD (the
+ * paper's size set N = M * 2^s, Sec. 2.1), 1 <= N <= 2^EFFT_MAX_LOG2N. */
+#define EFFT_MAX_ODD 15
 
 /*
  * Plan flags.
@@ -99,12 +102,22 @@ typedef struct efft_plan_s* efft_plan_t;
  * plan's device tables (O(sqrt N) twiddle factors, generated on the device in
  * FP64, plus a few bytes of per-plan state) and synchronises.
  *  out    [out] receives the handle (set to NULL on failure).
- *  n      transform length, a power of two, 1 <= n <= 2^EFFT_MAX_LOG2N.
+ *  n      transform length N = M * 2^e (M odd, M <= EFFT_MAX_ODD),
+ *         1 <= n <= 2^EFFT_MAX_LOG2N.  For M > 1 the schedule is one
+ *         mixed-radix pass (N up to 2048 complex128 / 4096 complex64 points)
+ *         or three passes (2^a, M*2^b, 2^a): palindromic, so the final digit
+ *         reversal is the same in-place swap; efft_plan_radices then reports
+ *         the power-of-two part of each radix (M belongs to the middle or
+ *         only pass, whose extent is N / 4^a).  EFFT_FLAG_NORMALIZE is
+ *         rejected for M > 1 (EFFT_ERR_UNSUPPORTED: 1/N is not exact in
+ *         binary floating point); explicit schedules, the autotuner, the
+ *         no-allocation entry point and real-data plans take powers of two.
  *  dtype  EFFT_C64 or EFFT_C128.
  *  sign   -1 (forward, Eq. 1) or +1 (conjugate sign).
  *  flags  bitwise OR of EFFT_FLAG_*.
- * Errors: INVALID_SIZE / INVALID_DTYPE / INVALID_SIGN / INVALID_FLAGS are
- * detected before any CUDA call; ALLOC or CUDA if device set-up fails.
+ * Errors: INVALID_SIZE / INVALID_DTYPE / INVALID_SIGN / INVALID_FLAGS /
+ * UNSUPPORTED are detected before any CUDA call; ALLOC or CUDA if device
+ * set-up fails.
  * Ownership: the caller destroys the plan with efft_plan_destroy().
  */
 int efft_plan_create(efft_plan_t* out, uint64_t n, int dtype, int sign, uint32_t flags);

@@ -59,13 +59,15 @@ __global__ void __launch_bounds__(256) efft_range_scan(const uint4* __restrict__
 
 // ----------------------------------------------------------------------------
 // Twiddle tables: out[t] = exp(-2*pi*i * t*stride / N) for t < count, FP64
-// sincospi (exact argument: N is a power of two) split into FP32 (hi, lo).
+// sincospi of the phase reduced mod N in integers (exact for N a power of
+// two; for N = M * 2^e the quotient is rounded once), split into FP32
+// (hi, lo).
 // ----------------------------------------------------------------------------
-__global__ void efft_twiddles(float4* __restrict__ out, uint64_t count, uint64_t stride, int log2N) {
+__global__ void efft_twiddles(float4* __restrict__ out, uint64_t count, uint64_t stride, uint64_t N) {
   uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= count) return;
-  uint64_t mN = (t * stride) & ((1ull << log2N) - 1ull);
-  double x = -2.0 * ldexp((double)mN, -log2N);  // exact
+  const uint64_t mN = (N & (N - 1)) ? (t * stride) % N : (t * stride) & (N - 1);
+  const double x = -2.0 * ((double)mN / (double)N);
   double sv, cv;
   sincospi(x, &sv, &cv);
   float ch = __double2float_rn(cv), sh = __double2float_rn(sv);
@@ -107,6 +109,83 @@ int ilog2_u64(uint64_t n) {
   int e = 0;
   while ((1ull << e) < n) ++e;
   return e;
+}
+
+bool valid_size(uint64_t n) {
+  if (n == 0 || n > (1ull << EFFT_MAX_LOG2N)) return false;
+  const uint64_t odd = n / (n & (~n + 1));
+  return odd <= kMaxOdd;
+}
+
+// N = M * 2^e, M > 1: one mixed-radix pass when N fits a CTA, else three
+// passes (A, B, A) with A = 2^a and B = M * 2^(e - 2a) (palindromic, so the
+// digit reversal is still the swap of the outer digits), choosing a to make
+// the larger of A and B smallest.
+int apply_mixed_schedule(efft_plan_s* p) {
+  const uint64_t n = p->n;
+  const int tile = (p->dtype == EFFT_C128) ? kMixTileC128 : kMixTileC64;
+  const size_t eb = (p->dtype == EFFT_C128) ? 16 : 8;
+  const int e = __builtin_ctzll(n);
+  int np = 1, a = 0;
+  if (n > (uint64_t)tile) {
+    uint64_t best = 0;
+    for (int c = 1; 2 * c <= e; ++c) {
+      const uint64_t A = 1ull << c, B = n / (A * A);
+      if (A > (uint64_t)tile || B > (uint64_t)tile) continue;
+      const uint64_t big = A > B ? A : B;
+      if (best == 0 || big < best) {
+        best = big;
+        a = c;
+      }
+    }
+    if (a == 0) return EFFT_ERR_UNSUPPORTED;
+    np = 3;
+  }
+  const uint64_t A = 1ull << a, B = (np == 3) ? n / (A * A) : n;
+  const uint64_t Rs[3] = {np == 3 ? A : n, B, A};
+  const uint64_t ss[3] = {np == 3 ? n / A : 1, A, 1};
+  const uint64_t Ls[3] = {n, A * B, A};
+  p->npasses = np;
+  p->small = false;
+  for (int j = 0; j < kMaxPasses; ++j) p->pass[j] = Pass();
+  for (int j = 0; j < np; ++j) {
+    Pass& ps = p->pass[j];
+    const int jj = (np == 1) ? 0 : j;
+    ps.mixed = true;
+    ps.R_int = (np == 1) ? n : Rs[jj];
+    ps.s_int = (np == 1) ? 1 : ss[jj];
+    ps.L_int = (np == 1) ? n : Ls[jj];
+    ps.kind = (np == 1) ? SINGLE : (j == 0 ? FIRST : (j == 1 ? MID : LAST));
+    ps.log2R = __builtin_ctzll(ps.R_int);  // the power-of-two part (efft_plan_radices)
+    // Stockham radices: the odd factor, then 4s, then a 2
+    uint64_t rest = ps.R_int;
+    ps.nrad = 0;
+    const uint64_t odd = rest / (rest & (~rest + 1));
+    if (odd > 1) {
+      ps.rad[ps.nrad++] = (int)odd;
+      rest /= odd;
+    }
+    while (rest % 4 == 0) {
+      ps.rad[ps.nrad++] = 4;
+      rest /= 4;
+    }
+    if (rest == 2) ps.rad[ps.nrad++] = 2;
+    // columns per CTA: a power of two dividing the stride (a CTA's columns
+    // stay inside one block) and the column count
+    const uint64_t ncol = n / ps.R_int;
+    int C = 1;
+    while ((uint64_t)(2 * C) * ps.R_int <= (uint64_t)tile && ncol % (uint64_t)(2 * C) == 0 &&
+           (ps.s_int == 1 || ps.s_int % (uint64_t)(2 * C) == 0))
+      C *= 2;
+    ps.C_int = C;
+    ps.grid = ncol / (uint64_t)C;
+    ps.threads = 256;
+    ps.smem = 2 * (size_t)C * ps.R_int * eb;
+  }
+  p->permute = (np == 3) && !(p->flags & EFFT_FLAG_DIGIT_REVERSED_OUT);
+  p->perm_log2A = (np == 3) ? a : 0;
+  p->perm_B = (np == 3) ? (uint32_t)B : 1u;
+  return EFFT_OK;
 }
 
 // Radix schedule.  Symmetric radix lists (R_j = R_{p-1-j}) make the final
@@ -176,7 +255,7 @@ void apply_schedule(efft_plan_s* p, const int* r, int np) {
   }
   p->permute = (np >= 2) && !(p->flags & EFFT_FLAG_DIGIT_REVERSED_OUT);
   p->perm_log2A = (np >= 2) ? r[0] : 0;
-  p->perm_log2B = (np == 3) ? r[1] : 0;
+  p->perm_B = (np == 3) ? (1u << r[1]) : 1u;
 }
 
 template <class P, int KIND, int CTA>
@@ -197,6 +276,15 @@ int init_kernels() {
     set_smem_attr<PolicyF32, MID, 1 << kLog2CtaC64>();
     set_smem_attr<PolicyF32, LAST, 1 << kLog2CtaC64>();
     set_smem_attr<PolicyF32, SINGLE, 1 << kLog2CtaC64>();
+    const int mix128 = 2 * kMixTileC128 * (int)sizeof(cdf), mix64 = 2 * kMixTileC64 * (int)sizeof(float2);
+    cudaFuncSetAttribute(efft_pass_mix<PolicyDF, FIRST>, cudaFuncAttributeMaxDynamicSharedMemorySize, mix128);
+    cudaFuncSetAttribute(efft_pass_mix<PolicyDF, MID>, cudaFuncAttributeMaxDynamicSharedMemorySize, mix128);
+    cudaFuncSetAttribute(efft_pass_mix<PolicyDF, LAST>, cudaFuncAttributeMaxDynamicSharedMemorySize, mix128);
+    cudaFuncSetAttribute(efft_pass_mix<PolicyDF, SINGLE>, cudaFuncAttributeMaxDynamicSharedMemorySize, mix128);
+    cudaFuncSetAttribute(efft_pass_mix<PolicyF32, FIRST>, cudaFuncAttributeMaxDynamicSharedMemorySize, mix64);
+    cudaFuncSetAttribute(efft_pass_mix<PolicyF32, MID>, cudaFuncAttributeMaxDynamicSharedMemorySize, mix64);
+    cudaFuncSetAttribute(efft_pass_mix<PolicyF32, LAST>, cudaFuncAttributeMaxDynamicSharedMemorySize, mix64);
+    cudaFuncSetAttribute(efft_pass_mix<PolicyF32, SINGLE>, cudaFuncAttributeMaxDynamicSharedMemorySize, mix64);
     cudaError_t e1 = fx_set_attrs_df2();
     cudaError_t e2 = fx_set_attrs_f32();
     err = cudaGetLastError();
@@ -205,10 +293,10 @@ int init_kernels() {
   return err == cudaSuccess ? EFFT_OK : EFFT_ERR_CUDA;
 }
 
-int gen_table(float4* out, uint64_t count, uint64_t stride, int log2N, cudaStream_t st) {
+int gen_table(float4* out, uint64_t count, uint64_t stride, uint64_t N, cudaStream_t st) {
   const int bs = 256;
   uint64_t grid = (count + bs - 1) / bs;
-  efft_twiddles<<<(unsigned)grid, bs, 0, st>>>(out, count, stride, log2N);
+  efft_twiddles<<<(unsigned)grid, bs, 0, st>>>(out, count, stride, N);
   return cudaGetLastError() == cudaSuccess ? EFFT_OK : EFFT_ERR_LAUNCH;
 }
 
@@ -271,8 +359,45 @@ void prof_end(efft_plan_s* p, int rec, cudaStream_t st) {
 }
 
 // P: policy of the generic kernel; PFX: policy of the specialised kernels
+template <class P, int KIND>
+void launch_mix_kind(const MixArgs& m, const Pass& ps, void* data, unsigned count, cudaStream_t st) {
+  efft_pass_mix<P, KIND><<<dim3((unsigned)ps.grid, count), ps.threads, ps.smem, st>>>(data, m);
+}
+
+template <class P>
+cudaError_t launch_mix(const efft_plan_s* p, const Pass& ps, void* data, const Batch& bt, cudaStream_t st) {
+  MixArgs m;
+  std::memset(&m, 0, sizeof(m));
+  m.N = p->n;
+  m.s = ps.s_int;
+  m.L = ps.L_int;
+  m.R = (int)ps.R_int;
+  m.C = ps.C_int;
+  m.nrad = ps.nrad;
+  for (int i = 0; i < ps.nrad; ++i) m.rad[i] = ps.rad[i];
+  m.M = (int)p->odd;
+  m.twB = p->twB;
+  m.tw_lo = p->tw_lo;
+  m.tw_hi = p->tw_hi;
+  m.state = bt.state;
+  m.ptrs = bt.ptrs;
+  const uint32_t conj = (p->sign > 0) ? 1u : 0u;
+  m.conj_in = (ps.kind == FIRST || ps.kind == SINGLE) ? conj : 0u;
+  m.conj_out = (ps.kind == LAST || ps.kind == SINGLE) ? conj : 0u;
+  // 1/N = 1/(M 2^e): the power of two here, 1/M is not exact and is not offered
+  m.out_shift = ((p->flags & EFFT_FLAG_NORMALIZE) && (ps.kind == LAST || ps.kind == SINGLE)) ? p->log2n : 0;
+  switch (ps.kind) {
+    case FIRST: launch_mix_kind<P, FIRST>(m, ps, data, bt.count, st); break;
+    case MID: launch_mix_kind<P, MID>(m, ps, data, bt.count, st); break;
+    case LAST: launch_mix_kind<P, LAST>(m, ps, data, bt.count, st); break;
+    default: launch_mix_kind<P, SINGLE>(m, ps, data, bt.count, st); break;
+  }
+  return cudaGetLastError();
+}
+
 template <class P, class PFX, int CTA>
 cudaError_t launch_pass(const efft_plan_s* p, const Pass& ps, void* data, const Batch& bt, cudaStream_t st) {
+  if (ps.mixed) return launch_mix<P>(p, ps, data, bt, st);
   PassArgs a;
   std::memset(&a, 0, sizeof(a));
   a.log2R = ps.log2R;
@@ -364,10 +489,18 @@ int plan_create_impl(efft_plan_t* out, uint64_t n, int dtype, int sign, uint32_t
   p->sign = sign;
   p->flags = flags;
 
-  const int e = p->log2n;
+  const int e = p->log2n;  // ceil(log2 N)
   const size_t eb = (dtype == EFFT_C128) ? 16 : 8;
+  p->odd = (uint32_t)(n / (n & (~n + 1)));
   bool tune = false;
-  if (r_explicit) {
+  if (p->odd > 1) {
+    // N = M * 2^e: the mixed-radix schedule (neither tuned nor cached)
+    const int rc0 = apply_mixed_schedule(p);
+    if (rc0 != EFFT_OK) {
+      delete p;
+      return rc0;
+    }
+  } else if (r_explicit) {
     apply_schedule(p, r_explicit, np_explicit);
   } else {
     Tuned t;
@@ -386,7 +519,7 @@ int plan_create_impl(efft_plan_t* out, uint64_t n, int dtype, int sign, uint32_t
     delete p;
     return EFFT_ERR_ALLOC;
   }
-  const uint64_t nlo = 1ull << p->twB, nhi = 1ull << (e - p->twB);
+  const uint64_t nlo = 1ull << p->twB, nhi = (n + nlo - 1) >> p->twB;
   cudaStream_t st = nullptr;
   int rc = EFFT_OK;
   if (cudaMalloc(&p->w2048, 2048 * sizeof(float4)) != cudaSuccess ||
@@ -396,9 +529,9 @@ int plan_create_impl(efft_plan_t* out, uint64_t n, int dtype, int sign, uint32_t
     rc = EFFT_ERR_ALLOC;
   }
   if (rc == EFFT_OK && cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) rc = EFFT_ERR_CUDA;
-  if (rc == EFFT_OK) rc = gen_table(p->w2048, 2048, 1, 11, st);
-  if (rc == EFFT_OK) rc = gen_table(p->tw_lo, nlo, 1, e, st);
-  if (rc == EFFT_OK) rc = gen_table(p->tw_hi, nhi, nlo, e, st);
+  if (rc == EFFT_OK) rc = gen_table(p->w2048, 2048, 1, 2048, st);
+  if (rc == EFFT_OK) rc = gen_table(p->tw_lo, nlo, 1, n, st);
+  if (rc == EFFT_OK) rc = gen_table(p->tw_hi, nhi, nlo, n, st);
   if (rc == EFFT_OK && cudaMemsetAsync(p->state, 0, 16, st) != cudaSuccess) rc = EFFT_ERR_CUDA;
   if (rc == EFFT_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = EFFT_ERR_CUDA;
   p->recs = new (std::nothrow) std::vector<efft_plan_s::Rec>();
@@ -431,7 +564,7 @@ int plan_create_impl(efft_plan_t* out, uint64_t n, int dtype, int sign, uint32_t
 int check_create_args(efft_plan_t* out, uint64_t n, int dtype, int sign) {
   if (!out) return EFFT_ERR_INVALID_PTR;
   *out = nullptr;
-  if (n == 0 || (n & (n - 1)) != 0 || n > (1ull << EFFT_MAX_LOG2N)) return EFFT_ERR_INVALID_SIZE;
+  if (!valid_size(n)) return EFFT_ERR_INVALID_SIZE;
   if (dtype != EFFT_C64 && dtype != EFFT_C128) return EFFT_ERR_INVALID_DTYPE;
   if (sign != -1 && sign != 1) return EFFT_ERR_INVALID_SIGN;
   return EFFT_OK;
@@ -446,6 +579,8 @@ int efft_plan_create(efft_plan_t* out, uint64_t n, int dtype, int sign, uint32_t
   int rc = check_create_args(out, n, dtype, sign);
   if (rc != EFFT_OK) return rc;
   if (flags & ~EFFT_FLAG_ALL) return EFFT_ERR_INVALID_FLAGS;
+  // 1/N is exact in binary floating point only for N a power of two
+  if ((n & (n - 1)) != 0 && (flags & EFFT_FLAG_NORMALIZE)) return EFFT_ERR_UNSUPPORTED;
   return plan_create_impl(out, n, dtype, sign, flags, nullptr, 0);
 }
 
@@ -454,6 +589,7 @@ int efft_plan_create_with_radices(efft_plan_t* out, uint64_t n, int dtype, int s
   int rc = check_create_args(out, n, dtype, sign);
   if (rc != EFFT_OK) return rc;
   if (flags & ~(EFFT_FLAG_ALL & ~EFFT_FLAG_AUTOTUNE)) return EFFT_ERR_INVALID_FLAGS;
+  if ((n & (n - 1)) != 0) return EFFT_ERR_UNSUPPORTED;  // explicit schedules: powers of two
   if (!valid_schedule(ilog2_u64(n), log2_radices, npasses)) return EFFT_ERR_UNSUPPORTED;
   static const int kNone[1] = {0};
   return plan_create_impl(out, n, dtype, sign, flags, log2_radices ? log2_radices : kNone, npasses);
@@ -578,16 +714,17 @@ int enqueue_batch(efft_plan_s* p, void* data, const Batch& bt, cudaStream_t st) 
     if (err != cudaSuccess) return EFFT_ERR_LAUNCH;
   }
   if (p->permute) {
-    const int la = p->perm_log2A, lb = p->perm_log2B;
+    const int la = p->perm_log2A;
+    const uint32_t B = p->perm_B;
     const int lt = la < 5 ? la : 5;
     const uint64_t nt = 1ull << (la - lt);
-    dim3 grid((unsigned)(nt * (nt + 1) / 2), 1u << lb, bt.count);
+    dim3 grid((unsigned)(nt * (nt + 1) / 2), B, bt.count);
     int rec = prof_begin(p, 5, st);
     if (c128)
-      efft_digit_swap<uint4><<<grid, 256, 0, st>>>(reinterpret_cast<uint4*>(data), la, lb, lt,
+      efft_digit_swap<uint4><<<grid, 256, 0, st>>>(reinterpret_cast<uint4*>(data), la, B, lt,
                                                     reinterpret_cast<uint4* const*>(bt.ptrs));
     else
-      efft_digit_swap<uint2><<<grid, 256, 0, st>>>(reinterpret_cast<uint2*>(data), la, lb, lt,
+      efft_digit_swap<uint2><<<grid, 256, 0, st>>>(reinterpret_cast<uint2*>(data), la, B, lt,
                                                     reinterpret_cast<uint2* const*>(bt.ptrs));
     prof_end(p, rec, st);
     if (cudaGetLastError() != cudaSuccess) return EFFT_ERR_LAUNCH;
@@ -807,9 +944,9 @@ int efft_internal_run_in_scratch(void* scratch, size_t scratch_bytes, bool regen
   int rc = check_buffer(&p, data);
   if (rc != EFFT_OK) return rc;
   if (regen) {
-    if ((rc = gen_table(p.w2048, 2048, 1, 11, st)) != EFFT_OK) return rc;
-    if ((rc = gen_table(p.tw_lo, nlo, 1, e, st)) != EFFT_OK) return rc;
-    if ((rc = gen_table(p.tw_hi, nhi, nlo, e, st)) != EFFT_OK) return rc;
+    if ((rc = gen_table(p.w2048, 2048, 1, 2048, st)) != EFFT_OK) return rc;
+    if ((rc = gen_table(p.tw_lo, nlo, 1, n, st)) != EFFT_OK) return rc;
+    if ((rc = gen_table(p.tw_hi, nhi, nlo, n, st)) != EFFT_OK) return rc;
   }
   return enqueue(&p, data, st);
 }

@@ -138,7 +138,7 @@ int efft_batch_create(efft_batch_t* out, const uint64_t* sizes, int count, int d
   std::map<uint64_t, std::vector<int>, std::greater<uint64_t>> by_size;
   for (int i = 0; i < count; ++i) {
     const uint64_t n = sizes[i];
-    if (n == 0 || (n & (n - 1)) != 0 || n > (1ull << EFFT_MAX_LOG2N)) return EFFT_ERR_INVALID_SIZE;
+    if (!valid_size(n)) return EFFT_ERR_INVALID_SIZE;
     by_size[n].push_back(i);
   }
   for (auto& kv : by_size)

@@ -29,7 +29,19 @@ struct Pass {
   uint64_t grid;
   int threads;
   size_t smem;
+  // N = M * 2^e (M > 1): the mixed-radix kernel with integer extents
+  bool mixed;
+  uint64_t R_int, s_int, L_int;
+  int C_int;
+  int nrad;
+  int rad[8];  // Stockham radices, product R_int
 };
+
+// Largest odd factor M of a supported size N = M * 2^e.
+constexpr uint32_t kMaxOdd = 15;
+// Elements per CTA of the mixed-radix kernel (two shared buffers of 64 KiB).
+constexpr int kMixTileC128 = 2048;
+constexpr int kMixTileC64 = 4096;
 
 // The transforms one enqueue covers: ptrs (device array of `count` data
 // pointers, or NULL for one transform at the enqueue's `data`) and their
@@ -75,7 +87,9 @@ struct efft_plan_s {
   efft::host::Pass pass[efft::host::kMaxPasses];
   bool small;    // N <= 8: direct-sum kernel
   bool permute;  // final digit swap enabled
-  int perm_log2A, perm_log2B;
+  int perm_log2A;     // digit swap: outer extent 2^perm_log2A,
+  uint32_t perm_B;    //   middle extent perm_B
+  uint32_t odd;       // N = odd * 2^e
   int twB;
   float4* w2048;
   float4* tw_lo;
@@ -109,6 +123,10 @@ void register_plan(efft_plan_s* p);
 // EFFT_FAULT_INJECT=<what>: host-side failure injection for tests.
 bool fault_injected(const char* what);
 int ilog2_u64(uint64_t n);
+// N = M * 2^e with M odd, M <= kMaxOdd, 1 <= N <= 2^EFFT_MAX_LOG2N.
+bool valid_size(uint64_t n);
+// Schedule of a plan with N = M * 2^e, M > 1 (pass table and swap).
+int apply_mixed_schedule(efft_plan_s* p);
 
 // Schedules: the planner's table, the accepted set, and filling a plan's
 // pass table from a radix list.
@@ -133,7 +151,7 @@ int check_buffer(const efft_plan_s* p, const void* data);
 // Bytes of the data array of a plan (n complex values, or n reals).
 size_t plan_bytes(const efft_plan_s* p);
 // Twiddle table generation and the range scan, shared with efft_real.cu.
-int gen_table(float4* out, uint64_t count, uint64_t stride, int log2N, cudaStream_t st);
+int gen_table(float4* out, uint64_t count, uint64_t stride, uint64_t N, cudaStream_t st);
 int launch_range_scan(const void* data, uint64_t n_complex, uint32_t* state, void* const* ptrs, unsigned count,
                       cudaStream_t st);
 void free_plan_memory(efft_plan_s* p);

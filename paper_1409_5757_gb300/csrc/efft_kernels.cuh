@@ -585,14 +585,14 @@ __global__ void efft_small(void* __restrict__ data, const PassArgs a) {
 // T x T tiles, T = min(32, A); 256 threads.
 // ----------------------------------------------------------------------------
 template <typename E>
-__global__ void __launch_bounds__(256) efft_digit_swap(E* __restrict__ data, int log2A, int log2B, int log2T,
+__global__ void __launch_bounds__(256) efft_digit_swap(E* __restrict__ data, int log2A, uint32_t B, int log2T,
                                                        E* const* ptrs) {
   if (ptrs) data = ptrs[blockIdx.z];  // batched launch: transform blockIdx.z
   __shared__ E t0[32][33];
   __shared__ E t1[32][33];
   const int T = 1 << log2T;
   const uint64_t A = 1ull << log2A;
-  const uint64_t rowstride = A << log2B;  // stride of i0
+  const uint64_t rowstride = A * B;  // stride of i0 (B = extent of the middle digit)
   const uint64_t i1 = blockIdx.y;
   // triangular decode: z -> (I, J), I <= J
   const uint32_t z = blockIdx.x;
@@ -613,6 +613,133 @@ __global__ void __launch_bounds__(256) efft_digit_swap(E* __restrict__ data, int
     int r = e >> log2T, col = e & (T - 1);
     data[base + ((uint64_t)J * T + r) * rowstride + (uint64_t)I * T + col] = t0[col][r];
     if (I != J) data[base + ((uint64_t)I * T + r) * rowstride + (uint64_t)J * T + col] = t1[col][r];
+  }
+}
+
+// ----------------------------------------------------------------------------
+// Mixed-radix pass for N = M * 2^e (M odd, the paper's size set of Sec. 2.1):
+// the same in-place pass as efft_pass (a batch of strided size-R DFTs and
+// the twiddle of Eq. 4), for any radix R = M' * 2^b (M' = 1 or M) and any
+// integer stride and block length.  The R-point DFT of each column is a
+// mixed-radix Stockham (self-sorting) sequence in shared memory: radices
+// 4, 2 and the odd factor, ping-ponging between two buffers, so every
+// column ends in natural order; odd radices are direct sums over the M-th
+// roots of unity.  Twiddles exp(-2*pi*i*idx/N) come from the two-level
+// table; every index used is < N (m*q < L for a pass twiddle).
+// ----------------------------------------------------------------------------
+struct MixArgs {
+  uint64_t N;      // transform length
+  uint64_t s, L;   // column stride and block length of this pass
+  int R, C;        // radix and columns per CTA
+  int nrad;        // Stockham stages
+  int rad[8];      // their radices (product R)
+  int M;           // odd factor of N (its roots are cached)
+  int twB;         // low-table bits of the two-level table
+  const float4* tw_lo;
+  const float4* tw_hi;
+  const uint32_t* state;
+  void* const* ptrs;
+  uint32_t conj_in, conj_out;
+  int out_shift;
+};
+
+__device__ __forceinline__ float4 twiddle_mix(const MixArgs& a, uint64_t idx) {
+  return tw_mul(__ldg(a.tw_hi + (idx >> a.twB)), __ldg(a.tw_lo + (idx & ((1ull << a.twB) - 1ull))));
+}
+
+// Y[q] = sum_r v[r] exp(-2*pi*i*q*r/p), natural order, p in {2, 4, odd <= 15}.
+template <class P>
+__device__ __forceinline__ void small_dft(typename P::V* v, int p, const float4* roots) {
+  typedef typename P::V V;
+  if (p == 2) {
+    const V a0 = v[0], a1 = v[1];
+    v[0] = P::add(a0, a1);
+    v[1] = P::sub(a0, a1);
+  } else if (p == 4) {
+    const V s02 = P::add(v[0], v[2]), d02 = P::sub(v[0], v[2]);
+    const V s13 = P::add(v[1], v[3]), d13 = P::mul_negi(P::sub(v[1], v[3]));
+    v[0] = P::add(s02, s13);
+    v[2] = P::sub(s02, s13);
+    v[1] = P::add(d02, d13);
+    v[3] = P::sub(d02, d13);
+  } else {
+    V y[15];
+    for (int q = 0; q < p; ++q) {
+      V acc = v[0];
+      for (int r = 1; r < p; ++r) {
+        const int j = (q * r) % p;
+        acc = P::add(acc, j ? P::mul_tw(v[r], roots[j]) : v[r]);
+      }
+      y[q] = acc;
+    }
+    for (int q = 0; q < p; ++q) v[q] = y[q];
+  }
+}
+
+template <class P, int KIND>
+__global__ void __launch_bounds__(256) efft_pass_mix(void* __restrict__ data, const MixArgs a) {
+  typedef typename P::V V;
+  if (a.ptrs) data = a.ptrs[blockIdx.y];
+  const uint32_t* state = a.state + (a.ptrs ? 4u * blockIdx.y : 0u);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ float4 roots[16];
+  const int R = a.R, C = a.C, CR = R * C;
+  V* in = reinterpret_cast<V*>(smem_raw);
+  V* out = in + CR;
+
+  int D = 0, Dout = a.out_shift;
+  bool nonfinite = false;
+  if (P::kElemBytes == 16) {
+    const uint32_t emax = __ldg(state);
+    D = (int)emax - 127;
+    Dout = D - a.out_shift;
+    nonfinite = (emax >= 0x7FFu);
+  }
+  if ((int)threadIdx.x < a.M) roots[threadIdx.x] = twiddle_mix(a, (uint64_t)threadIdx.x * (a.N / (uint64_t)a.M));
+
+  const uint64_t jcol0 = (uint64_t)blockIdx.x * C;
+  const bool strided = (a.s > 1);
+  // load: adjacent threads read adjacent columns of a row (strided) or
+  // adjacent elements of a column (contiguous blocks)
+  for (int e = threadIdx.x; e < CR; e += blockDim.x) {
+    const int r = strided ? e / C : e % R, c = strided ? e % C : e / R;
+    const uint64_t col = jcol0 + c;
+    const uint64_t base = (col / a.s) * a.L + (col % a.s);
+    in[c * R + r] = Mem<P, KIND>::load(data, base + (uint64_t)r * a.s, D, a.conj_in);
+  }
+  __syncthreads();
+
+  int Ns = 1;
+  for (int st = 0; st < a.nrad; ++st) {
+    const int p = a.rad[st], Rp = R / p;
+    const uint64_t unit = a.N / (uint64_t)(Ns * p);
+    for (int w = threadIdx.x; w < C * Rp; w += blockDim.x) {
+      const int c = w / Rp, j = w - c * Rp, k = j % Ns;
+      V v[15];
+      for (int r = 0; r < p; ++r) v[r] = in[c * R + j + r * Rp];
+      if (k)
+        for (int r = 1; r < p; ++r) v[r] = P::mul_tw(v[r], twiddle_mix(a, (uint64_t)(k * r) * unit));
+      small_dft<P>(v, p, roots);
+      const int d = (j / Ns) * Ns * p + k;
+      for (int r = 0; r < p; ++r) out[c * R + d + r * Ns] = v[r];
+    }
+    __syncthreads();
+    V* t = in;
+    in = out;
+    out = t;
+    Ns *= p;
+  }
+
+  // epilogue: in[c*R + q] holds X[q] of column c; the pass twiddle
+  // exp(-2*pi*i*m*q/L) on strided passes, then the store
+  const uint64_t tw_unit = a.N / a.L;
+  for (int e = threadIdx.x; e < CR; e += blockDim.x) {
+    const int r = strided ? e / C : e % R, c = strided ? e % C : e / R;
+    const uint64_t col = jcol0 + c;
+    const uint64_t m = col % a.s;
+    V v = in[c * R + r];
+    if (strided && m != 0 && r != 0) v = P::mul_tw(v, twiddle_mix(a, m * (uint64_t)r * tw_unit));
+    Mem<P, KIND>::store(data, (col / a.s) * a.L + m + (uint64_t)r * a.s, v, Dout, a.conj_out, nonfinite);
   }
 }
 

@@ -243,8 +243,8 @@ extern "C" int efft_plan_create_real(efft_plan_t* out, uint64_t n, int precision
       cudaMalloc(&p->rtw_hi, nhi * sizeof(float4)) != cudaSuccess || cudaMalloc(&p->state, 16) != cudaSuccess)
     rc = EFFT_ERR_ALLOC;
   if (rc == EFFT_OK && cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) rc = EFFT_ERR_CUDA;
-  if (rc == EFFT_OK) rc = gen_table(p->rtw_lo, nlo, 1, p->log2n, st);
-  if (rc == EFFT_OK) rc = gen_table(p->rtw_hi, nhi, nlo, p->log2n, st);
+  if (rc == EFFT_OK) rc = gen_table(p->rtw_lo, nlo, 1, n, st);
+  if (rc == EFFT_OK) rc = gen_table(p->rtw_hi, nhi, nlo, n, st);
   if (rc == EFFT_OK && cudaMemsetAsync(p->state, 0, 16, st) != cudaSuccess) rc = EFFT_ERR_CUDA;
   if (rc == EFFT_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = EFFT_ERR_CUDA;
   if (st) cudaStreamDestroy(st);

@@ -150,6 +150,7 @@ int efft_plan_autotune(efft_plan_t plan, void* scratch, void* stream, int* cand_
   int rc = check_buffer(plan, scratch);
   if (rc != EFFT_OK) return rc;
   if (plan->real) plan = plan->inner;  // a real plan's schedule is its complex plan's
+  if (plan->odd > 1) return EFFT_ERR_UNSUPPORTED;  // N = M * 2^e: one schedule
   return autotune_impl(plan, scratch, reinterpret_cast<cudaStream_t>(stream), cand_log2r, cand_ms,
                        cap < 0 ? 0 : cap, ncand);
 }

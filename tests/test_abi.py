@@ -45,7 +45,8 @@ def test_argument_errors_before_cuda(libs):
     h = ctypes.c_void_p()
     assert L.efft_plan_create(None, 8, 1, -1, 0) == 4                    # NULL out
     assert L.efft_plan_create(ctypes.byref(h), 0, 1, -1, 0) == 1         # N = 0
-    assert L.efft_plan_create(ctypes.byref(h), 12, 1, -1, 0) == 1        # not a power of two
+    assert L.efft_plan_create(ctypes.byref(h), 34, 1, -1, 0) == 1        # odd factor 17 > 15
+    assert L.efft_plan_create(ctypes.byref(h), 3 * 1024, 1, -1, 2) == 9  # 1/N not exact for N = 3 * 2^10
     assert L.efft_plan_create(ctypes.byref(h), 1 << 34, 1, -1, 0) == 1   # too large
     assert L.efft_plan_create(ctypes.byref(h), 1 << 10, 2, -1, 0) == 2   # dtype
     assert L.efft_plan_create(ctypes.byref(h), 1 << 10, 1, 0, 0) == 3    # sign
@@ -161,7 +162,8 @@ def test_schedule_and_batch_argument_errors_before_cuda(libs):
     assert create(1 << 4, []) == 9                  # N > 8 needs a pass
     assert create(1 << 3, [3]) == 9                 # N <= 8: direct sums only
     assert create(1 << 12, [6, 6], flags=0x4) == 12  # autotune with an explicit schedule
-    assert create(12, [6, 6]) == 1
+    assert create(34, [6, 6]) == 1
+    assert create(12, [2]) == 9                     # explicit schedules: powers of two
     assert L.efft_plan_create_with_radices(None, 1 << 12, 1, -1, 0, radices(6, 6)[0], 2) == 4
     assert h.value is None
 
@@ -172,7 +174,7 @@ def test_schedule_and_batch_argument_errors_before_cuda(libs):
     assert L.efft_batch_create(ctypes.byref(h), sizes, 3, 2, -1, 0) == 2
     assert L.efft_batch_create(ctypes.byref(h), sizes, 3, 0, 0, 0) == 3
     assert L.efft_batch_create(ctypes.byref(h), sizes, 3, 0, -1, 0x80) == 12
-    bad = (ctypes.c_uint64 * 2)(1 << 10, 3 << 10)
+    bad = (ctypes.c_uint64 * 2)(1 << 10, 17 << 10)
     assert L.efft_batch_create(ctypes.byref(h), bad, 2, 0, -1, 0) == 1
     big = (ctypes.c_uint64 * 1)(1 << 34)
     assert L.efft_batch_create(ctypes.byref(h), big, 1, 0, -1, 0) == 1
