@@ -1,7 +1,7 @@
 #!/usr/bin/env python3
 """Throughput of the in-place 1-D complex DFT on GB300.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload c2|c3|c1|c4|c5|r1]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload c2|c3|c1|c4|c5|r1|m1]
                     [--impl ours|reference]
 
 Default workload (the headline configuration): one step = a forward DFT
@@ -51,6 +51,9 @@ WORKLOADS = {
                desc="complex128 N=2^20 in place, one transform per step; uniform[-1,1) re/im"),
     "c4": dict(log2n=31, dtype="c64", seed=4, tones=0, fwd_inv=False, gauss=True,
                desc="complex64 N=2^31 in place, one transform per step; Gaussian(0,1) re/im"),
+    "m1": dict(log2n=30, n=3 << 28, dtype="c128", seed=7, tones=0, fwd_inv=True, gauss=False, normalize=False,
+               desc="complex128 N=3*2^28 (12 GiB, the paper's size set N = M*2^s) in place, forward then the "
+                    "unnormalised conjugate-sign transform (1/N is not exact); uniform[-1,1) re/im"),
     "r1": dict(log2n=31, real=True, dtype="c64", seed=6, tones=0, fwd_inv=True, gauss=False,
                desc="real float32 N=2^32 reals (16 GiB) in place, forward to the perm layout (Eq. 3) then the "
                     "normalised inverse; uniform[-1,1); GFLOP/s by the real-data count (5/2) N log2 N (Eq. 7)"),
@@ -341,7 +344,7 @@ def config_of(wl):
                 "transforms_per_step": 2 if wl["fwd_inv"] else 1, "in_place": True,
                 "l2_between_steps": "inputs larger than L2 (no flush needed)",
                 "seed": wl["seed"], "parallelism": "replicas only (one transform per GPU)"}
-    return {"workload": wl["desc"], "N": 1 << wl["log2n"], "log2N": wl["log2n"],
+    return {"workload": wl["desc"], "N": wl.get("n", 1 << wl["log2n"]), "log2N": wl["log2n"],
             "element": "complex128" if wl["dtype"] == "c128" else "complex64",
             "transforms_per_step": 2 if wl["fwd_inv"] else 1, "in_place": True,
             "l2_between_steps": "inputs larger than L2 (no flush needed)" if wl["log2n"] >= 24
@@ -373,7 +376,7 @@ def run_ours(args, wl):
     if world > 1:
         dist.barrier()
 
-    N = 1 << wl["log2n"]
+    N = wl.get("n", 1 << wl["log2n"])
     c128 = wl["dtype"] == "c128"
     tdt = torch.complex128 if c128 else torch.complex64
     code = efft.EFFT_C128 if c128 else efft.EFFT_C64
@@ -400,8 +403,9 @@ def run_ours(args, wl):
         fwd = efft.Plan.real(2 * N, code, efft.EFFT_REAL_FORWARD, tune)
         inv = efft.Plan.real(2 * N, code, efft.EFFT_REAL_INVERSE, efft.EFFT_FLAG_NORMALIZE | tune)
     else:
+        norm_flag = efft.EFFT_FLAG_NORMALIZE if wl.get("normalize", True) else 0
         fwd = efft.Plan(N, code, -1, tune)
-        inv = efft.Plan(N, code, +1, efft.EFFT_FLAG_NORMALIZE | tune)
+        inv = efft.Plan(N, code, +1, norm_flag | tune)
     fpt = flops_real(2 * N) if real else flops(N)  # flop per transform
     stream = torch.cuda.current_stream(dev)
     sp = stream.cuda_stream
@@ -466,8 +470,10 @@ def run_ours(args, wl):
         done += 1
     round_trips = done if wl["fwd_inv"] else done // 2
     if keep is not None:
-        # forward then normalised inverse, round_trips times: x should return
-        num, den = inputs.diff_norms(x, keep, 1.0)
+        # forward then inverse, round_trips times: x returns (times N per
+        # round trip when the inverse is unnormalised)
+        scale = 1.0 if wl.get("normalize", True) else float(N) ** (-round_trips)
+        num, den = inputs.diff_norms(x, keep, scale)
         accuracy = {"roundtrip_rel_l2_after_all_steps": math.sqrt(num / den), "round_trips": round_trips,
                     "tolerance_per_round_trip": 2e-14 * wl["log2n"] if c128 else 4e-6 * wl["log2n"]}
 
@@ -749,7 +755,7 @@ def main():
         wl["log2n"] = args.log2n
         wl["desc"] = wl["desc"].replace("2^30", f"2^{args.log2n}").replace("2^33", f"2^{args.log2n}")
     if args.steps is None:
-        args.steps = {"c2": 20, "c3": 6, "c1": 200, "c4": 40, "c5": 40, "r1": 20}[args.workload]
+        args.steps = {"c2": 20, "c3": 6, "c1": 200, "c4": 40, "c5": 40, "r1": 20, "m1": 10}[args.workload]
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
     if args.impl == "reference":

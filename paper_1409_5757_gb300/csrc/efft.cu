@@ -276,19 +276,11 @@ int init_kernels() {
     set_smem_attr<PolicyF32, MID, 1 << kLog2CtaC64>();
     set_smem_attr<PolicyF32, LAST, 1 << kLog2CtaC64>();
     set_smem_attr<PolicyF32, SINGLE, 1 << kLog2CtaC64>();
-    const int mix128 = 2 * kMixTileC128 * (int)sizeof(cdf), mix64 = 2 * kMixTileC64 * (int)sizeof(float2);
-    cudaFuncSetAttribute(efft_pass_mix<PolicyDF, FIRST>, cudaFuncAttributeMaxDynamicSharedMemorySize, mix128);
-    cudaFuncSetAttribute(efft_pass_mix<PolicyDF, MID>, cudaFuncAttributeMaxDynamicSharedMemorySize, mix128);
-    cudaFuncSetAttribute(efft_pass_mix<PolicyDF, LAST>, cudaFuncAttributeMaxDynamicSharedMemorySize, mix128);
-    cudaFuncSetAttribute(efft_pass_mix<PolicyDF, SINGLE>, cudaFuncAttributeMaxDynamicSharedMemorySize, mix128);
-    cudaFuncSetAttribute(efft_pass_mix<PolicyF32, FIRST>, cudaFuncAttributeMaxDynamicSharedMemorySize, mix64);
-    cudaFuncSetAttribute(efft_pass_mix<PolicyF32, MID>, cudaFuncAttributeMaxDynamicSharedMemorySize, mix64);
-    cudaFuncSetAttribute(efft_pass_mix<PolicyF32, LAST>, cudaFuncAttributeMaxDynamicSharedMemorySize, mix64);
-    cudaFuncSetAttribute(efft_pass_mix<PolicyF32, SINGLE>, cudaFuncAttributeMaxDynamicSharedMemorySize, mix64);
+    cudaError_t e0 = mix_set_attrs();
     cudaError_t e1 = fx_set_attrs_df2();
     cudaError_t e2 = fx_set_attrs_f32();
     err = cudaGetLastError();
-    if (err == cudaSuccess) err = (e1 != cudaSuccess) ? e1 : e2;
+    if (err == cudaSuccess) err = (e0 != cudaSuccess) ? e0 : (e1 != cudaSuccess) ? e1 : e2;
   });
   return err == cudaSuccess ? EFFT_OK : EFFT_ERR_CUDA;
 }
@@ -359,45 +351,9 @@ void prof_end(efft_plan_s* p, int rec, cudaStream_t st) {
 }
 
 // P: policy of the generic kernel; PFX: policy of the specialised kernels
-template <class P, int KIND>
-void launch_mix_kind(const MixArgs& m, const Pass& ps, void* data, unsigned count, cudaStream_t st) {
-  efft_pass_mix<P, KIND><<<dim3((unsigned)ps.grid, count), ps.threads, ps.smem, st>>>(data, m);
-}
-
-template <class P>
-cudaError_t launch_mix(const efft_plan_s* p, const Pass& ps, void* data, const Batch& bt, cudaStream_t st) {
-  MixArgs m;
-  std::memset(&m, 0, sizeof(m));
-  m.N = p->n;
-  m.s = ps.s_int;
-  m.L = ps.L_int;
-  m.R = (int)ps.R_int;
-  m.C = ps.C_int;
-  m.nrad = ps.nrad;
-  for (int i = 0; i < ps.nrad; ++i) m.rad[i] = ps.rad[i];
-  m.M = (int)p->odd;
-  m.twB = p->twB;
-  m.tw_lo = p->tw_lo;
-  m.tw_hi = p->tw_hi;
-  m.state = bt.state;
-  m.ptrs = bt.ptrs;
-  const uint32_t conj = (p->sign > 0) ? 1u : 0u;
-  m.conj_in = (ps.kind == FIRST || ps.kind == SINGLE) ? conj : 0u;
-  m.conj_out = (ps.kind == LAST || ps.kind == SINGLE) ? conj : 0u;
-  // 1/N = 1/(M 2^e): the power of two here, 1/M is not exact and is not offered
-  m.out_shift = ((p->flags & EFFT_FLAG_NORMALIZE) && (ps.kind == LAST || ps.kind == SINGLE)) ? p->log2n : 0;
-  switch (ps.kind) {
-    case FIRST: launch_mix_kind<P, FIRST>(m, ps, data, bt.count, st); break;
-    case MID: launch_mix_kind<P, MID>(m, ps, data, bt.count, st); break;
-    case LAST: launch_mix_kind<P, LAST>(m, ps, data, bt.count, st); break;
-    default: launch_mix_kind<P, SINGLE>(m, ps, data, bt.count, st); break;
-  }
-  return cudaGetLastError();
-}
-
 template <class P, class PFX, int CTA>
 cudaError_t launch_pass(const efft_plan_s* p, const Pass& ps, void* data, const Batch& bt, cudaStream_t st) {
-  if (ps.mixed) return launch_mix<P>(p, ps, data, bt, st);
+  if (ps.mixed) return launch_mix(p, ps, data, bt, st);
   PassArgs a;
   std::memset(&a, 0, sizeof(a));
   a.log2R = ps.log2R;

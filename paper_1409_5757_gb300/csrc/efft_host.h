@@ -157,6 +157,9 @@ int launch_range_scan(const void* data, uint64_t n_complex, uint32_t* state, voi
 void free_plan_memory(efft_plan_s* p);
 int prof_begin(efft_plan_s* p, int slot, cudaStream_t st);
 void prof_end(efft_plan_s* p, int rec, cudaStream_t st);
+// Mixed-radix passes (efft_mix.cu): kernel attributes and one pass launch.
+cudaError_t mix_set_attrs();
+cudaError_t launch_mix(const efft_plan_s* p, const Pass& ps, void* data, const Batch& bt, cudaStream_t st);
 // The real-data launch sequence (efft_real.cu).
 int enqueue_real(efft_plan_s* p, void* data, cudaStream_t st);
 int enqueue_batch(efft_plan_s* p, void* data, const Batch& bt, cudaStream_t st);

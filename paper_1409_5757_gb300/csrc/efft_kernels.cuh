@@ -648,8 +648,8 @@ __device__ __forceinline__ float4 twiddle_mix(const MixArgs& a, uint64_t idx) {
 }
 
 // Y[q] = sum_r v[r] exp(-2*pi*i*q*r/p), natural order, p in {2, 4, odd <= 15}.
-template <class P>
-__device__ __forceinline__ void small_dft(typename P::V* v, int p, const float4* roots) {
+template <class P, int p>
+__device__ __forceinline__ void small_dft(typename P::V* v, const float4* roots) {
   typedef typename P::V V;
   if (p == 2) {
     const V a0 = v[0], a1 = v[1];
@@ -663,16 +663,45 @@ __device__ __forceinline__ void small_dft(typename P::V* v, int p, const float4*
     v[1] = P::add(d02, d13);
     v[3] = P::sub(d02, d13);
   } else {
-    V y[15];
+    V y[p];
+#pragma unroll
     for (int q = 0; q < p; ++q) {
       V acc = v[0];
+#pragma unroll
       for (int r = 1; r < p; ++r) {
         const int j = (q * r) % p;
         acc = P::add(acc, j ? P::mul_tw(v[r], roots[j]) : v[r]);
       }
       y[q] = acc;
     }
+#pragma unroll
     for (int q = 0; q < p; ++q) v[q] = y[q];
+  }
+}
+
+// One Stockham stage of radix p over the C columns of a tile: work item
+// (column c, j < R/p) reads v[r] = in[j + r R/p], multiplies by
+// exp(-2*pi*i*k*r/(Ns p)) (k = j mod Ns), transforms and writes
+// out[(j/Ns) Ns p + k + r Ns].
+template <class P, int p>
+__device__ __forceinline__ void mix_stage(const typename P::V* in, typename P::V* out, int R, int C, int Ns,
+                                          const MixArgs& a, const float4* roots) {
+  typedef typename P::V V;
+  const int Rp = R / p;
+  const uint64_t unit = a.N / (uint64_t)(Ns * p);
+  for (int w = threadIdx.x; w < C * Rp; w += blockDim.x) {
+    const int c = w / Rp, j = w - c * Rp, k = j % Ns;
+    V v[p];
+#pragma unroll
+    for (int r = 0; r < p; ++r) v[r] = in[c * R + j + r * Rp];
+    if (k) {
+#pragma unroll
+      for (int r = 1; r < p; ++r) v[r] = P::mul_tw(v[r], twiddle_mix(a, (uint64_t)(k * r) * unit));
+    }
+    small_dft<P, p>(v, roots);
+    const int d = (j / Ns) * Ns * p + k;
+#pragma unroll
+    for (int r = 0; r < p; ++r) out[c * R + d + r * Ns] = v[r];
   }
 }
 
@@ -711,17 +740,17 @@ __global__ void __launch_bounds__(256) efft_pass_mix(void* __restrict__ data, co
 
   int Ns = 1;
   for (int st = 0; st < a.nrad; ++st) {
-    const int p = a.rad[st], Rp = R / p;
-    const uint64_t unit = a.N / (uint64_t)(Ns * p);
-    for (int w = threadIdx.x; w < C * Rp; w += blockDim.x) {
-      const int c = w / Rp, j = w - c * Rp, k = j % Ns;
-      V v[15];
-      for (int r = 0; r < p; ++r) v[r] = in[c * R + j + r * Rp];
-      if (k)
-        for (int r = 1; r < p; ++r) v[r] = P::mul_tw(v[r], twiddle_mix(a, (uint64_t)(k * r) * unit));
-      small_dft<P>(v, p, roots);
-      const int d = (j / Ns) * Ns * p + k;
-      for (int r = 0; r < p; ++r) out[c * R + d + r * Ns] = v[r];
+    const int p = a.rad[st];
+    switch (p) {
+      case 2: mix_stage<P, 2>(in, out, R, C, Ns, a, roots); break;
+      case 4: mix_stage<P, 4>(in, out, R, C, Ns, a, roots); break;
+      case 3: mix_stage<P, 3>(in, out, R, C, Ns, a, roots); break;
+      case 5: mix_stage<P, 5>(in, out, R, C, Ns, a, roots); break;
+      case 7: mix_stage<P, 7>(in, out, R, C, Ns, a, roots); break;
+      case 9: mix_stage<P, 9>(in, out, R, C, Ns, a, roots); break;
+      case 11: mix_stage<P, 11>(in, out, R, C, Ns, a, roots); break;
+      case 13: mix_stage<P, 13>(in, out, R, C, Ns, a, roots); break;
+      default: mix_stage<P, 15>(in, out, R, C, Ns, a, roots); break;
     }
     __syncthreads();
     V* t = in;

@@ -1,0 +1,83 @@
+// efft_mix.cu -- launches of the mixed-radix pass kernel (efft_pass_mix in
+// efft_kernels.cuh) for transform lengths N = M * 2^e with M odd (the
+// paper's size set N = M * 2^s, Sec. 2.1).  A translation unit of its own:
+// the kernel is instantiated for every odd radix and compiles in parallel
+// with the others.
+#include <cuda_runtime.h>
+
+#include <cstring>
+
+#include "../../include/efft.h"
+#include "efft_host.h"
+#include "efft_kernels.cuh"
+
+using namespace efft;
+using namespace efft::host;
+
+namespace {
+
+template <class P, int KIND>
+void launch_mix_kind(const MixArgs& m, const Pass& ps, void* data, unsigned count, cudaStream_t st) {
+  efft_pass_mix<P, KIND><<<dim3((unsigned)ps.grid, count), ps.threads, ps.smem, st>>>(data, m);
+}
+
+template <class P>
+cudaError_t launch_mix_p(const efft_plan_s* p, const Pass& ps, void* data, const Batch& bt, cudaStream_t st) {
+  MixArgs m;
+  std::memset(&m, 0, sizeof(m));
+  m.N = p->n;
+  m.s = ps.s_int;
+  m.L = ps.L_int;
+  m.R = (int)ps.R_int;
+  m.C = ps.C_int;
+  m.nrad = ps.nrad;
+  for (int i = 0; i < ps.nrad; ++i) m.rad[i] = ps.rad[i];
+  m.M = (int)p->odd;
+  m.twB = p->twB;
+  m.tw_lo = p->tw_lo;
+  m.tw_hi = p->tw_hi;
+  m.state = bt.state;
+  m.ptrs = bt.ptrs;
+  const uint32_t conj = (p->sign > 0) ? 1u : 0u;
+  m.conj_in = (ps.kind == FIRST || ps.kind == SINGLE) ? conj : 0u;
+  m.conj_out = (ps.kind == LAST || ps.kind == SINGLE) ? conj : 0u;
+  // 1/N = 1/(M 2^e): the power of two here, 1/M is not exact and is not offered
+  m.out_shift = ((p->flags & EFFT_FLAG_NORMALIZE) && (ps.kind == LAST || ps.kind == SINGLE)) ? p->log2n : 0;
+  switch (ps.kind) {
+    case FIRST: launch_mix_kind<P, FIRST>(m, ps, data, bt.count, st); break;
+    case MID: launch_mix_kind<P, MID>(m, ps, data, bt.count, st); break;
+    case LAST: launch_mix_kind<P, LAST>(m, ps, data, bt.count, st); break;
+    default: launch_mix_kind<P, SINGLE>(m, ps, data, bt.count, st); break;
+  }
+  return cudaGetLastError();
+}
+
+
+}  // namespace
+
+namespace efft {
+namespace host {
+
+cudaError_t mix_set_attrs() {
+  const int mix128 = 2 * kMixTileC128 * (int)sizeof(cdf), mix64 = 2 * kMixTileC64 * (int)sizeof(float2);
+  const cudaFuncAttribute attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  cudaError_t e[8] = {cudaFuncSetAttribute(efft_pass_mix<PolicyDF, FIRST>, attr, mix128),
+                      cudaFuncSetAttribute(efft_pass_mix<PolicyDF, MID>, attr, mix128),
+                      cudaFuncSetAttribute(efft_pass_mix<PolicyDF, LAST>, attr, mix128),
+                      cudaFuncSetAttribute(efft_pass_mix<PolicyDF, SINGLE>, attr, mix128),
+                      cudaFuncSetAttribute(efft_pass_mix<PolicyF32, FIRST>, attr, mix64),
+                      cudaFuncSetAttribute(efft_pass_mix<PolicyF32, MID>, attr, mix64),
+                      cudaFuncSetAttribute(efft_pass_mix<PolicyF32, LAST>, attr, mix64),
+                      cudaFuncSetAttribute(efft_pass_mix<PolicyF32, SINGLE>, attr, mix64)};
+  for (cudaError_t x : e)
+    if (x != cudaSuccess) return x;
+  return cudaSuccess;
+}
+
+cudaError_t launch_mix(const efft_plan_s* p, const Pass& ps, void* data, const Batch& bt, cudaStream_t st) {
+  return (p->dtype == EFFT_C128) ? launch_mix_p<PolicyDF>(p, ps, data, bt, st)
+                                 : launch_mix_p<PolicyF32>(p, ps, data, bt, st);
+}
+
+}  // namespace host
+}  // namespace efft
