@@ -76,30 +76,30 @@ __device__ __forceinline__ df f64bits_to_df(uint32_t lo, uint32_t hi, int D, uin
   return out;
 }
 
-// Normalised df (s, e) -> binary64 bits (truncating the sum to 53 bits).
+// Normalised df (h, l) -> binary64 bits: the magnitude of h as a 64-bit
+// integer (Ed << 52 | significand) in units of ulp64(h), plus l expressed in
+// the same units -- an exact power-of-two scaling, |l| < 2^28 units -- and
+// rounded to an integer by F2I (round to nearest even).  When h is a power
+// of two and l has the opposite sign the sum lies in the binade below, whose
+// unit is half as large: there l is scaled by one more factor of two and the
+// borrow from the exponent field lands the result in that binade.  Low parts
+// of |h| < 2^-75 (relative to the scale) are dropped.
 __device__ __forceinline__ void df_to_f64bits(df v, int D, uint32_t flip, uint32_t& olo, uint32_t& ohi) {
   v = df_norm(v);
-  uint32_t S = __float_as_uint(v.h);
-  uint32_t sign = (S ^ flip) & 0x80000000u;
-  int Es = (int)((S >> 23) & 0xFFu);
-  uint32_t ms = S & 0x7FFFFFu;
-  int Ed = Es + D;
-  // magnitude as a 64-bit integer (Ed << 52 | m52) in units of ulp64(s)
-  uint32_t mh = ((uint32_t)Ed << 20) | (ms >> 3);
-  uint32_t ml = ms << 29;
-  // add the low float, expressed in ulp64(s) units
-  uint32_t Eb = __float_as_uint(v.l);
-  int Ee = (int)((Eb >> 23) & 0xFFu);
-  uint32_t Me = (Ee != 0) ? ((Eb & 0x7FFFFFu) | 0x800000u) : 0u;
-  bool opposite = ((Eb ^ S) & 0x80000000u) != 0u;
-  int sh = Ee - Es + 29 + ((opposite && ms == 0u) ? 1 : 0);
-  uint32_t emag = (sh >= 0) ? (Me << (sh > 31 ? 31 : sh)) : (sh > -32 ? (Me >> (-sh)) : 0u);
-  // 64-bit add / subtract of emag
-  uint64_t mag = ((uint64_t)mh << 32) | ml;
-  mag = opposite ? (mag - emag) : (mag + emag);
+  const uint32_t S = __float_as_uint(v.h), L = __float_as_uint(v.l);
+  const uint32_t sign = (S ^ flip) & 0x80000000u;
+  const int Es = (int)((S >> 23) & 0xFFu);
+  const int Ed = Es + D;
+  const bool down = ((S & 0x7FFFFFu) == 0u) && (((S ^ L) & 0x80000000u) != 0u);
+  int lu = 0;
+  if (Es >= 52)  // l * 2^(179-Es), or 2^(180-Es) in the binade below
+    lu = __float2int_rn(__fmul_rn(v.l, __uint_as_float((uint32_t)(306 - Es + (down ? 1 : 0)) << 23)));
+  if (S & 0x80000000u) lu = -lu;  // l relative to the sign of h
+  const uint64_t mag =
+      (((uint64_t)(uint32_t)Ed << 52) | ((uint64_t)(S & 0x7FFFFFu) << 29)) + (uint64_t)(int64_t)lu;
   uint32_t rh = (uint32_t)(mag >> 32), rl = (uint32_t)mag;
-  bool zero = (Es == 0) || (Ed <= 0);
-  bool inf = (Ed >= 2047) || ((rh >> 20) >= 2047u);
+  const bool zero = (Es == 0) || (Ed <= 0);
+  const bool inf = (Ed >= 2047) || ((rh >> 20) >= 2047u);
   if (zero) { rh = 0u; rl = 0u; }
   if (inf && !zero) { rh = 0x7FF00000u; rl = 0u; }
   ohi = sign | rh;

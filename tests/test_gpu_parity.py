@@ -233,3 +233,19 @@ def test_fault_injection_is_host_side(monkeypatch):
     monkeypatch.delenv("EFFT_FAULT_INJECT")
     p.execute(t.data_ptr())
     torch.cuda.synchronize()
+
+
+@pytest.mark.parametrize("e", [10, 20])
+def test_c128_output_just_below_a_power_of_two(e):
+    """x = v * delta_0 gives X[k] = v for every k.  With v = +-(2^k - 2^(k-30))
+    the double-float value is (2^k, -2^(k-30)): a power-of-two high part
+    with an opposite-sign low part, whose sum lies in the binade below --
+    the binary64 conversion must still return v exactly."""
+    N = 1 << e
+    for k in (0, 9, 40, -20):
+        for sgn in (1.0, -1.0):
+            v = sgn * (2.0 ** k - 2.0 ** (k - 30))
+            x = np.zeros(N, np.complex128)
+            x[0] = v + 1j * v
+            got = gpu_fft(x, "c128", -1)
+            assert np.max(np.abs(got - (v + 1j * v))) <= 1e-15 * abs(v), (k, sgn)
