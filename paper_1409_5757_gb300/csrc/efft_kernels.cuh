@@ -616,162 +616,6 @@ __global__ void __launch_bounds__(256) efft_digit_swap(E* __restrict__ data, int
   }
 }
 
-// ----------------------------------------------------------------------------
-// Mixed-radix pass for N = M * 2^e (M odd, the paper's size set of Sec. 2.1):
-// the same in-place pass as efft_pass (a batch of strided size-R DFTs and
-// the twiddle of Eq. 4), for any radix R = M' * 2^b (M' = 1 or M) and any
-// integer stride and block length.  The R-point DFT of each column is a
-// mixed-radix Stockham (self-sorting) sequence in shared memory: radices
-// 4, 2 and the odd factor, ping-ponging between two buffers, so every
-// column ends in natural order; odd radices are direct sums over the M-th
-// roots of unity.  Twiddles exp(-2*pi*i*idx/N) come from the two-level
-// table; every index used is < N (m*q < L for a pass twiddle).
-// ----------------------------------------------------------------------------
-struct MixArgs {
-  uint64_t N;      // transform length
-  uint64_t s, L;   // column stride and block length of this pass
-  int R, C;        // radix and columns per CTA
-  int nrad;        // Stockham stages
-  int rad[8];      // their radices (product R)
-  int M;           // odd factor of N (its roots are cached)
-  int twB;         // low-table bits of the two-level table
-  const float4* tw_lo;
-  const float4* tw_hi;
-  const uint32_t* state;
-  void* const* ptrs;
-  uint32_t conj_in, conj_out;
-  int out_shift;
-};
-
-__device__ __forceinline__ float4 twiddle_mix(const MixArgs& a, uint64_t idx) {
-  return tw_mul(__ldg(a.tw_hi + (idx >> a.twB)), __ldg(a.tw_lo + (idx & ((1ull << a.twB) - 1ull))));
-}
-
-// Y[q] = sum_r v[r] exp(-2*pi*i*q*r/p), natural order, p in {2, 4, odd <= 15}.
-template <class P, int p>
-__device__ __forceinline__ void small_dft(typename P::V* v, const float4* roots) {
-  typedef typename P::V V;
-  if (p == 2) {
-    const V a0 = v[0], a1 = v[1];
-    v[0] = P::add(a0, a1);
-    v[1] = P::sub(a0, a1);
-  } else if (p == 4) {
-    const V s02 = P::add(v[0], v[2]), d02 = P::sub(v[0], v[2]);
-    const V s13 = P::add(v[1], v[3]), d13 = P::mul_negi(P::sub(v[1], v[3]));
-    v[0] = P::add(s02, s13);
-    v[2] = P::sub(s02, s13);
-    v[1] = P::add(d02, d13);
-    v[3] = P::sub(d02, d13);
-  } else {
-    V y[p];
-#pragma unroll
-    for (int q = 0; q < p; ++q) {
-      V acc = v[0];
-#pragma unroll
-      for (int r = 1; r < p; ++r) {
-        const int j = (q * r) % p;
-        acc = P::add(acc, j ? P::mul_tw(v[r], roots[j]) : v[r]);
-      }
-      y[q] = acc;
-    }
-#pragma unroll
-    for (int q = 0; q < p; ++q) v[q] = y[q];
-  }
-}
-
-// One Stockham stage of radix p over the C columns of a tile: work item
-// (column c, j < R/p) reads v[r] = in[j + r R/p], multiplies by
-// exp(-2*pi*i*k*r/(Ns p)) (k = j mod Ns), transforms and writes
-// out[(j/Ns) Ns p + k + r Ns].
-template <class P, int p>
-__device__ __forceinline__ void mix_stage(const typename P::V* in, typename P::V* out, int R, int C, int Ns,
-                                          const MixArgs& a, const float4* roots) {
-  typedef typename P::V V;
-  const int Rp = R / p;
-  const uint64_t unit = a.N / (uint64_t)(Ns * p);
-  for (int w = threadIdx.x; w < C * Rp; w += blockDim.x) {
-    const int c = w / Rp, j = w - c * Rp, k = j % Ns;
-    V v[p];
-#pragma unroll
-    for (int r = 0; r < p; ++r) v[r] = in[c * R + j + r * Rp];
-    if (k) {
-#pragma unroll
-      for (int r = 1; r < p; ++r) v[r] = P::mul_tw(v[r], twiddle_mix(a, (uint64_t)(k * r) * unit));
-    }
-    small_dft<P, p>(v, roots);
-    const int d = (j / Ns) * Ns * p + k;
-#pragma unroll
-    for (int r = 0; r < p; ++r) out[c * R + d + r * Ns] = v[r];
-  }
-}
-
-template <class P, int KIND>
-__global__ void __launch_bounds__(256) efft_pass_mix(void* __restrict__ data, const MixArgs a) {
-  typedef typename P::V V;
-  if (a.ptrs) data = a.ptrs[blockIdx.y];
-  const uint32_t* state = a.state + (a.ptrs ? 4u * blockIdx.y : 0u);
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ float4 roots[16];
-  const int R = a.R, C = a.C, CR = R * C;
-  V* in = reinterpret_cast<V*>(smem_raw);
-  V* out = in + CR;
-
-  int D = 0, Dout = a.out_shift;
-  bool nonfinite = false;
-  if (P::kElemBytes == 16) {
-    const uint32_t emax = __ldg(state);
-    D = (int)emax - 127;
-    Dout = D - a.out_shift;
-    nonfinite = (emax >= 0x7FFu);
-  }
-  if ((int)threadIdx.x < a.M) roots[threadIdx.x] = twiddle_mix(a, (uint64_t)threadIdx.x * (a.N / (uint64_t)a.M));
-
-  const uint64_t jcol0 = (uint64_t)blockIdx.x * C;
-  const bool strided = (a.s > 1);
-  // load: adjacent threads read adjacent columns of a row (strided) or
-  // adjacent elements of a column (contiguous blocks)
-  for (int e = threadIdx.x; e < CR; e += blockDim.x) {
-    const int r = strided ? e / C : e % R, c = strided ? e % C : e / R;
-    const uint64_t col = jcol0 + c;
-    const uint64_t base = (col / a.s) * a.L + (col % a.s);
-    in[c * R + r] = Mem<P, KIND>::load(data, base + (uint64_t)r * a.s, D, a.conj_in);
-  }
-  __syncthreads();
-
-  int Ns = 1;
-  for (int st = 0; st < a.nrad; ++st) {
-    const int p = a.rad[st];
-    switch (p) {
-      case 2: mix_stage<P, 2>(in, out, R, C, Ns, a, roots); break;
-      case 4: mix_stage<P, 4>(in, out, R, C, Ns, a, roots); break;
-      case 3: mix_stage<P, 3>(in, out, R, C, Ns, a, roots); break;
-      case 5: mix_stage<P, 5>(in, out, R, C, Ns, a, roots); break;
-      case 7: mix_stage<P, 7>(in, out, R, C, Ns, a, roots); break;
-      case 9: mix_stage<P, 9>(in, out, R, C, Ns, a, roots); break;
-      case 11: mix_stage<P, 11>(in, out, R, C, Ns, a, roots); break;
-      case 13: mix_stage<P, 13>(in, out, R, C, Ns, a, roots); break;
-      default: mix_stage<P, 15>(in, out, R, C, Ns, a, roots); break;
-    }
-    __syncthreads();
-    V* t = in;
-    in = out;
-    out = t;
-    Ns *= p;
-  }
-
-  // epilogue: in[c*R + q] holds X[q] of column c; the pass twiddle
-  // exp(-2*pi*i*m*q/L) on strided passes, then the store
-  const uint64_t tw_unit = a.N / a.L;
-  for (int e = threadIdx.x; e < CR; e += blockDim.x) {
-    const int r = strided ? e / C : e % R, c = strided ? e % C : e / R;
-    const uint64_t col = jcol0 + c;
-    const uint64_t m = col % a.s;
-    V v = in[c * R + r];
-    if (strided && m != 0 && r != 0) v = P::mul_tw(v, twiddle_mix(a, m * (uint64_t)r * tw_unit));
-    Mem<P, KIND>::store(data, (col / a.s) * a.L + m + (uint64_t)r * a.s, v, Dout, a.conj_out, nonfinite);
-  }
-}
-
 // Launch interface of the specialised kernels (one translation unit per
 // policy, compiled in parallel): efft_fx_df2.cu (complex128, packed
 // double-float), efft_fx_f32.cu (complex64).

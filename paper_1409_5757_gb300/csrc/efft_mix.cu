@@ -1,5 +1,5 @@
 // efft_mix.cu -- launches of the mixed-radix pass kernel (efft_pass_mix in
-// efft_kernels.cuh) for transform lengths N = M * 2^e with M odd (the
+// efft_mix.cuh) for transform lengths N = M * 2^e with M odd (the
 // paper's size set N = M * 2^s, Sec. 2.1).  A translation unit of its own:
 // the kernel is instantiated for every odd radix and compiles in parallel
 // with the others.
@@ -10,6 +10,7 @@
 #include "../../include/efft.h"
 #include "efft_host.h"
 #include "efft_kernels.cuh"
+#include "efft_mix.cuh"
 
 using namespace efft;
 using namespace efft::host;

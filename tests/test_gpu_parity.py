@@ -249,3 +249,18 @@ def test_c128_output_just_below_a_power_of_two(e):
             x[0] = v + 1j * v
             got = gpu_fft(x, "c128", -1)
             assert np.max(np.abs(got - (v + 1j * v))) <= 1e-15 * abs(v), (k, sgn)
+
+
+@pytest.mark.parametrize("e", [11, 16, 20, 24])
+@pytest.mark.parametrize("pattern", ["element", "column"])
+def test_c128_tiles_of_different_scales(orc, e, pattern):
+    """The complex128 scale is found per first-pass tile and reconciled in
+    the second pass: inputs whose binary exponents vary by up to 2^+-48
+    between elements, or between column groups (so that whole tiles differ),
+    still match the oracle."""
+    N = 1 << e
+    n = np.arange(N)
+    shift = ((n * 7919) % 97) - 48 if pattern == "element" else ((n % 4096) >> 6) % 97 - 48
+    x = orc.gen_uniform(60 + e, N) * np.ldexp(1.0, shift)
+    got = gpu_fft(x, "c128", -1)
+    check(got, orc.dft(x, -1), "c128", N, pattern)
