@@ -404,8 +404,9 @@ def run_ours(args, wl):
         inv = efft.Plan.real(2 * N, code, efft.EFFT_REAL_INVERSE, efft.EFFT_FLAG_NORMALIZE | tune)
     else:
         norm_flag = efft.EFFT_FLAG_NORMALIZE if wl.get("normalize", True) else 0
-        fwd = efft.Plan(N, code, -1, tune)
-        inv = efft.Plan(N, code, +1, norm_flag | tune)
+        rad = [int(v) for v in args.radices.split(",")] if args.radices else None
+        fwd = efft.Plan(N, code, -1, 0 if rad else tune, radices=rad)
+        inv = efft.Plan(N, code, +1, norm_flag | (0 if rad else tune), radices=rad)
     fpt = flops_real(2 * N) if real else flops(N)  # flop per transform
     stream = torch.cuda.current_stream(dev)
     sp = stream.cuda_stream
@@ -491,7 +492,9 @@ def run_ours(args, wl):
                     "frac": achieved / peak, "traffic": tr["bytes"] if tr else None,
                     "traffic_source": tr["source"] if tr else None,
                     "fp32_view": ({"fma_pipe_active_pct": tr["fma_pipe_pct"], "issue_active_pct": tr["issue_pct"],
-                                   "note": "the double-float pass kernels are bound by FP32 issue, not HBM"}
+                                   "note": ("the double-float pass kernels are bound by the FP32 pipe, not HBM"
+                                            if c128 else "the FP32 pass kernels are bound by the L1/LSU data "
+                                            "pipe and load latency, not HBM")}
                                   if tr else None),
                     "peak_kind": f"{peak_kind} STREAM-style copy (MEASURED_PEAKS.json hbm_gbs)",
                     "per_launch_ms": tot_ms / nl, "algorithmic_bytes_per_launch": alg_bytes,
@@ -745,6 +748,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg")
     ap.add_argument("--autotune", action="store_true",
                     help="plans with EFFT_FLAG_AUTOTUNE (measured radix schedules; c5 always tunes)")
+    ap.add_argument("--radices", default=None,
+                    help="explicit schedule, log2 radices comma-separated (profiling of one kernel variant)")
     ap.add_argument("--no-compare", action="store_true",
                     help="complex64 workloads: skip the complex128 run at the same N")
     ap.add_argument("--log2n", type=int, default=None,
