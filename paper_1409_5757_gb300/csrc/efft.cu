@@ -157,7 +157,7 @@ int apply_mixed_schedule(efft_plan_s* p) {
     ps.L_int = (np == 1) ? n : Ls[jj];
     ps.kind = (np == 1) ? SINGLE : (j == 0 ? FIRST : (j == 1 ? MID : LAST));
     ps.log2R = __builtin_ctzll(ps.R_int);  // the power-of-two part (efft_plan_radices)
-    // Stockham radices: the odd factor, then 4s, then a 2
+    // Stockham radices: the odd factor, then 16s, then one 8, 4 or 2
     uint64_t rest = ps.R_int;
     ps.nrad = 0;
     const uint64_t odd = rest / (rest & (~rest + 1));
@@ -165,11 +165,11 @@ int apply_mixed_schedule(efft_plan_s* p) {
       ps.rad[ps.nrad++] = (int)odd;
       rest /= odd;
     }
-    while (rest % 4 == 0) {
-      ps.rad[ps.nrad++] = 4;
-      rest /= 4;
+    while (rest % 16 == 0) {
+      ps.rad[ps.nrad++] = 16;
+      rest /= 16;
     }
-    if (rest == 2) ps.rad[ps.nrad++] = 2;
+    if (rest > 1) ps.rad[ps.nrad++] = (int)rest;
     // columns per CTA: a power of two dividing the stride (a CTA's columns
     // stay inside one block) and the column count
     const uint64_t ncol = n / ps.R_int;
@@ -180,7 +180,7 @@ int apply_mixed_schedule(efft_plan_s* p) {
     ps.C_int = C;
     ps.grid = ncol / (uint64_t)C;
     ps.threads = 256;
-    ps.smem = 2 * (size_t)C * ps.R_int * eb;
+    ps.smem = 2 * (size_t)C * ps.R_int * eb + ps.R_int * sizeof(float4);  // two buffers, the R-th roots
   }
   p->permute = (np == 3) && !(p->flags & EFFT_FLAG_DIGIT_REVERSED_OUT);
   p->perm_log2A = (np == 3) ? a : 0;

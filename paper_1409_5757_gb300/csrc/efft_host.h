@@ -39,9 +39,10 @@ struct Pass {
 
 // Largest odd factor M of a supported size N = M * 2^e.
 constexpr uint32_t kMaxOdd = 15;
-// Elements per CTA of the mixed-radix kernel (two shared buffers of 64 KiB).
+// Elements per CTA of the mixed-radix kernel (two buffers and the R-th roots
+// in shared memory: 96 KiB complex128, 64 KiB complex64).
 constexpr int kMixTileC128 = 2048;
-constexpr int kMixTileC64 = 4096;
+constexpr int kMixTileC64 = 2048;
 
 // The transforms one enqueue covers: ptrs (device array of `count` data
 // pointers, or NULL for one transform at the enqueue's `data`) and their

@@ -33,7 +33,6 @@ cudaError_t launch_mix_p(const efft_plan_s* p, const Pass& ps, void* data, const
   m.C = ps.C_int;
   m.nrad = ps.nrad;
   for (int i = 0; i < ps.nrad; ++i) m.rad[i] = ps.rad[i];
-  m.M = (int)p->odd;
   m.twB = p->twB;
   m.tw_lo = p->tw_lo;
   m.tw_hi = p->tw_hi;
@@ -60,12 +59,14 @@ namespace efft {
 namespace host {
 
 cudaError_t mix_set_attrs() {
-  const int mix128 = 2 * kMixTileC128 * (int)sizeof(cdf), mix64 = 2 * kMixTileC64 * (int)sizeof(float2);
+  // two buffers of the tile plus R <= tile roots (float4)
+  const int mix128 = kMixTileC128 * (2 * (int)sizeof(cdf2) + (int)sizeof(float4));
+  const int mix64 = kMixTileC64 * (2 * (int)sizeof(float2) + (int)sizeof(float4));
   const cudaFuncAttribute attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
-  cudaError_t e[8] = {cudaFuncSetAttribute(efft_pass_mix<PolicyDF, FIRST>, attr, mix128),
-                      cudaFuncSetAttribute(efft_pass_mix<PolicyDF, MID>, attr, mix128),
-                      cudaFuncSetAttribute(efft_pass_mix<PolicyDF, LAST>, attr, mix128),
-                      cudaFuncSetAttribute(efft_pass_mix<PolicyDF, SINGLE>, attr, mix128),
+  cudaError_t e[8] = {cudaFuncSetAttribute(efft_pass_mix<PolicyDF2, FIRST>, attr, mix128),
+                      cudaFuncSetAttribute(efft_pass_mix<PolicyDF2, MID>, attr, mix128),
+                      cudaFuncSetAttribute(efft_pass_mix<PolicyDF2, LAST>, attr, mix128),
+                      cudaFuncSetAttribute(efft_pass_mix<PolicyDF2, SINGLE>, attr, mix128),
                       cudaFuncSetAttribute(efft_pass_mix<PolicyF32, FIRST>, attr, mix64),
                       cudaFuncSetAttribute(efft_pass_mix<PolicyF32, MID>, attr, mix64),
                       cudaFuncSetAttribute(efft_pass_mix<PolicyF32, LAST>, attr, mix64),
@@ -76,7 +77,7 @@ cudaError_t mix_set_attrs() {
 }
 
 cudaError_t launch_mix(const efft_plan_s* p, const Pass& ps, void* data, const Batch& bt, cudaStream_t st) {
-  return (p->dtype == EFFT_C128) ? launch_mix_p<PolicyDF>(p, ps, data, bt, st)
+  return (p->dtype == EFFT_C128) ? launch_mix_p<PolicyDF2>(p, ps, data, bt, st)
                                  : launch_mix_p<PolicyF32>(p, ps, data, bt, st);
 }
 

@@ -14,10 +14,11 @@ namespace efft {
 // the twiddle of Eq. 4), for any radix R = M' * 2^b (M' = 1 or M) and any
 // integer stride and block length.  The R-point DFT of each column is a
 // mixed-radix Stockham (self-sorting) sequence in shared memory: radices
-// 4, 2 and the odd factor, ping-ponging between two buffers, so every
-// column ends in natural order; odd radices are direct sums over the M-th
-// roots of unity.  Twiddles exp(-2*pi*i*idx/N) come from the two-level
-// table; every index used is < N (m*q < L for a pass twiddle).
+// 16, 8, 4, 2 and the odd factor, ping-ponging between two buffers, so every
+// column ends in natural order; odd radices are direct sums.  The R-th roots
+// of unity are computed once per CTA into shared memory and serve every
+// stage twiddle and the odd radix; the pass twiddle exp(-2*pi*i*m*q/L) comes
+// from the two-level table of exp(-2*pi*i*idx/N) (idx = m*q*N/L < N).
 // ----------------------------------------------------------------------------
 struct MixArgs {
   uint64_t N;      // transform length
@@ -25,7 +26,6 @@ struct MixArgs {
   int R, C;        // radix and columns per CTA
   int nrad;        // Stockham stages
   int rad[8];      // their radices (product R)
-  int M;           // odd factor of N (its roots are cached)
   int twB;         // low-table bits of the two-level table
   const float4* tw_lo;
   const float4* tw_hi;
@@ -39,48 +39,19 @@ __device__ __forceinline__ float4 twiddle_mix(const MixArgs& a, uint64_t idx) {
   return tw_mul(__ldg(a.tw_hi + (idx >> a.twB)), __ldg(a.tw_lo + (idx & ((1ull << a.twB) - 1ull))));
 }
 
-// Y[q] = sum_r v[r] exp(-2*pi*i*q*r/p), natural order, p in {2, 4, odd <= 15}.
-template <class P, int p>
-__device__ __forceinline__ void small_dft(typename P::V* v, const float4* roots) {
-  typedef typename P::V V;
-  if (p == 2) {
-    const V a0 = v[0], a1 = v[1];
-    v[0] = P::add(a0, a1);
-    v[1] = P::sub(a0, a1);
-  } else if (p == 4) {
-    const V s02 = P::add(v[0], v[2]), d02 = P::sub(v[0], v[2]);
-    const V s13 = P::add(v[1], v[3]), d13 = P::mul_negi(P::sub(v[1], v[3]));
-    v[0] = P::add(s02, s13);
-    v[2] = P::sub(s02, s13);
-    v[1] = P::add(d02, d13);
-    v[3] = P::sub(d02, d13);
-  } else {
-    V y[p];
-#pragma unroll
-    for (int q = 0; q < p; ++q) {
-      V acc = v[0];
-#pragma unroll
-      for (int r = 1; r < p; ++r) {
-        const int j = (q * r) % p;
-        acc = P::add(acc, j ? P::mul_tw(v[r], roots[j]) : v[r]);
-      }
-      y[q] = acc;
-    }
-#pragma unroll
-    for (int q = 0; q < p; ++q) v[q] = y[q];
-  }
-}
-
 // One Stockham stage of radix p over the C columns of a tile: work item
 // (column c, j < R/p) reads v[r] = in[j + r R/p], multiplies by
-// exp(-2*pi*i*k*r/(Ns p)) (k = j mod Ns), transforms and writes
-// out[(j/Ns) Ns p + k + r Ns].
+// exp(-2*pi*i*k*r/(Ns p)) = roots[k r R/(Ns p)] (k = j mod Ns), takes the
+// p-point DFT Y[q] = sum_r v[r] exp(-2*pi*i*q*r/p) (roots[q r R/p]) and
+// writes Y[q] to out[(j/Ns) Ns p + k + q Ns].  Radices 8 and 16 run the
+// in-register DIF butterflies of the power-of-two passes, 2 and 4 direct
+// butterflies; an odd radix is a direct sum whose outputs go straight to
+// shared memory one by one (only the p inputs stay in registers).
 template <class P, int p>
 __device__ __forceinline__ void mix_stage(const typename P::V* in, typename P::V* out, int R, int C, int Ns,
-                                          const MixArgs& a, const float4* roots) {
+                                          const float4* roots) {
   typedef typename P::V V;
-  const int Rp = R / p;
-  const uint64_t unit = a.N / (uint64_t)(Ns * p);
+  const int Rp = R / p, tstep = R / (Ns * p);
   for (int w = threadIdx.x; w < C * Rp; w += blockDim.x) {
     const int c = w / Rp, j = w - c * Rp, k = j % Ns;
     V v[p];
@@ -88,25 +59,52 @@ __device__ __forceinline__ void mix_stage(const typename P::V* in, typename P::V
     for (int r = 0; r < p; ++r) v[r] = in[c * R + j + r * Rp];
     if (k) {
 #pragma unroll
-      for (int r = 1; r < p; ++r) v[r] = P::mul_tw(v[r], twiddle_mix(a, (uint64_t)(k * r) * unit));
+      for (int r = 1; r < p; ++r) v[r] = P::mul_tw(v[r], P::expand(roots[k * r * tstep]));
     }
-    small_dft<P, p>(v, roots);
-    const int d = (j / Ns) * Ns * p + k;
+    V* o = out + c * R + (j / Ns) * Ns * p + k;
+    if (p == 8 || p == 16) {
+      // in-register decimation in frequency: register u holds Y[bitrev(u)]
+      constexpr int LOG = (p == 16) ? 4 : 3;
+      dif_regs<P, LOG>(v);
 #pragma unroll
-    for (int r = 0; r < p; ++r) out[c * R + d + r * Ns] = v[r];
+      for (int u = 0; u < p; ++u) o[bitrev_c(u, LOG) * Ns] = v[u];
+    } else if (p == 2) {
+      o[0] = P::add(v[0], v[1]);
+      o[Ns] = P::sub(v[0], v[1]);
+    } else if (p == 4) {
+      const V s02 = P::add(v[0], v[2]), d02 = P::sub(v[0], v[2]);
+      const V s13 = P::add(v[1], v[3]), d13 = P::mul_negi(P::sub(v[1], v[3]));
+      o[0] = P::add(s02, s13);
+      o[2 * Ns] = P::sub(s02, s13);
+      o[Ns] = P::add(d02, d13);
+      o[3 * Ns] = P::sub(d02, d13);
+    } else {
+      V acc = v[0];
+#pragma unroll
+      for (int r = 1; r < p; ++r) acc = P::add(acc, v[r]);
+      o[0] = acc;
+#pragma unroll 1
+      for (int q = 1; q < p; ++q) {
+        acc = v[0];
+#pragma unroll
+        for (int r = 1; r < p; ++r) acc = P::add(acc, P::mul_tw(v[r], P::expand(roots[((q * r) % p) * Rp])));
+        o[q * Ns] = acc;
+      }
+    }
   }
 }
 
+// Dynamic shared memory: two buffers of C*R values, then R roots.
 template <class P, int KIND>
-__global__ void __launch_bounds__(256) efft_pass_mix(void* __restrict__ data, const MixArgs a) {
+__global__ void __launch_bounds__(256, 2) efft_pass_mix(void* __restrict__ data, const MixArgs a) {
   typedef typename P::V V;
   if (a.ptrs) data = a.ptrs[blockIdx.y];
   const uint32_t* state = a.state + (a.ptrs ? 4u * blockIdx.y : 0u);
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ float4 roots[16];
   const int R = a.R, C = a.C, CR = R * C;
   V* in = reinterpret_cast<V*>(smem_raw);
   V* out = in + CR;
+  float4* roots = reinterpret_cast<float4*>(out + CR);
 
   int D = 0, Dout = a.out_shift;
   bool nonfinite = false;
@@ -116,7 +114,9 @@ __global__ void __launch_bounds__(256) efft_pass_mix(void* __restrict__ data, co
     Dout = D - a.out_shift;
     nonfinite = (emax >= 0x7FFu);
   }
-  if ((int)threadIdx.x < a.M) roots[threadIdx.x] = twiddle_mix(a, (uint64_t)threadIdx.x * (a.N / (uint64_t)a.M));
+  // exp(-2*pi*i*j/R), j < R
+  const uint64_t runit = a.N / (uint64_t)R;
+  for (int j = threadIdx.x; j < R; j += blockDim.x) roots[j] = twiddle_mix(a, (uint64_t)j * runit);
 
   const uint64_t jcol0 = (uint64_t)blockIdx.x * C;
   const bool strided = (a.s > 1);
@@ -134,15 +134,17 @@ __global__ void __launch_bounds__(256) efft_pass_mix(void* __restrict__ data, co
   for (int st = 0; st < a.nrad; ++st) {
     const int p = a.rad[st];
     switch (p) {
-      case 2: mix_stage<P, 2>(in, out, R, C, Ns, a, roots); break;
-      case 4: mix_stage<P, 4>(in, out, R, C, Ns, a, roots); break;
-      case 3: mix_stage<P, 3>(in, out, R, C, Ns, a, roots); break;
-      case 5: mix_stage<P, 5>(in, out, R, C, Ns, a, roots); break;
-      case 7: mix_stage<P, 7>(in, out, R, C, Ns, a, roots); break;
-      case 9: mix_stage<P, 9>(in, out, R, C, Ns, a, roots); break;
-      case 11: mix_stage<P, 11>(in, out, R, C, Ns, a, roots); break;
-      case 13: mix_stage<P, 13>(in, out, R, C, Ns, a, roots); break;
-      default: mix_stage<P, 15>(in, out, R, C, Ns, a, roots); break;
+      case 2: mix_stage<P, 2>(in, out, R, C, Ns, roots); break;
+      case 4: mix_stage<P, 4>(in, out, R, C, Ns, roots); break;
+      case 8: mix_stage<P, 8>(in, out, R, C, Ns, roots); break;
+      case 16: mix_stage<P, 16>(in, out, R, C, Ns, roots); break;
+      case 3: mix_stage<P, 3>(in, out, R, C, Ns, roots); break;
+      case 5: mix_stage<P, 5>(in, out, R, C, Ns, roots); break;
+      case 7: mix_stage<P, 7>(in, out, R, C, Ns, roots); break;
+      case 9: mix_stage<P, 9>(in, out, R, C, Ns, roots); break;
+      case 11: mix_stage<P, 11>(in, out, R, C, Ns, roots); break;
+      case 13: mix_stage<P, 13>(in, out, R, C, Ns, roots); break;
+      default: mix_stage<P, 15>(in, out, R, C, Ns, roots); break;
     }
     __syncthreads();
     V* t = in;
@@ -159,7 +161,7 @@ __global__ void __launch_bounds__(256) efft_pass_mix(void* __restrict__ data, co
     const uint64_t col = jcol0 + c;
     const uint64_t m = col % a.s;
     V v = in[c * R + r];
-    if (strided && m != 0 && r != 0) v = P::mul_tw(v, twiddle_mix(a, m * (uint64_t)r * tw_unit));
+    if (strided && m != 0 && r != 0) v = P::mul_tw(v, P::expand(twiddle_mix(a, m * (uint64_t)r * tw_unit)));
     Mem<P, KIND>::store(data, (col / a.s) * a.L + m + (uint64_t)r * a.s, v, Dout, a.conj_out, nonfinite);
   }
 }
