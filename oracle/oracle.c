@@ -306,8 +306,7 @@ static int two_level_init(two_level* tl, int64_t N, int sign) {
   int e = ilog2_i64(N);
   tl->N = N;
   tl->B = (e + 1) / 2;
-  int64_t nlo = (int64_t)1 << tl->B, nhi = N >> tl->B;
-  if (nhi < 1) nhi = 1;
+  int64_t nlo = (int64_t)1 << tl->B, nhi = ((N - 1) >> tl->B) + 1; /* hi index of m <= N-1 */
   tl->lo = (double*)malloc(sizeof(double) * 2 * (size_t)nlo);
   tl->hi = (double*)malloc(sizeof(double) * 2 * (size_t)nhi);
   if (!tl->lo || !tl->hi) {
@@ -346,11 +345,11 @@ static void two_level_get(const two_level* tl, uint64_t m, double* wr, double* w
 /* Shared body: x_at(n, &re, &im) yields input n. */
 static int dft_bins_impl(const double* xarr, uint64_t seed, int64_t N, int sign,
                          const int64_t* ks, int64_t nk, double* X) {
-  if (!is_pow2(N) || (sign != 1 && sign != -1) || nk < 0 || (nk > 0 && (!ks || !X))) return -1;
+  if (N < 1 || (sign != 1 && sign != -1) || nk < 0 || (nk > 0 && (!ks || !X))) return -1;
   if (nk == 0) return 0;
   two_level tl;
   if (two_level_init(&tl, N, sign)) return -2;
-  const uint64_t mask = (uint64_t)N - 1;
+  const uint64_t UN = (uint64_t)N;
   int nth = oracle_threads();
   /* per-thread, per-bin compensated totals */
   nsum* acc = (nsum*)calloc((size_t)nth * (size_t)nk * 2, sizeof(nsum));
@@ -384,11 +383,12 @@ static int dft_bins_impl(const double* xarr, uint64_t seed, int64_t N, int sign,
         xb = blk;
       }
       for (int64_t j = 0; j < nk; j++) {
-        uint64_t k = (uint64_t)ks[j] & mask;
+        const uint64_t k = (uint64_t)(((ks[j] % N) + N) % N);
+        /* exact phase m = (n*k) mod N: 128-bit product at the block start,
+         * then one addition of k (mod N) per term */
+        uint64_t m = (uint64_t)(((unsigned __int128)(uint64_t)n0 * k) % UN);
         double sr = 0.0, si = 0.0;
-        for (int64_t i = 0; i < cnt; i++) {
-          uint64_t n = (uint64_t)(n0 + i);
-          uint64_t m = (n * k) & mask; /* exact (n*k) mod N, N | 2^64 */
+        for (int64_t i = 0; i < cnt; i++, m = (m + k >= UN) ? m + k - UN : m + k) {
           double wr, wi;
           two_level_get(&tl, m, &wr, &wi);
           double xr = xb[2 * i], xi = xb[2 * i + 1];

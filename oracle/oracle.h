@@ -75,10 +75,10 @@ uint64_t oracle_splitmix64(uint64_t seed, uint64_t i);
 /*
  * Sampled mode: X[k] of Eq. 1 for the nk frequencies ks[], where x is the
  * uniform input of oracle_gen_uniform(seed, 0, N) regenerated on the fly, so
- * no N-element array is ever held.  Phase (n*k) mod N is exact in 64-bit
- * integers; exp(sign*2*pi*i*m/N) = hi-table * lo-table (two levels, double);
- * partial sums over blocks of 4096 terms are combined with Neumaier
- * compensation.  N must be a power of two.  Returns 0 or -1 / -2 as above.
+ * no N-element array is ever held.  Any N >= 1.  Phase (n*k) mod N is exact
+ * in integers; exp(sign*2*pi*i*m/N) = hi-table * lo-table (two levels,
+ * double); partial sums over blocks of 4096 terms are combined with Neumaier
+ * compensation.  Returns 0 or -1 / -2 as above.
  */
 int oracle_dft_bins_uniform(uint64_t seed, int64_t N, int sign,
                             const int64_t* ks, int64_t nk, double* X);

@@ -290,6 +290,28 @@ def pin_bins_tone(o):
     assert np.max(np.abs(X[1:])) <= 1e-10 * N
 
 
+def pin_bins_any_size(o):
+    """Sizes N = M * 2^e (and odd N): the sampled direct sums equal numpy's
+    full transform, and a tone at f gives N at k = f."""
+    for N in (7, 13 * 64, 15 << 5, 5 << 7, 3 << 9):
+        e = int(np.ceil(np.log2(N)))
+        ks = np.array(sorted({0, 1, N // 2, N - 1, 5 % N, N // 3}), np.int64)
+        x = o.gen_uniform(11, N)
+        for sign in (-1, 1):
+            full = np.fft.fft(x) if sign == -1 else N * np.fft.ifft(x)
+            scale = np.linalg.norm(full) / np.sqrt(N)
+            Xb = o.dft_bins_uniform(11, N, ks, sign)
+            assert np.max(np.abs(Xb - full[ks])) <= 1e-14 * scale * e, (N, sign)
+            # negative and out-of-range frequencies are taken mod N
+            Xw = o.dft_bins_uniform(11, N, np.concatenate([ks - N, ks + 3 * N]), sign)
+            assert np.max(np.abs(Xw - np.concatenate([full[ks], full[ks]]))) <= 1e-14 * scale * e
+    N, f = 3 << 14, 4097
+    n = np.arange(N)
+    X = o.dft_bins(np.exp(2j * np.pi * ((f * n) % N) / N), [f, 0, 1, N - 1, N // 3], -1)
+    assert abs(X[0] - N) <= 1e-10 * N
+    assert np.max(np.abs(X[1:])) <= 1e-10 * N
+
+
 # --------------------------------------------------------------------------
 # Real data: the perm layout of Eq. 3 (Sec. 2.1)
 # --------------------------------------------------------------------------
