@@ -180,7 +180,22 @@ int apply_mixed_schedule(efft_plan_s* p) {
     ps.C_int = C;
     ps.grid = ncol / (uint64_t)C;
     ps.threads = 256;
-    ps.smem = 2 * (size_t)C * ps.R_int * eb + ps.R_int * sizeof(float4);  // two buffers, the R-th roots
+    const size_t cr = (size_t)C * ps.R_int;
+    ps.smem = 2 * (cr + cr / 16) * eb + ps.R_int * sizeof(float4);  // two padded buffers, the R-th roots
+    // outer passes of radix 2^8..2^11: the specialised power-of-two kernels
+    // (the first pass with stride M * 2^(e-a), the last on contiguous blocks)
+    if (np == 3 && j != 1 && a >= 8 && a <= 11) {
+      const int log2cta = (p->dtype == EFFT_C128) ? kLog2CtaC128 : kLog2CtaC64;
+      ps.mixed = false;
+      ps.log2s = (j == 0) ? e - a : 0;
+      ps.log2L = ps.log2s + a;
+      ps.wide = (p->dtype == EFFT_C128 && j == 0 && a >= 10 && n >= (1ull << kWideMinLog2N));
+      ps.log2C = (ps.wide ? kLog2CtaWide : log2cta) - a;
+      ps.grid = ncol >> ps.log2C;
+      ps.threads = 1 << (a + ps.log2C - 4);
+      const size_t elems = 1ull << (a + ps.log2C);
+      ps.smem = (elems + elems / 16 + 1) * eb;
+    }
   }
   p->permute = (np == 3) && !(p->flags & EFFT_FLAG_DIGIT_REVERSED_OUT);
   p->perm_log2A = (np == 3) ? a : 0;
@@ -371,6 +386,7 @@ cudaError_t launch_pass(const efft_plan_s* p, const Pass& ps, void* data, const 
   a.conj_in = (ps.kind == FIRST || ps.kind == SINGLE) ? conj : 0u;
   a.conj_out = (ps.kind == LAST || ps.kind == SINGLE) ? conj : 0u;
   a.out_shift = ((p->flags & EFFT_FLAG_NORMALIZE) && (ps.kind == LAST || ps.kind == SINGLE)) ? p->log2n : 0;
+  a.s_odd = (ps.kind == FIRST && p->odd > 1) ? p->odd : 1u;
   dim3 grid((unsigned)ps.grid, bt.count), block(ps.threads);
   constexpr int LOG2CTA = (P::kElemBytes == 16) ? kLog2CtaC128 : kLog2CtaC64;
   if (ps.wide) {
@@ -382,6 +398,7 @@ cudaError_t launch_pass(const efft_plan_s* p, const Pass& ps, void* data, const 
                                           : fx_launch_f32(ps.kind, ps.log2R, grid, block, ps.smem, st, data, a);
     if (ok) return cudaGetLastError();
   }
+  if (p->odd > 1) return cudaErrorInvalidConfiguration;  // only the specialised kernels take s_odd
   switch (ps.kind) {
     case FIRST: efft_pass<P, FIRST, CTA><<<grid, block, ps.smem, st>>>(data, a); break;
     case MID: efft_pass<P, MID, CTA><<<grid, block, ps.smem, st>>>(data, a); break;
@@ -885,6 +902,7 @@ int efft_internal_run_in_scratch(void* scratch, size_t scratch_bytes, bool regen
   p.dtype = dtype;
   p.sign = sign;
   p.flags = flags;
+  p.odd = 1;  // powers of two only
   const int e = p.log2n;
   int r[kMaxPasses] = {0, 0, 0, 0};
   apply_schedule(&p, r, choose_radices(e, r));

@@ -39,8 +39,8 @@ struct Pass {
 
 // Largest odd factor M of a supported size N = M * 2^e.
 constexpr uint32_t kMaxOdd = 15;
-// Elements per CTA of the mixed-radix kernel (two buffers and the R-th roots
-// in shared memory: 96 KiB complex128, 64 KiB complex64).
+// Elements per CTA of the mixed-radix kernel (two padded buffers and the R-th
+// roots in shared memory: 100 KiB complex128, 66 KiB complex64).
 constexpr int kMixTileC128 = 2048;
 constexpr int kMixTileC64 = 2048;
 

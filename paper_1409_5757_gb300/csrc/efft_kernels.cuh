@@ -42,6 +42,8 @@ struct PassArgs {
   uint32_t conj_in;      // 1: conjugate the input (sign = +1 transforms)
   uint32_t conj_out;     // 1: conjugate the output
   int out_shift;         // output multiplied by 2^-out_shift (1/N normalisation)
+  uint32_t s_odd;        // first pass of N = M * 2^e: stride s = s_odd * 2^log2s
+                         // (s_odd = M); 1 for power-of-two N
 };
 
 // Shared-memory slot of (position p, column c): one pad slot per 16 keeps the
@@ -437,7 +439,12 @@ efft_pass_fx(void* __restrict__ data, const PassArgs a) {
   const int t = CM ? (tid & (TPC - 1)) : (tid >> LC);
   const uint64_t jcol = (uint64_t)blockIdx.x * C + c;
   uint64_t m = 0, colbase, step;
-  if (STRIDED) {
+  if (KIND == FIRST) {
+    // the first pass spans the whole array (L = N): column j starts at j
+    step = (uint64_t)a.s_odd << a.log2s;
+    m = jcol;
+    colbase = jcol;
+  } else if (STRIDED) {
     step = 1ull << a.log2s;
     m = jcol & (step - 1);
     colbase = ((jcol >> a.log2s) << a.log2L) + m;
@@ -458,11 +465,11 @@ efft_pass_fx(void* __restrict__ data, const PassArgs a) {
   const int kt = digit_rev_c(t << 4, LR);
   typename P::TW wt;
   if (STRIDED) {
-    const int sh = a.log2N - a.log2L;
+    const int sh = (KIND == FIRST) ? 0 : a.log2N - a.log2L;
     // V_c[u] stored as [u][c]: the columns of one warp read consecutive entries
     if (tid < 16 * C) {
       const int cc = tid >> 4, u = tid & 15;
-      const uint64_t mc = ((uint64_t)blockIdx.x * C + cc) & (step - 1);
+      const uint64_t mc = ((uint64_t)blockIdx.x * C + cc) & (KIND == FIRST ? ~0ull : step - 1);
       const int kc = digit_rev_c(last_pos_c(u, REM), LR);
       vtw[u * C + cc] = P::expand(twiddle_N(a, (mc * (uint64_t)kc) << sh));
     }
@@ -527,7 +534,8 @@ efft_pass_fx(void* __restrict__ data, const PassArgs a) {
     for (int u = 0; u < 16; ++u) {
       const int k = kt | digit_rev_c(last_pos_c(u, REM), LR);
       v[u] = P::pass_tw(v[u], wt, vtw[u * C + c]);
-      Mem<P, KIND>::store(data, colbase + ((uint64_t)k << a.log2s), v[u], Dout, a.conj_out, nonfinite);
+      const uint64_t off = (KIND == FIRST) ? ((uint64_t)(k * a.s_odd) << a.log2s) : ((uint64_t)k << a.log2s);
+      Mem<P, KIND>::store(data, colbase + off, v[u], Dout, a.conj_out, nonfinite);
     }
   } else {
     __syncthreads();  // last-stage reads are complete before the slots are reused

@@ -17,9 +17,12 @@ using namespace efft::host;
 
 namespace {
 
+static_assert(kMixTileC128 <= kMixThreads * kMixPerThread && kMixTileC64 <= kMixThreads * kMixPerThread,
+              "a tile is loaded and stored in kMixPerThread elements per thread");
+
 template <class P, int KIND>
 void launch_mix_kind(const MixArgs& m, const Pass& ps, void* data, unsigned count, cudaStream_t st) {
-  efft_pass_mix<P, KIND><<<dim3((unsigned)ps.grid, count), ps.threads, ps.smem, st>>>(data, m);
+  efft_pass_mix<P, KIND><<<dim3((unsigned)ps.grid, count), kMixThreads, ps.smem, st>>>(data, m);
 }
 
 template <class P>
@@ -31,6 +34,7 @@ cudaError_t launch_mix_p(const efft_plan_s* p, const Pass& ps, void* data, const
   m.L = ps.L_int;
   m.R = (int)ps.R_int;
   m.C = ps.C_int;
+  m.log2C = __builtin_ctz((unsigned)ps.C_int);
   m.nrad = ps.nrad;
   for (int i = 0; i < ps.nrad; ++i) m.rad[i] = ps.rad[i];
   m.twB = p->twB;
@@ -59,9 +63,9 @@ namespace efft {
 namespace host {
 
 cudaError_t mix_set_attrs() {
-  // two buffers of the tile plus R <= tile roots (float4)
-  const int mix128 = kMixTileC128 * (2 * (int)sizeof(cdf2) + (int)sizeof(float4));
-  const int mix64 = kMixTileC64 * (2 * (int)sizeof(float2) + (int)sizeof(float4));
+  // two padded buffers of the tile plus R <= tile roots (float4)
+  const int mix128 = 2 * (kMixTileC128 + kMixTileC128 / 16) * (int)sizeof(cdf2) + kMixTileC128 * (int)sizeof(float4);
+  const int mix64 = 2 * (kMixTileC64 + kMixTileC64 / 16) * (int)sizeof(float2) + kMixTileC64 * (int)sizeof(float4);
   const cudaFuncAttribute attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
   cudaError_t e[8] = {cudaFuncSetAttribute(efft_pass_mix<PolicyDF2, FIRST>, attr, mix128),
                       cudaFuncSetAttribute(efft_pass_mix<PolicyDF2, MID>, attr, mix128),

@@ -23,7 +23,8 @@ namespace efft {
 struct MixArgs {
   uint64_t N;      // transform length
   uint64_t s, L;   // column stride and block length of this pass
-  int R, C;        // radix and columns per CTA
+  int R, C;        // radix and columns per CTA (C a power of two dividing s)
+  int log2C;
   int nrad;        // Stockham stages
   int rad[8];      // their radices (product R)
   int twB;         // low-table bits of the two-level table
@@ -38,6 +39,10 @@ struct MixArgs {
 __device__ __forceinline__ float4 twiddle_mix(const MixArgs& a, uint64_t idx) {
   return tw_mul(__ldg(a.tw_hi + (idx >> a.twB)), __ldg(a.tw_lo + (idx & ((1ull << a.twB) - 1ull))));
 }
+
+// Shared-memory slot of buffer index i: one pad slot per 16, so the
+// stride-p writes of a stage (p = 16 at Ns = 1) spread over the banks.
+__device__ __forceinline__ int mix_slot(int i) { return i + (i >> 4); }
 
 // One Stockham stage of radix p over the C columns of a tile: work item
 // (column c, j < R/p) reads v[r] = in[j + r R/p], multiplies by
@@ -56,55 +61,60 @@ __device__ __forceinline__ void mix_stage(const typename P::V* in, typename P::V
     const int c = w / Rp, j = w - c * Rp, k = j % Ns;
     V v[p];
 #pragma unroll
-    for (int r = 0; r < p; ++r) v[r] = in[c * R + j + r * Rp];
+    for (int r = 0; r < p; ++r) v[r] = in[mix_slot(c * R + j + r * Rp)];
     if (k) {
 #pragma unroll
       for (int r = 1; r < p; ++r) v[r] = P::mul_tw(v[r], P::expand(roots[k * r * tstep]));
     }
-    V* o = out + c * R + (j / Ns) * Ns * p + k;
+    const int ob = c * R + (j / Ns) * Ns * p + k;  // output q at ob + q*Ns
     if (p == 8 || p == 16) {
       // in-register decimation in frequency: register u holds Y[bitrev(u)]
       constexpr int LOG = (p == 16) ? 4 : 3;
       dif_regs<P, LOG>(v);
 #pragma unroll
-      for (int u = 0; u < p; ++u) o[bitrev_c(u, LOG) * Ns] = v[u];
+      for (int u = 0; u < p; ++u) out[mix_slot(ob + bitrev_c(u, LOG) * Ns)] = v[u];
     } else if (p == 2) {
-      o[0] = P::add(v[0], v[1]);
-      o[Ns] = P::sub(v[0], v[1]);
+      out[mix_slot(ob)] = P::add(v[0], v[1]);
+      out[mix_slot(ob + Ns)] = P::sub(v[0], v[1]);
     } else if (p == 4) {
       const V s02 = P::add(v[0], v[2]), d02 = P::sub(v[0], v[2]);
       const V s13 = P::add(v[1], v[3]), d13 = P::mul_negi(P::sub(v[1], v[3]));
-      o[0] = P::add(s02, s13);
-      o[2 * Ns] = P::sub(s02, s13);
-      o[Ns] = P::add(d02, d13);
-      o[3 * Ns] = P::sub(d02, d13);
+      out[mix_slot(ob)] = P::add(s02, s13);
+      out[mix_slot(ob + 2 * Ns)] = P::sub(s02, s13);
+      out[mix_slot(ob + Ns)] = P::add(d02, d13);
+      out[mix_slot(ob + 3 * Ns)] = P::sub(d02, d13);
     } else {
       V acc = v[0];
 #pragma unroll
       for (int r = 1; r < p; ++r) acc = P::add(acc, v[r]);
-      o[0] = acc;
+      out[mix_slot(ob)] = acc;
 #pragma unroll 1
       for (int q = 1; q < p; ++q) {
         acc = v[0];
 #pragma unroll
         for (int r = 1; r < p; ++r) acc = P::add(acc, P::mul_tw(v[r], P::expand(roots[((q * r) % p) * Rp])));
-        o[q * Ns] = acc;
+        out[mix_slot(ob + q * Ns)] = acc;
       }
     }
   }
 }
 
-// Dynamic shared memory: two buffers of C*R values, then R roots.
+// Threads per CTA and elements per thread of the tile load and store
+// (tiles of at most 2048 elements).
+constexpr int kMixThreads = 256;
+constexpr int kMixPerThread = 8;
+
+// Dynamic shared memory: two padded buffers of C*R values, then R roots.
 template <class P, int KIND>
-__global__ void __launch_bounds__(256, 2) efft_pass_mix(void* __restrict__ data, const MixArgs a) {
+__global__ void __launch_bounds__(kMixThreads, 2) efft_pass_mix(void* __restrict__ data, const MixArgs a) {
   typedef typename P::V V;
   if (a.ptrs) data = a.ptrs[blockIdx.y];
   const uint32_t* state = a.state + (a.ptrs ? 4u * blockIdx.y : 0u);
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int R = a.R, C = a.C, CR = R * C;
+  const int R = a.R, C = a.C, CR = R * C, CRP = CR + CR / 16;
   V* in = reinterpret_cast<V*>(smem_raw);
-  V* out = in + CR;
-  float4* roots = reinterpret_cast<float4*>(out + CR);
+  V* out = in + CRP;
+  float4* roots = reinterpret_cast<float4*>(out + CRP);
 
   int D = 0, Dout = a.out_shift;
   bool nonfinite = false;
@@ -118,15 +128,41 @@ __global__ void __launch_bounds__(256, 2) efft_pass_mix(void* __restrict__ data,
   const uint64_t runit = a.N / (uint64_t)R;
   for (int j = threadIdx.x; j < R; j += blockDim.x) roots[j] = twiddle_mix(a, (uint64_t)j * runit);
 
+  // The CTA's columns jcol0 .. jcol0 + C - 1 lie in one block (C divides s):
+  // column jcol0 + c, row r is at base0 + c * cstep + r * s.
   const uint64_t jcol0 = (uint64_t)blockIdx.x * C;
+  const uint64_t blk = jcol0 / a.s, m0 = jcol0 - blk * a.s;
+  const uint64_t base0 = blk * a.L + m0;
   const bool strided = (a.s > 1);
+  const uint64_t cstep = strided ? 1ull : a.L;
   // load: adjacent threads read adjacent columns of a row (strided) or
-  // adjacent elements of a column (contiguous blocks)
-  for (int e = threadIdx.x; e < CR; e += blockDim.x) {
-    const int r = strided ? e / C : e % R, c = strided ? e % C : e / R;
-    const uint64_t col = jcol0 + c;
-    const uint64_t base = (col / a.s) * a.L + (col % a.s);
-    in[c * R + r] = Mem<P, KIND>::load(data, base + (uint64_t)r * a.s, D, a.conj_in);
+  // adjacent elements of a column (contiguous blocks); all of a thread's
+  // loads are issued before the first shared-memory write
+  auto rc_of = [&](int e, int& r, int& c) {
+    if (strided) {
+      r = e >> a.log2C;
+      c = e & (C - 1);
+    } else {
+      c = e / R;
+      r = e - c * R;
+    }
+  };
+  {
+    V x[kMixPerThread];
+#pragma unroll
+    for (int i = 0; i < kMixPerThread; ++i) {
+      const int e = threadIdx.x + i * kMixThreads;
+      int r = 0, c = 0;
+      rc_of(e, r, c);
+      if (e < CR) x[i] = Mem<P, KIND>::load(data, base0 + c * cstep + (uint64_t)r * a.s, D, a.conj_in);
+    }
+#pragma unroll
+    for (int i = 0; i < kMixPerThread; ++i) {
+      const int e = threadIdx.x + i * kMixThreads;
+      int r = 0, c = 0;
+      rc_of(e, r, c);
+      if (e < CR) in[mix_slot(c * R + r)] = x[i];
+    }
   }
   __syncthreads();
 
@@ -156,13 +192,29 @@ __global__ void __launch_bounds__(256, 2) efft_pass_mix(void* __restrict__ data,
   // epilogue: in[c*R + q] holds X[q] of column c; the pass twiddle
   // exp(-2*pi*i*m*q/L) on strided passes, then the store
   const uint64_t tw_unit = a.N / a.L;
-  for (int e = threadIdx.x; e < CR; e += blockDim.x) {
-    const int r = strided ? e / C : e % R, c = strided ? e % C : e / R;
-    const uint64_t col = jcol0 + c;
-    const uint64_t m = col % a.s;
-    V v = in[c * R + r];
-    if (strided && m != 0 && r != 0) v = P::mul_tw(v, P::expand(twiddle_mix(a, m * (uint64_t)r * tw_unit)));
-    Mem<P, KIND>::store(data, (col / a.s) * a.L + m + (uint64_t)r * a.s, v, Dout, a.conj_out, nonfinite);
+  {
+    // twiddle lookups of all the thread's elements first, then the stores
+    float4 w[kMixPerThread];
+#pragma unroll
+    for (int i = 0; i < kMixPerThread; ++i) {
+      const int e = threadIdx.x + i * kMixThreads;
+      int r = 0, c = 0;
+      rc_of(e, r, c);
+      const uint64_t m = strided ? m0 + c : 0;
+      if (e < CR && m != 0 && r != 0) w[i] = twiddle_mix(a, m * (uint64_t)r * tw_unit);
+    }
+#pragma unroll
+    for (int i = 0; i < kMixPerThread; ++i) {
+      const int e = threadIdx.x + i * kMixThreads;
+      int r = 0, c = 0;
+      rc_of(e, r, c);
+      if (e < CR) {
+        V v = in[mix_slot(c * R + r)];
+        const uint64_t m = strided ? m0 + c : 0;
+        if (m != 0 && r != 0) v = P::mul_tw(v, P::expand(w[i]));
+        Mem<P, KIND>::store(data, base0 + c * cstep + (uint64_t)r * a.s, v, Dout, a.conj_out, nonfinite);
+      }
+    }
   }
 }
 

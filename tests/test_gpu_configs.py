@@ -120,6 +120,36 @@ def test_config_c3_2p33_complex128(orc):
     _free()
 
 
+def test_config_m1_3x2p28_complex128(orc):
+    """N = 3 * 2^28 complex128 (12 GiB), schedule (2^10, 3 * 2^8, 2^10): the
+    first pass on 8192-element tiles at stride 3 * 2^18, the middle pass on the
+    mixed-radix kernel.  Sampled bins, Parseval, and the unnormalised inverse
+    divided by N."""
+    import paper_1409_5757_gb300 as efft
+    from paper_1409_5757_gb300 import inputs
+    N, seed, e = 3 << 28, 8, 30
+    assert efft.Plan(N, efft.EFFT_C128, -1).radices() == [10, 8, 10]
+    x = torch.empty(N, dtype=torch.complex128, device="cuda")
+    inputs.fill_uniform(x, seed)
+    keep = x.clone()
+    sumsq = inputs.diff_norms(x)[0]
+    efft.fft_(x, -1)
+    torch.cuda.synchronize()
+    ssX = inputs.diff_norms(x)[0]
+    assert abs(ssX / (N * sumsq) - 1) <= 1e-14 * e
+    ks = np.concatenate([_ks(N, 12, 13), [N // 3, 2 * N // 3, N // 3 + 1]]).astype(np.int64)
+    got = x[torch.from_numpy(ks).cuda()].cpu().numpy()
+    ref = orc.dft_bins_uniform(seed, N, ks, -1)
+    err = math.sqrt(np.mean(np.abs(got - ref) ** 2)) / math.sqrt(sumsq)
+    assert err <= 1e-14 * e, err
+    efft.fft_(x, +1)
+    x.div_(N)
+    num, den = inputs.diff_norms(x, keep)
+    assert math.sqrt(num / den) <= 2e-14 * e
+    del x, keep
+    _free()
+
+
 def test_config_c4_2p31_complex64_gaussian(orc):
     """N = 2^31 complex64, Gaussian input; error vs the FP64 oracle on the
     FP32-rounded input promoted to FP64."""

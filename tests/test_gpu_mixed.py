@@ -89,6 +89,20 @@ def test_mixed_large(orc, name, N):
     _check(got, orc.dft(x, -1), name, N, "large")
 
 
+@pytest.mark.parametrize("name,N,a", [("c128", 5 << 20, 8), ("c64", 11 << 20, 8), ("c128", 9 << 22, 9),
+                                      ("c64", 13 << 22, 9), ("c64", 3 << 26, 9)])
+def test_mixed_outer_passes_on_specialised_kernels(orc, name, N, a):
+    """(2^a, M 2^b, 2^a) with a in 8..11: the outer passes run on the
+    power-of-two pass kernels (first pass at stride M * 2^(e-a)), the middle
+    one on the mixed-radix kernel; both signs against the full oracle."""
+    import paper_1409_5757_gb300 as efft
+    assert efft.Plan(N, _code(name), -1).radices()[::2] == [a, a]
+    x = host_input(orc, name, N, seed=N % 1000)
+    for sign in (-1, 1):
+        got, _ = _gpu(x, name, sign)
+        _check(got, orc.dft(x, sign), name, N, f"sign {sign}")
+
+
 def test_mixed_extreme_magnitudes_and_nan(orc):
     N = 3 << 12
     x = orc.gen_uniform(4, N)
