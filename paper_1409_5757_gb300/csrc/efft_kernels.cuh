@@ -419,7 +419,7 @@ efft_pass_fx(void* __restrict__ data, const PassArgs a) {
   // loads) and shared memory is column-major, raw index c*R + p; its stage-0
   // twiddles then differ per lane, so it is used only there.  Either way
   // slot = raw + raw/16 (one pad slot per 16).
-  constexpr bool CM = (KIND == LAST) && ((32 / C) * P::kElemBytes < 32);
+  constexpr bool CM = (KIND == LAST) && ((32 / C) * P::kElemBytes <= 32);
   constexpr int PS = CM ? 1 : C;  // raw step of one position p
   static_assert(LR >= 5 && LR <= 12, "radix range");
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -529,13 +529,21 @@ efft_pass_fx(void* __restrict__ data, const PassArgs a) {
     else dif_groups<P, (REM == 0 ? 4 : REM)>(v);
   }
 
-  if (STRIDED) {
+  if (STRIDED && (KIND != FIRST || a.s_odd == 1)) {
 #pragma unroll
     for (int u = 0; u < 16; ++u) {
       const int k = kt | digit_rev_c(last_pos_c(u, REM), LR);
       v[u] = P::pass_tw(v[u], wt, vtw[u * C + c]);
-      const uint64_t off = (KIND == FIRST) ? ((uint64_t)(k * a.s_odd) << a.log2s) : ((uint64_t)k << a.log2s);
-      Mem<P, KIND>::store(data, colbase + off, v[u], Dout, a.conj_out, nonfinite);
+      Mem<P, KIND>::store(data, colbase + ((uint64_t)k << a.log2s), v[u], Dout, a.conj_out, nonfinite);
+    }
+  } else if (STRIDED) {
+    // first pass of N = M * 2^e: output k at k * M * 2^log2s
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+      const int k = kt | digit_rev_c(last_pos_c(u, REM), LR);
+      v[u] = P::pass_tw(v[u], wt, vtw[u * C + c]);
+      Mem<P, KIND>::store(data, colbase + ((uint64_t)(k * a.s_odd) << a.log2s), v[u], Dout, a.conj_out,
+                          nonfinite);
     }
   } else {
     __syncthreads();  // last-stage reads are complete before the slots are reused

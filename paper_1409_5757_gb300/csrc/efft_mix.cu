@@ -25,6 +25,26 @@ void launch_mix_kind(const MixArgs& m, const Pass& ps, void* data, unsigned coun
   efft_pass_mix<P, KIND><<<dim3((unsigned)ps.grid, count), kMixThreads, ps.smem, st>>>(data, m);
 }
 
+// The middle pass with the odd factor fixed at compile time (efft_pass_mixm).
+template <class P, int M>
+void launch_mixm(const MixArgs& m, const Pass& ps, void* data, unsigned count, cudaStream_t st) {
+  efft_pass_mixm<P, M><<<dim3((unsigned)ps.grid, count), kMixThreads, ps.smem, st>>>(data, m);
+}
+
+template <class P>
+bool launch_mixm_odd(int odd, const MixArgs& m, const Pass& ps, void* data, unsigned count, cudaStream_t st) {
+  switch (odd) {
+    case 3: launch_mixm<P, 3>(m, ps, data, count, st); return true;
+    case 5: launch_mixm<P, 5>(m, ps, data, count, st); return true;
+    case 7: launch_mixm<P, 7>(m, ps, data, count, st); return true;
+    case 9: launch_mixm<P, 9>(m, ps, data, count, st); return true;
+    case 11: launch_mixm<P, 11>(m, ps, data, count, st); return true;
+    case 13: launch_mixm<P, 13>(m, ps, data, count, st); return true;
+    case 15: launch_mixm<P, 15>(m, ps, data, count, st); return true;
+    default: return false;
+  }
+}
+
 template <class P>
 cudaError_t launch_mix_p(const efft_plan_s* p, const Pass& ps, void* data, const Batch& bt, cudaStream_t st) {
   MixArgs m;
@@ -47,6 +67,13 @@ cudaError_t launch_mix_p(const efft_plan_s* p, const Pass& ps, void* data, const
   m.conj_out = (ps.kind == LAST || ps.kind == SINGLE) ? conj : 0u;
   // 1/N = 1/(M 2^e): the power of two here, 1/M is not exact and is not offered
   m.out_shift = ((p->flags & EFFT_FLAG_NORMALIZE) && (ps.kind == LAST || ps.kind == SINGLE)) ? p->log2n : 0;
+  // middle pass, R = M * 2^b with b >= 4, power-of-two stride, C <= 32
+  const uint64_t odd = ps.R_int / (ps.R_int & (~ps.R_int + 1));
+  m.log2b = __builtin_ctzll(ps.R_int);
+  m.log2s = __builtin_ctzll(ps.s_int);
+  if (ps.kind == MID && odd > 1 && m.log2b >= 4 && (ps.s_int & (ps.s_int - 1)) == 0 && ps.C_int <= 32 &&
+      launch_mixm_odd<P>((int)odd, m, ps, data, bt.count, st))
+    return cudaGetLastError();
   switch (ps.kind) {
     case FIRST: launch_mix_kind<P, FIRST>(m, ps, data, bt.count, st); break;
     case MID: launch_mix_kind<P, MID>(m, ps, data, bt.count, st); break;
@@ -76,6 +103,23 @@ cudaError_t mix_set_attrs() {
                       cudaFuncSetAttribute(efft_pass_mix<PolicyF32, LAST>, attr, mix64),
                       cudaFuncSetAttribute(efft_pass_mix<PolicyF32, SINGLE>, attr, mix64)};
   for (cudaError_t x : e)
+    if (x != cudaSuccess) return x;
+  const cudaError_t f[14] = {
+      cudaFuncSetAttribute(efft_pass_mixm<PolicyDF2, 3>, attr, mix128),
+      cudaFuncSetAttribute(efft_pass_mixm<PolicyDF2, 5>, attr, mix128),
+      cudaFuncSetAttribute(efft_pass_mixm<PolicyDF2, 7>, attr, mix128),
+      cudaFuncSetAttribute(efft_pass_mixm<PolicyDF2, 9>, attr, mix128),
+      cudaFuncSetAttribute(efft_pass_mixm<PolicyDF2, 11>, attr, mix128),
+      cudaFuncSetAttribute(efft_pass_mixm<PolicyDF2, 13>, attr, mix128),
+      cudaFuncSetAttribute(efft_pass_mixm<PolicyDF2, 15>, attr, mix128),
+      cudaFuncSetAttribute(efft_pass_mixm<PolicyF32, 3>, attr, mix64),
+      cudaFuncSetAttribute(efft_pass_mixm<PolicyF32, 5>, attr, mix64),
+      cudaFuncSetAttribute(efft_pass_mixm<PolicyF32, 7>, attr, mix64),
+      cudaFuncSetAttribute(efft_pass_mixm<PolicyF32, 9>, attr, mix64),
+      cudaFuncSetAttribute(efft_pass_mixm<PolicyF32, 11>, attr, mix64),
+      cudaFuncSetAttribute(efft_pass_mixm<PolicyF32, 13>, attr, mix64),
+      cudaFuncSetAttribute(efft_pass_mixm<PolicyF32, 15>, attr, mix64)};
+  for (cudaError_t x : f)
     if (x != cudaSuccess) return x;
   return cudaSuccess;
 }

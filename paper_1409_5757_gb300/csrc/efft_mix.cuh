@@ -34,6 +34,7 @@ struct MixArgs {
   void* const* ptrs;
   uint32_t conj_in, conj_out;
   int out_shift;
+  int log2b, log2s;  // middle-pass kernel: R = M * 2^log2b, s = 2^log2s
 };
 
 __device__ __forceinline__ float4 twiddle_mix(const MixArgs& a, uint64_t idx) {
@@ -214,6 +215,211 @@ __global__ void __launch_bounds__(kMixThreads, 2) efft_pass_mix(void* __restrict
         if (m != 0 && r != 0) v = P::mul_tw(v, P::expand(w[i]));
         Mem<P, KIND>::store(data, base0 + c * cstep + (uint64_t)r * a.s, v, Dout, a.conj_out, nonfinite);
       }
+    }
+  }
+}
+
+// ----------------------------------------------------------------------------
+// Middle pass of N = M * 2^e with the odd factor M fixed at compile time:
+// R = M * 2^b (b >= 4), stride s = 2^log2s, C = 2^log2C <= 32 columns per
+// CTA.  The same Stockham sequence as efft_pass_mix with the power-of-two
+// stages first (radix 8, then one of 2 or 4: Ns is a power of two and the
+// index arithmetic shifts; radix-16 stages spill at two CTAs per SM and
+// measured slower) and the odd stages last (9 = 3*3, 15 = 3*5); radix 3 is
+// the butterfly
+//   Y0 = v0 + t1, Y1,2 = v0 - t1/2 -/+ i (sqrt(3)/2)(v1 - v2), t1 = v1 + v2,
+// the others direct sums.  The pass twiddle exp(-2*pi*i*m*r/L) is factored
+// as in efft_pass_fx: a thread's elements r = r0 + i*RS of column c
+// (RS = threads / C) take W(m r0) * W(m RS i), the first formed once per
+// thread, the second from a table of kMixPerThread entries per column.
+// ----------------------------------------------------------------------------
+template <int M> struct MixOdd { static constexpr int p0 = M, p1 = 1; };
+template <> struct MixOdd<9> { static constexpr int p0 = 3, p1 = 3; };
+template <> struct MixOdd<15> { static constexpr int p0 = 3, p1 = 5; };
+
+// x times the real double-float constant c
+__device__ __forceinline__ cdf2 mix_scale(cdf2 x, df c) { return c2mulr(x, c); }
+__device__ __forceinline__ float2 mix_scale(float2 x, df c) {
+  return make_float2(__fmaf_rn(x.x, c.h, __fmul_rn(x.x, c.l)), __fmaf_rn(x.y, c.h, __fmul_rn(x.y, c.l)));
+}
+__device__ __forceinline__ df K_SQRT3_2() { return {0x1.bb67aep-1f, 0x1.0b0996p-26f}; }  // sqrt(3)/2
+
+// Power-of-two Stockham stage of radix Q = 2^LQ at Ns = 2^ls (see mix_stage).
+template <class P, int M, int LQ>
+__device__ __forceinline__ void mixm_pow2_stage(const typename P::V* in, typename P::V* out, int b, int lc, int ls,
+                                                const float4* roots) {
+  typedef typename P::V V;
+  constexpr int Q = 1 << LQ;
+  const int lrq = b - LQ, RQ = M << lrq, R = M << b;  // R/Q = M * 2^lrq
+  const int tsh = b - ls - LQ;                        // R/(Ns Q) = M * 2^tsh
+  const int items = RQ << lc, Ns = 1 << ls;
+  for (int w = threadIdx.x; w < items; w += kMixThreads) {
+    const int c = (w >> lrq) / M;
+    const int j = w - c * RQ;
+    const int k = j & (Ns - 1);
+    V v[Q];
+#pragma unroll
+    for (int r = 0; r < Q; ++r) v[r] = in[mix_slot(c * R + j + r * RQ)];
+    if (k) {
+#pragma unroll
+      for (int r = 1; r < Q; ++r) v[r] = P::mul_tw(v[r], P::expand(roots[(k * r * M) << tsh]));
+    }
+    const int ob = c * R + ((j - k) << LQ) + k;  // (j/Ns) Ns Q + k
+    if constexpr (Q >= 8) {
+      dif_regs<P, LQ>(v);
+#pragma unroll
+      for (int u = 0; u < Q; ++u) out[mix_slot(ob + bitrev_c(u, LQ) * Ns)] = v[u];
+    } else if constexpr (Q == 4) {
+      const V s02 = P::add(v[0], v[2]), d02 = P::sub(v[0], v[2]);
+      const V s13 = P::add(v[1], v[3]), d13 = P::mul_negi(P::sub(v[1], v[3]));
+      out[mix_slot(ob)] = P::add(s02, s13);
+      out[mix_slot(ob + 2 * Ns)] = P::sub(s02, s13);
+      out[mix_slot(ob + Ns)] = P::add(d02, d13);
+      out[mix_slot(ob + 3 * Ns)] = P::sub(d02, d13);
+    } else {
+      out[mix_slot(ob)] = P::add(v[0], v[1]);
+      out[mix_slot(ob + Ns)] = P::sub(v[0], v[1]);
+    }
+  }
+}
+
+// Odd Stockham stage of radix PO after odd stages of product PREV:
+// Ns = PREV * 2^b, R/PO = (M/PO) * 2^b.
+template <class P, int M, int PO, int PREV>
+__device__ __forceinline__ void mixm_odd_stage(const typename P::V* in, typename P::V* out, int b, int lc,
+                                               const float4* roots) {
+  typedef typename P::V V;
+  constexpr int RQM = M / PO, TST = M / (PREV * PO);  // R/(Ns PO) = TST
+  const int R = M << b, RQ = RQM << b, Ns = PREV << b;
+  const int items = RQ << lc;
+  for (int w = threadIdx.x; w < items; w += kMixThreads) {
+    const int c = (w >> b) / RQM;
+    const int j = w - c * RQ;
+    const int jq = (j >> b) / PREV;  // j / Ns
+    const int k = j - jq * Ns;
+    V v[PO];
+#pragma unroll
+    for (int r = 0; r < PO; ++r) v[r] = in[mix_slot(c * R + j + r * RQ)];
+    if (k) {
+#pragma unroll
+      for (int r = 1; r < PO; ++r) v[r] = P::mul_tw(v[r], P::expand(roots[k * r * TST]));
+    }
+    const int ob = c * R + jq * Ns * PO + k;
+    if constexpr (PO == 3) {
+      const V t1 = P::add(v[1], v[2]);
+      const V t2 = P::sub(v[0], mix_scale(t1, df{0.5f, 0.f}));
+      const V t3 = P::mul_negi(mix_scale(P::sub(v[1], v[2]), K_SQRT3_2()));
+      out[mix_slot(ob)] = P::add(v[0], t1);
+      out[mix_slot(ob + Ns)] = P::add(t2, t3);
+      out[mix_slot(ob + 2 * Ns)] = P::sub(t2, t3);
+    } else {
+      V acc = v[0];
+#pragma unroll
+      for (int r = 1; r < PO; ++r) acc = P::add(acc, v[r]);
+      out[mix_slot(ob)] = acc;
+#pragma unroll 1
+      for (int q = 1; q < PO; ++q) {
+        acc = v[0];
+#pragma unroll
+        for (int r = 1; r < PO; ++r) acc = P::add(acc, P::mul_tw(v[r], P::expand(roots[((q * r) % PO) * RQ])));
+        out[mix_slot(ob + q * Ns)] = acc;
+      }
+    }
+  }
+}
+
+// Dynamic shared memory: two padded buffers of C*R values, then R roots.
+template <class P, int M>
+__global__ void __launch_bounds__(kMixThreads, 2) efft_pass_mixm(void* __restrict__ data, const MixArgs a) {
+  typedef typename P::V V;
+  constexpr int KIND = MID;
+  if (a.ptrs) data = a.ptrs[blockIdx.y];
+  const uint32_t* state = a.state + (a.ptrs ? 4u * blockIdx.y : 0u);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ float4 vtab[kMixPerThread * 32];
+  __shared__ float4 wtab[kMixThreads];  // W_t of each thread, kept out of registers across the stages
+  const int b = a.log2b, lc = a.log2C, ls = a.log2s;
+  const int R = M << b, C = 1 << lc, CR = R << lc, CRP = CR + CR / 16;
+  V* in = reinterpret_cast<V*>(smem_raw);
+  V* out = in + CRP;
+  float4* roots = reinterpret_cast<float4*>(out + CRP);
+
+  int D = 0;
+  if (P::kElemBytes == 16) D = (int)__ldg(state) - 127;
+  const uint64_t runit = a.N / (uint64_t)R, tw_unit = a.N / a.L;
+  for (int j = threadIdx.x; j < R; j += kMixThreads) roots[j] = twiddle_mix(a, (uint64_t)j * runit);
+
+  // columns jcol0 .. jcol0 + C - 1, all in block jcol0 / s (C divides s)
+  const uint64_t jcol0 = (uint64_t)blockIdx.x << lc;
+  const uint64_t m0 = jcol0 & ((1ull << ls) - 1ull);
+  const uint64_t base0 = (jcol0 >> ls) * a.L + m0;
+  const int c = threadIdx.x & (C - 1), r0 = threadIdx.x >> lc, RS = kMixThreads >> lc;
+  // pass twiddle factors: V_c[i] = W(m_c RS i), W_t = W(m_c r0)
+  if (threadIdx.x < kMixPerThread * C) {
+    const int i = threadIdx.x >> lc;
+    if (i * RS < R) vtab[threadIdx.x] = twiddle_mix(a, (m0 + c) * (uint64_t)(i * RS) * tw_unit);
+  }
+  wtab[threadIdx.x] = (r0 < R) ? twiddle_mix(a, (m0 + c) * (uint64_t)r0 * tw_unit) : make_float4(1.f, 0.f, 0.f, 0.f);
+
+  {
+    V x[kMixPerThread];
+#pragma unroll
+    for (int i = 0; i < kMixPerThread; ++i) {
+      const int r = r0 + i * RS;
+      if (r < R) x[i] = Mem<P, KIND>::load(data, base0 + c + ((uint64_t)r << ls), D, 0u);
+    }
+#pragma unroll
+    for (int i = 0; i < kMixPerThread; ++i) {
+      const int r = r0 + i * RS;
+      if (r < R) in[mix_slot(c * R + r)] = x[i];
+    }
+  }
+  __syncthreads();
+
+  int s0 = 0;
+  for (; s0 + 3 <= b; s0 += 3) {
+    mixm_pow2_stage<P, M, 3>(in, out, b, lc, s0, roots);
+    __syncthreads();
+    V* t = in;
+    in = out;
+    out = t;
+  }
+  if (b > s0) {
+    switch (b - s0) {
+      case 1: mixm_pow2_stage<P, M, 1>(in, out, b, lc, s0, roots); break;
+      case 2: mixm_pow2_stage<P, M, 2>(in, out, b, lc, s0, roots); break;
+      default: mixm_pow2_stage<P, M, 3>(in, out, b, lc, s0, roots); break;
+    }
+    __syncthreads();
+    V* t = in;
+    in = out;
+    out = t;
+  }
+  constexpr int P0 = MixOdd<M>::p0, P1 = MixOdd<M>::p1;
+  mixm_odd_stage<P, M, P0, 1>(in, out, b, lc, roots);
+  __syncthreads();
+  {
+    V* t = in;
+    in = out;
+    out = t;
+  }
+  if constexpr (P1 > 1) {
+    mixm_odd_stage<P, M, P1, P0>(in, out, b, lc, roots);
+    __syncthreads();
+    V* t = in;
+    in = out;
+    out = t;
+  }
+
+  // epilogue: in[c*R + r] holds X[r] of column c
+  const typename P::TW wt = P::expand(wtab[threadIdx.x]);
+  const uint64_t base = (((uint64_t)blockIdx.x << lc) >> ls) * a.L + (((uint64_t)blockIdx.x << lc) & ((1ull << ls) - 1ull)) + c;
+#pragma unroll
+  for (int i = 0; i < kMixPerThread; ++i) {
+    const int r = (threadIdx.x >> lc) + i * RS;
+    if (r < R) {
+      const V v = P::pass_tw(in[mix_slot(c * R + r)], wt, P::expand(vtab[i * C + c]));
+      Mem<P, KIND>::store(data, base + ((uint64_t)r << ls), v, 0, 0u, false);
     }
   }
 }
