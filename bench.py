@@ -94,10 +94,14 @@ def job_rate(world: int, transforms_per_step: int, n: int, ms_per_step: float, r
     return world * transforms_per_step * f / (ms_per_step * 1e-3) / 1e9
 
 
-def kernel_fingerprint() -> str:
+def kernel_fingerprint(mixed: bool = False) -> str:
+    """sha1 (16 hex digits) of the sources of the power-of-two pass kernels,
+    or with mixed=True of the mixed-radix middle-pass kernel."""
     import hashlib
     h = hashlib.sha1()
-    for f in ("efft_kernels.cuh", "efft_arith.cuh", "efft_fx_df2.cu", "efft_fx_f32.cu"):
+    files = ("efft_kernels.cuh", "efft_arith.cuh") + (
+        ("efft_mix.cuh", "efft_mix.cu") if mixed else ("efft_fx_df2.cu", "efft_fx_f32.cu"))
+    for f in files:
         with open(os.path.join(ROOT, "paper_1409_5757_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -108,7 +112,7 @@ def measured_traffic(workload: str, log2n: int, kernel: str):
     or None when there is none for this kernel or the kernel changed since."""
     path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
     try:
-        fp = kernel_fingerprint()
+        fp = kernel_fingerprint(mixed=(workload == "m1" and kernel == "pass1"))
         with open(path) as f:
             for line in f:
                 if not line.strip() or line.startswith("#"):
@@ -757,6 +761,12 @@ def main():
     args = ap.parse_args()
     wl = dict(WORKLOADS[args.workload])
     if args.log2n is not None:
+        if "n" in wl:
+            # N = M * 2^e: keep M, scale 2^e (log2n is ceil(log2 N))
+            e = (wl["n"] & -wl["n"]).bit_length() - 1
+            odd, e_new = wl["n"] >> e, e + args.log2n - wl["log2n"]
+            wl["desc"] = wl["desc"].replace(f"{odd}*2^{e}", f"{odd}*2^{e_new}")
+            wl["n"] = odd << e_new
         wl["log2n"] = args.log2n
         wl["desc"] = wl["desc"].replace("2^30", f"2^{args.log2n}").replace("2^33", f"2^{args.log2n}")
     if args.steps is None:
