@@ -261,15 +261,19 @@ int efft_plan_profile_read(efft_plan_t plan, double* ms, int* count, int cap, in
  *               spectrum (F[N-k] = conj F[k]), a real result: N times the
  *               original data, or the original data with EFFT_FLAG_NORMALIZE.
  *  precision  EFFT_C64: float32 reals (4 bytes each); EFFT_C128: float64.
- *  n          number of reals, a power of two, 2 <= n <= 2^(EFFT_MAX_LOG2N+1).
- *  flags      EFFT_FLAG_NORMALIZE (multiply by 1/N), EFFT_FLAG_AUTOTUNE (for
- *             the complex plan); EFFT_FLAG_DIGIT_REVERSED_OUT is rejected.
+ *  n          number of reals, even, with n/2 a supported complex size
+ *             (n = M * 2^e, M odd <= EFFT_MAX_ODD, e >= 1,
+ *             2 <= n <= 2^(EFFT_MAX_LOG2N+1)).
+ *  flags      EFFT_FLAG_NORMALIZE (multiply by 1/N; powers of two only, as
+ *             for complex plans), EFFT_FLAG_AUTOTUNE (for the complex plan);
+ *             EFFT_FLAG_DIGIT_REVERSED_OUT is rejected.
  * The plan is executed with efft_execute / efft_execute_host /
  * efft_execute_host_stream like a complex plan (data: n reals, aligned to
  * two reals); efft_plan_radices reports the complex plan's radices and
  * efft_plan_autotune tunes it; batches take complex plans only.
- * Errors: as efft_plan_create (INVALID_SIZE for n < 2), INVALID_SIGN for
- * another direction, INVALID_FLAGS.
+ * Errors: as efft_plan_create (INVALID_SIZE for n < 2, odd n or n/2 not a
+ * supported size; UNSUPPORTED for EFFT_FLAG_NORMALIZE with M > 1),
+ * INVALID_SIGN for another direction, INVALID_FLAGS.
  */
 #define EFFT_REAL_FORWARD (-1)
 #define EFFT_REAL_INVERSE (+1)

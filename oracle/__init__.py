@@ -179,7 +179,7 @@ class Oracle:
         return F
 
     def rdft_perm(self, x, sign: int = -1) -> np.ndarray:
-        """Eq. 1 for real x (N a power of two >= 2), packed by pack_perm."""
+        """Eq. 1 for real x (N even >= 2), packed by pack_perm."""
         x = np.asarray(x, dtype=np.float64)
         return self.pack_perm(self.dft(x.astype(np.complex128), sign))
 

@@ -372,7 +372,7 @@ def _real_execute(t, direction: int, flags: int, stream):
 
 def rfft_(t, flags: int = 0, stream=None):
     """In-place real-data DFT of a contiguous 1-D CUDA float32/float64 tensor
-    of N = 2^e reals: afterwards t holds the perm layout
+    of N = M * 2^e reals (e >= 1, M odd <= 15): afterwards t holds the perm layout
     {R_0, R_{N/2}, R_1, I_1, ..., R_{N/2-1}, I_{N/2-1}} (Eq. 3)."""
     return _real_execute(t, EFFT_REAL_FORWARD, flags, stream)
 

@@ -6,12 +6,14 @@
 // half-length spectra of Eq. 4 are E_k = (Z_k + conj Z_{N/2-k})/2 and
 // O_k = (Z_k - conj Z_{N/2-k})/(2i), and F_k = E_k + W^k O_k (the butterfly
 // of Eqs. 5-6), F_{N/2-k} = conj(E_k - W^k O_k).  Writing A = Z_k + Q,
-// B = Z_k - Q (Q = conj Z_{N/2-k}) and using -i W^k = W^(k+N/4):
-//     F_k = (A + W^(k+N/4) B) / 2,   F_{N/2-k} = conj(A - W^(k+N/4) B) / 2,
+// B = Z_k - Q (Q = conj Z_{N/2-k}) and D = -i W^k B:
+//     F_k = (A + D) / 2,   F_{N/2-k} = conj(A - D) / 2,
 // so one kernel thread reads slots k and N/2-k and writes both back: the pair
-// is combined in place.  Slot 0 holds Z_0 and receives (F_0, F_{N/2}).  The
-// inverse runs the same step first, with conj(W) and without the 1/2, and
-// then the conjugate-sign complex transform.
+// is combined in place.  Slot 0 holds Z_0 and receives (F_0, F_{N/2}).  Any
+// even N: N = M * 2^e with the complex plan of N/2 = M * 2^(e-1) points; when
+// N/2 is odd no slot pairs with itself.  The inverse runs the same step
+// first, with conj(W), +i and without the 1/2, and then the conjugate-sign
+// complex transform.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -39,7 +41,7 @@ struct RealArgs {
   int out_shift;          // outputs multiplied by 2^-out_shift
 };
 
-// W^m (conj(W)^m for the inverse) for N/4 < m < N/2 from the two-level table.
+// W^m (conj(W)^m for the inverse) for 0 < m <= N/4 from the two-level table.
 __device__ __forceinline__ float4 w_of(const RealArgs& a, uint64_t m) {
   const uint32_t lo = (uint32_t)(m & ((1ull << a.rtwB) - 1ull));
   const uint32_t hi = (uint32_t)(m >> a.rtwB);
@@ -67,11 +69,17 @@ __global__ void __launch_bounds__(256) efft_real_pairs_f32(float2* __restrict__ 
       q = make_float2(zm.x, -zm.y);
     }
     const float2 A = PolicyF32::add(p, q), B = PolicyF32::sub(p, q);
-    // W^(k+N/4): exactly -i at k = 0 (conj: +i), -1 at k = N/4, else the table
+    // D = -i W^k B (inverse +i conj(W)^k B): exactly -i B at k = 0, -B at
+    // k = N/4 (N/2 even), else with W^k from the table
     float2 D;
-    if (k == 0) D = a.inverse ? make_float2(-B.y, B.x) : make_float2(B.y, -B.x);
-    else if (k == half) D = make_float2(-B.x, -B.y);
-    else D = PolicyF32::mul_tw(B, w_of(a, k + half));
+    if (k == 0) {
+      D = a.inverse ? make_float2(-B.y, B.x) : make_float2(B.y, -B.x);
+    } else if (2 * k == a.nh) {
+      D = make_float2(-B.x, -B.y);
+    } else {
+      const float2 wb = PolicyF32::mul_tw(B, w_of(a, k));
+      D = a.inverse ? make_float2(-wb.y, wb.x) : make_float2(wb.y, -wb.x);
+    }
     float2 x = PolicyF32::add(A, D), y = PolicyF32::sub(A, D);
     x = make_float2(__fmul_rn(x.x, sc), __fmul_rn(x.y, sc));
     y = make_float2(__fmul_rn(y.x, sc), __fmul_rn(-y.y, sc));  // conj
@@ -117,11 +125,17 @@ __global__ void __launch_bounds__(256) efft_real_pairs_df(uint4* __restrict__ z,
       }
     }
     const cdf2 A = c2add(p, q), B = c2sub(p, q);
-    // W^(k+N/4): exactly -i at k = 0 (conj: +i), -1 at k = N/4, else the table
+    // D = -i W^k B (inverse +i conj(W)^k B): exactly -i B at k = 0, -B at
+    // k = N/4 (N/2 even), else with W^k from the table
     cdf2 Dv;
-    if (k == 0) Dv = a.inverse ? c2negi(c2negi(c2negi(B))) : c2negi(B);
-    else if (k == half) Dv = cdf2{f2neg(B.h), f2neg(B.l)};
-    else Dv = c2mul(B, tw_expand(w_of(a, k + half)));
+    if (k == 0) {
+      Dv = a.inverse ? c2negi(c2negi(c2negi(B))) : c2negi(B);
+    } else if (2 * k == a.nh) {
+      Dv = cdf2{f2neg(B.h), f2neg(B.l)};
+    } else {
+      const cdf2 wb = c2mul(B, tw_expand(w_of(a, k)));
+      Dv = a.inverse ? c2negi(c2negi(c2negi(wb))) : c2negi(wb);
+    }
     const cdf2 x = c2add(A, Dv), y = c2sub(A, Dv);
     uint4 ox, oy;
     df_to_f64bits(df{x.h.x, x.l.x}, Dout, 0u, ox.x, ox.y);
@@ -207,7 +221,8 @@ extern "C" int efft_plan_create_real(efft_plan_t* out, uint64_t n, int precision
                                      uint32_t flags) {
   if (!out) return EFFT_ERR_INVALID_PTR;
   *out = nullptr;
-  if (n < 2 || (n & (n - 1)) != 0 || n > (1ull << (EFFT_MAX_LOG2N + 1))) return EFFT_ERR_INVALID_SIZE;
+  if (n < 2 || (n & 1) != 0 || n > (1ull << (EFFT_MAX_LOG2N + 1)) || !valid_size(n >> 1))
+    return EFFT_ERR_INVALID_SIZE;
   if (precision != EFFT_C64 && precision != EFFT_C128) return EFFT_ERR_INVALID_DTYPE;
   if (direction != EFFT_REAL_FORWARD && direction != EFFT_REAL_INVERSE) return EFFT_ERR_INVALID_SIGN;
   if (flags & ~(EFFT_FLAG_NORMALIZE | EFFT_FLAG_AUTOTUNE)) return EFFT_ERR_INVALID_FLAGS;
@@ -234,8 +249,8 @@ extern "C" int efft_plan_create_real(efft_plan_t* out, uint64_t n, int precision
   p->flags = flags;
   p->real = direction;
   p->inner = inner;
-  // W table exp(-2*pi*i*m/N) for m < N/2, two-level
-  const int em = p->log2n - 1;  // bits of m
+  // W table exp(-2*pi*i*m/N) for m < 2^em (>= N/2), two-level
+  const int em = p->log2n - 1;  // log2n = ceil(log2 N)
   p->rtwB = (em + 1) / 2;
   const uint64_t nlo = 1ull << p->rtwB, nhi = 1ull << (em - p->rtwB);
   cudaStream_t st = nullptr;

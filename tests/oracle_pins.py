@@ -321,8 +321,8 @@ def pin_real_perm_closed_forms(o):
     {R_0, R_{N/2}, R_1, I_1, ..., R_{N/2-1}, I_{N/2-1}}:
     cos(2 pi f n / N) -> R_f = N/2; sin(2 pi f n / N) -> I_f = -N/2 (sign -1);
     delta_0 -> every R_k = 1, I_k = 0; a constant c -> R_0 = N c;
-    (-1)^n -> R_{N/2} = N."""
-    for N in (2, 4, 8, 64, 1024, 8192):
+    (-1)^n -> R_{N/2} = N.  Powers of two and N = M * 2^e (N/2 odd too)."""
+    for N in (2, 4, 8, 64, 1024, 8192, 6, 10, 30, 12, 96, 5 << 7, 15 << 9):
         n = np.arange(N)
         tol = 1e-14 * N
         for f in range(1, N // 2):
@@ -350,7 +350,7 @@ def pin_real_perm_closed_forms(o):
 
 def pin_real_perm_brute_force(o):
     """mpmath's Eq. 1 on random real inputs, packed by hand into Eq. 3."""
-    for N, seed in ((2, 1), (4, 2), (8, 3), (16, 4), (32, 5)):
+    for N, seed in ((2, 1), (4, 2), (8, 3), (16, 4), (32, 5), (6, 6), (10, 7), (12, 8), (30, 9), (24, 10)):
         x = _rng(seed).uniform(-1, 1, N)
         X = _mp_dft(x, -1)
         want = [X[0].real, X[N // 2].real]
@@ -362,7 +362,7 @@ def pin_real_perm_brute_force(o):
 def pin_real_perm_round_trip(o):
     """irdft_perm(rdft_perm(x)) = N x, and the conjugate-sign inverse of a
     perm spectrum equals numpy's irfft of the same spectrum times N."""
-    for N in (2, 4, 16, 256, 4096, 1 << 14):
+    for N in (2, 4, 16, 256, 4096, 1 << 14, 6, 14, 30, 96, 3 << 10):
         x = _rng(N).uniform(-1, 1, N)
         assert _rel(o.irdft_perm(o.rdft_perm(x)), N * x) <= 1e-14 * np.log2(N) + 1e-16, N
         p = _rng(N + 1).uniform(-1, 1, N)

@@ -220,7 +220,8 @@ def test_real_plan_argument_errors_before_cuda(libs):
     h = ctypes.c_void_p()
     assert L.efft_plan_create_real(None, 16, 1, -1, 0) == 4
     assert L.efft_plan_create_real(ctypes.byref(h), 1, 1, -1, 0) == 1        # N < 2
-    assert L.efft_plan_create_real(ctypes.byref(h), 24, 1, -1, 0) == 1       # not a power of two
+    assert L.efft_plan_create_real(ctypes.byref(h), 34, 1, -1, 0) == 1       # N/2 = 17: odd factor > 15
+    assert L.efft_plan_create_real(ctypes.byref(h), 45, 1, -1, 0) == 1       # odd N
     assert L.efft_plan_create_real(ctypes.byref(h), 1 << 35, 1, -1, 0) == 1  # above 2^34 reals
     assert L.efft_plan_create_real(ctypes.byref(h), 16, 2, -1, 0) == 2       # precision
     assert L.efft_plan_create_real(ctypes.byref(h), 16, 1, 0, 0) == 3        # direction

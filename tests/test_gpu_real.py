@@ -92,6 +92,42 @@ def test_forward_normalised(orc, name):
     _check(got, orc.rdft_perm(x) / N, name, N, "normalised")
 
 
+REAL_MIXED = [6, 10, 14, 18, 22, 26, 30, 12, 20, 3 << 5, 5 << 9, 7 << 11, 9 << 8, 11 << 10, 13 << 7,
+              15 << 12, 3 << 20]
+
+
+@pytest.mark.parametrize("name", ["c128", "c64"])
+@pytest.mark.parametrize("N", REAL_MIXED)
+def test_mixed_sizes_forward_and_inverse(orc, name, N):
+    """N = M * 2^e reals (the paper's size set, Sec. 2.1): the complex plan of
+    N/2 = M * 2^(e-1) points, then the mirrored pairs; N/2 odd (N = 2M) has
+    no self-paired slot.  Forward and inverse against the oracle."""
+    x = _real_input(orc, name, N, 1300 + N % 997)
+    got, _ = _run(x, name, -1)
+    _check(got, orc.rdft_perm(x), name, N, "forward")
+    got, _ = _run(x, name, +1)
+    _check(got, orc.irdft_perm(x), name, N, "inverse")
+
+
+@pytest.mark.parametrize("name", ["c128", "c64"])
+def test_mixed_round_trip_and_rules(orc, name):
+    import paper_1409_5757_gb300 as efft
+    N = 5 << 14
+    x = _real_input(orc, name, N, 41)
+    t = torch.from_numpy(x.astype(np.float64 if name == "c128" else np.float32)).cuda()
+    efft.rfft_(t)
+    efft.irfft_(t, normalize=False)
+    got = t.cpu().numpy().astype(np.float64) / N
+    assert oracle.rel_l2(got.astype(np.complex128), x.astype(np.complex128)) <= 2 * TOL[name] * 17
+    code = efft.EFFT_C128 if name == "c128" else efft.EFFT_C64
+    with pytest.raises(efft.EfftError) as ei:
+        efft.Plan.real(N, code, efft.EFFT_REAL_FORWARD, efft.EFFT_FLAG_NORMALIZE)
+    assert ei.value.status == 9  # 1/N is not exact for M > 1
+    with pytest.raises(efft.EfftError) as ei:
+        efft.Plan.real(2 * 17, code, efft.EFFT_REAL_FORWARD)
+    assert ei.value.status == 1
+
+
 @pytest.mark.parametrize("name", ["c128", "c64"])
 def test_closed_forms_on_gpu(name):
     """cos(2 pi f n / N) -> R_f = N/2; (-1)^n -> R_{N/2} = N; delta -> ones.
