@@ -100,7 +100,7 @@ def kernel_fingerprint(mixed: bool = False) -> str:
     import hashlib
     h = hashlib.sha1()
     files = ("efft_kernels.cuh", "efft_arith.cuh") + (
-        ("efft_mix.cuh", "efft_mix.cu") if mixed else ("efft_fx_df2.cu", "efft_fx_f32.cu"))
+        ("efft_mix.cuh", "efft_mix.cu") if mixed else ("efft_fx_df2.cu", "efft_fx_f32.cu", "efft_fx32.cuh"))
     for f in files:
         with open(os.path.join(ROOT, "paper_1409_5757_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())

@@ -34,7 +34,7 @@ COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INC]
 LIBS = {
     "libefft.so": (["efft.cu", "efft_tune.cu", "efft_batch.cu", "efft_real.cu", "efft_mix.cu", "efft_fx_df2.cu",
                     "efft_fx_f32.cu", "efft_noalloc.cu"],
-                   ["efft_kernels.cuh", "efft_arith.cuh", "efft_mix.cuh", "efft_host.h"], ["efft.h"]),
+                   ["efft_kernels.cuh", "efft_arith.cuh", "efft_mix.cuh", "efft_fx32.cuh", "efft_host.h"], ["efft.h"]),
     "libefft_inputs.so": (["inputs.cu"], [], ["efft_inputs.h"]),
 }
 

@@ -189,8 +189,8 @@ int apply_mixed_schedule(efft_plan_s* p) {
       ps.mixed = false;
       ps.log2s = (j == 0) ? e - a : 0;
       ps.log2L = ps.log2s + a;
-      ps.wide = (p->dtype == EFFT_C128 && j == 0 && a >= 10 && n >= (1ull << kWideMinLog2N));
-      ps.log2C = (ps.wide ? kLog2CtaWide : log2cta) - a;
+      ps.wide = j == 0 && n >= (1ull << kWideMinLog2N) && (p->dtype == EFFT_C128 ? a >= 10 : a == 10);
+      ps.log2C = (ps.wide ? (p->dtype == EFFT_C128 ? kLog2CtaWide : kLog2CtaWideC64) : log2cta) - a;
       ps.grid = ncol >> ps.log2C;
       ps.threads = 1 << (a + ps.log2C - 4);
       const size_t elems = 1ull << (a + ps.log2C);
@@ -259,8 +259,10 @@ void apply_schedule(efft_plan_s* p, const int* r, int np) {
     else ps.kind = MID;
     // the first pass of a large complex128 array reads rows 2^(e-R) elements
     // apart, each in its own page; wider tiles move twice the bytes per row
-    ps.wide = (p->dtype == EFFT_C128 && ps.kind == FIRST && (r[j] == 10 || r[j] == 11) && e >= kWideMinLog2N);
-    int log2C = (ps.wide ? kLog2CtaWide : log2cta) - r[j];
+    // (complex64: 16384-element tiles of the radix-32 kernel, R = 2^10 only)
+    ps.wide = ps.kind == FIRST && e >= kWideMinLog2N &&
+              (p->dtype == EFFT_C128 ? (r[j] == 10 || r[j] == 11) : r[j] == 10);
+    int log2C = (ps.wide ? (p->dtype == EFFT_C128 ? kLog2CtaWide : kLog2CtaWideC64) : log2cta) - r[j];
     if (log2C > e - r[j]) log2C = e - r[j];
     ps.log2C = log2C;
     ps.grid = 1ull << (e - r[j] - log2C);
@@ -390,8 +392,9 @@ cudaError_t launch_pass(const efft_plan_s* p, const Pass& ps, void* data, const 
   dim3 grid((unsigned)ps.grid, bt.count), block(ps.threads);
   constexpr int LOG2CTA = (P::kElemBytes == 16) ? kLog2CtaC128 : kLog2CtaC64;
   if (ps.wide) {
-    if (fx_launch_df2_wide(ps.log2R, grid, block, ps.smem, st, data, a)) return cudaGetLastError();
-    return cudaErrorInvalidConfiguration;
+    const bool ok = (P::kElemBytes == 16) ? fx_launch_df2_wide(ps.log2R, grid, block, ps.smem, st, data, a)
+                                          : fx_launch_f32_wide(ps.log2R, grid, st, data, a);
+    return ok ? cudaGetLastError() : cudaErrorInvalidConfiguration;
   }
   if (ps.kind != SINGLE && ps.log2R >= 8 && ps.log2R <= 11 && ps.log2R + ps.log2C == LOG2CTA) {
     const bool ok = (P::kElemBytes == 16) ? fx_launch_df2(ps.kind, ps.log2R, grid, block, ps.smem, st, data, a)

@@ -1,0 +1,173 @@
+// efft_fx32.cuh -- the complex64 pass kernel for radix R = 2^10 as two
+// radix-32 stages (32 values per thread).  Included by efft_fx_f32.cu only.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "efft_kernels.cuh"
+
+namespace efft {
+
+// cos / sin of pi/16 and 3*pi/16 as (hi, lo) float pairs (the exp(-2*pi*i*e/32)
+// factors of the radix-32 butterflies; those of even e are the radix-16 ones).
+__device__ __forceinline__ df K_C1_32() { return {0x1.f6297cp-1f, 0x1.feeb96p-26f}; }
+__device__ __forceinline__ df K_S1_32() { return {0x1.8f8b84p-3f, -0x1.cb2cfap-30f}; }
+__device__ __forceinline__ df K_C3_32() { return {0x1.a9b662p-1f, 0x1.21d434p-26f}; }
+__device__ __forceinline__ df K_S3_32() { return {0x1.1c73b4p-1f, -0x1.9465cep-27f}; }
+
+// x * exp(-2*pi*i*e/32), e = 0..15 (compile-time after unrolling).
+template <class P>
+__device__ __forceinline__ typename P::V tw32(int e, typename P::V x) {
+  if ((e & 1) == 0) return tw16<P>(e >> 1, x);
+  // exp(-2*pi*i*e/32) = cos(pi e/16) - i sin(pi e/16)
+  switch (e) {
+    case 1: return P::mul_const(x, K_C1_32(), P::negd(K_S1_32()));
+    case 3: return P::mul_const(x, K_C3_32(), P::negd(K_S3_32()));
+    case 5: return P::mul_const(x, K_S3_32(), P::negd(K_C3_32()));
+    case 7: return P::mul_const(x, K_S1_32(), P::negd(K_C1_32()));
+    case 9: return P::mul_const(x, P::negd(K_S1_32()), P::negd(K_C1_32()));
+    case 11: return P::mul_const(x, P::negd(K_S3_32()), P::negd(K_C3_32()));
+    case 13: return P::mul_const(x, P::negd(K_C3_32()), P::negd(K_S3_32()));
+    default: return P::mul_const(x, P::negd(K_C1_32()), P::negd(K_S1_32()));
+  }
+}
+
+// In-register radix-32 decimation in frequency (the butterfly pair of
+// Eqs. 5-6 level by level); register u ends up holding output bitrev5(u).
+template <class P>
+__device__ __forceinline__ void dif32_regs(typename P::V* v) {
+#pragma unroll
+  for (int half = 16; half >= 1; half /= 2) {
+#pragma unroll
+    for (int blk = 0; blk < 32; blk += 2 * half) {
+#pragma unroll
+      for (int j = 0; j < half; ++j) {
+        typename P::V a = v[blk + j], b = v[blk + j + half];
+        v[blk + j] = P::add(a, b);
+        v[blk + j + half] = tw32<P>(j * (16 / half), P::sub(a, b));
+      }
+    }
+  }
+}
+
+// ----------------------------------------------------------------------------
+// The pass of efft_pass_fx for R = 1024 = 32 * 32 rows and C = 2^LC columns
+// (complex64): with n = t + 32 j (t, j < 32) and output k = q + 32 k2,
+//   stage 0 (thread t of its column):  Y_t[q] = sum_j x[t + 32 j] W32^(j q),
+//                                      times W1024^(t q), to shared memory;
+//   stage 1 (thread q of its column):  X[q + 32 k2] = sum_t Y_t[q] W32^(t k2).
+// One shared-memory exchange per pass (the radix-16 form 16 * 16 * 4 needs
+// two, and a third to reorder the last pass's output): the L1 data pipe,
+// not the FP32 pipe, bounds the complex64 passes.
+//  - strided passes (FIRST, MID): C adjacent columns in adjacent threads
+//    (row-major shared memory, raw = p*C + c, eight pad slots per 256 raw:
+//    stage-0 writes and stage-1 reads both conflict-free for C = 8 and 16);
+//    the first pass of a large array takes C = 16 (128 bytes per row
+//    segment, 512 threads, one CTA per SM);
+//  - last pass: a warp holds one column, lanes walk t (loads of 256
+//    contiguous bytes), raw = c*R + p with one pad slot per 32, and the
+//    stage-1 outputs k = q + 32 k2 of the 32 lanes are contiguous, so the
+//    result goes straight to global memory.  Stage-0 twiddles then come from
+//    a shared copy of the 1024-th roots (root k at k + k/8).
+// The pass twiddle exp(-2*pi*i*m*k/L) = W(m q) * W(m 32 k2): the first per
+// thread, the second per column in shared memory, as in efft_pass_fx.
+// ----------------------------------------------------------------------------
+template <int KIND, int LC, int MINB = 2>
+__global__ void __launch_bounds__(32 << LC, MINB) efft_pass_fx32(void* __restrict__ data, const PassArgs a) {
+  typedef PolicyF32 P;
+  typedef float2 V;
+  if (a.ptrs) data = a.ptrs[blockIdx.y];
+  constexpr int R = 1024, C = 1 << LC, NT = 32 * C;
+  constexpr bool STRIDED = (KIND == FIRST || KIND == MID);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  V* sm = reinterpret_cast<V*>(smem_raw);
+  __shared__ float4 vtw[STRIDED ? 32 * C : 1];
+  __shared__ float4 wroot[STRIDED ? 1 : R + R / 8];
+  auto slot = [](int p, int col) {
+    const int raw = STRIDED ? (p << LC) + col : (col << 10) + p;
+    return STRIDED ? raw + ((raw >> 8) << 3) : raw + (raw >> 5);
+  };
+
+  const int tid = threadIdx.x;
+  const int c = STRIDED ? (tid & (C - 1)) : (tid >> 5);
+  const int t = STRIDED ? (tid >> LC) : (tid & 31);
+  const uint64_t jcol = (uint64_t)blockIdx.x * C + c;
+  uint64_t m = 0, colbase, step;
+  if (KIND == FIRST) {
+    step = (uint64_t)a.s_odd << a.log2s;
+    m = jcol;
+    colbase = jcol;
+  } else if (STRIDED) {
+    step = 1ull << a.log2s;
+    m = jcol & (step - 1);
+    colbase = ((jcol >> a.log2s) << a.log2L) + m;
+  } else {
+    step = 1;
+    colbase = jcol << 10;
+  }
+  const int Dout = a.out_shift;
+
+  // pass twiddle factors: V_c[k2] = W(m_c 32 k2) ([k2][c]), W_t = W(m t)
+  float4 wt = make_float4(1.f, 0.f, 0.f, 0.f);
+  if (STRIDED) {
+    const int sh = (KIND == FIRST) ? 0 : a.log2N - a.log2L;
+    {
+      const int cc = tid & (C - 1), k2 = tid >> LC;  // NT = 32 C entries, one per thread
+      const uint64_t mc = ((uint64_t)blockIdx.x * C + cc) & (KIND == FIRST ? ~0ull : step - 1);
+      vtw[k2 * C + cc] = twiddle_N(a, (mc * (uint64_t)(32 * k2)) << sh);
+    }
+    wt = twiddle_N(a, (m * (uint64_t)t) << sh);
+  } else {
+    for (int k = tid; k < R; k += NT) wroot[k + (k >> 3)] = __ldg(a.w2048 + 2 * k);
+  }
+
+  V v[32];
+  // ---- stage 0: rows t + 32 j straight from global memory ----
+  {
+    const uint64_t b0 = colbase + (uint64_t)t * step, sj = 32ull * step;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) v[j] = Mem<P, KIND>::load(data, b0 + (uint64_t)j * sj, 0, a.conj_in);
+  }
+  if (!STRIDED) __syncthreads();  // wroot
+  dif32_regs<P>(v);
+  // W1024^(t q), q = bitrev5(u), to position p = 32 q + t
+#pragma unroll
+  for (int u = 1; u < 32; ++u) {
+    const int q = bitrev_c(u, 5);
+    const int e = t * q;
+    v[u] = P::mul_tw(v[u], STRIDED ? __ldg(a.w2048 + 2 * e) : wroot[e + (e >> 3)]);
+  }
+#pragma unroll
+  for (int u = 0; u < 32; ++u) sm[slot(32 * bitrev_c(u, 5) + t, c)] = v[u];
+  __syncthreads();
+
+  // ---- stage 1: thread q = t reads positions 32 q + j, j < 32 ----
+#pragma unroll
+  for (int j = 0; j < 32; ++j) v[j] = sm[slot(32 * t + j, c)];
+  dif32_regs<P>(v);
+
+  // ---- epilogue: register u holds X[q + 32 k2], k2 = bitrev5(u) ----
+  if (STRIDED) {
+    const P::TW w = wt;
+#pragma unroll
+    for (int u = 0; u < 32; ++u) {
+      const int k2 = bitrev_c(u, 5);
+      const int k = t + 32 * k2;
+      v[u] = P::pass_tw(v[u], w, vtw[k2 * C + c]);
+      const uint64_t off = (KIND == FIRST) ? ((uint64_t)(k * a.s_odd) << a.log2s) : ((uint64_t)k << a.log2s);
+      Mem<P, KIND>::store(data, colbase + off, v[u], Dout, a.conj_out, false);
+    }
+  } else {
+#pragma unroll
+    for (int u = 0; u < 32; ++u) {
+      const int k = t + 32 * bitrev_c(u, 5);
+      Mem<P, KIND>::store(data, colbase + (uint64_t)k, v[u], Dout, a.conj_out, false);
+    }
+  }
+}
+
+// Dynamic shared memory of efft_pass_fx32 with 2^LC columns: 1024 * 2^LC
+// values plus one pad slot per 32.
+constexpr int fx32_smem_bytes(int LC) { return ((1024 << LC) + (1024 << LC) / 32) * 8; }
+
+}  // namespace efft

@@ -3,6 +3,7 @@
 // in parallel.
 #include <cuda_runtime.h>
 
+#include "efft_fx32.cuh"
 #include "efft_kernels.cuh"
 
 namespace efft {
@@ -20,10 +21,18 @@ void attrs(cudaError_t& err) {
       cudaFuncSetAttribute(efft_pass_fx<PolicyF32, KIND, 11, kLog2Cta - 11>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)};
   for (cudaError_t x : e)
     if (x != cudaSuccess && err == cudaSuccess) err = x;
+  const cudaError_t f = cudaFuncSetAttribute(efft_pass_fx32<KIND, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             fx32_smem_bytes(3));
+  if (f != cudaSuccess && err == cudaSuccess) err = f;
 }
 
 template <int KIND>
 bool launch(int log2R, dim3 grid, dim3 block, size_t smem, cudaStream_t st, void* data, const PassArgs& a) {
+  if (log2R == 10 && a.log2C == 3) {
+    // 2^10 = 32 * 32: the radix-32 kernel, 256 threads on the same 8192-element tile
+    efft_pass_fx32<KIND, 3><<<grid, 256, fx32_smem_bytes(3), st>>>(data, a);
+    return true;
+  }
   switch (log2R) {
     case 8: efft_pass_fx<PolicyF32, KIND, 8, kLog2Cta - 8><<<grid, block, smem, st>>>(data, a); return true;
     case 9: efft_pass_fx<PolicyF32, KIND, 9, kLog2Cta - 9><<<grid, block, smem, st>>>(data, a); return true;
@@ -40,7 +49,18 @@ cudaError_t fx_set_attrs_f32() {
   attrs<FIRST>(err);
   attrs<MID>(err);
   attrs<LAST>(err);
+  const cudaError_t w = cudaFuncSetAttribute(efft_pass_fx32<FIRST, kLog2CtaWideC64 - 10, 1>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             fx32_smem_bytes(kLog2CtaWideC64 - 10));
+  if (w != cudaSuccess && err == cudaSuccess) err = w;
   return err;
+}
+
+bool fx_launch_f32_wide(int log2R, dim3 grid, cudaStream_t st, void* data, const PassArgs& a) {
+  constexpr int LC = kLog2CtaWideC64 - 10;
+  if (log2R != 10 || a.log2C != LC) return false;
+  efft_pass_fx32<FIRST, LC, 1><<<grid, 32 << LC, fx32_smem_bytes(LC), st>>>(data, a);
+  return true;
 }
 
 bool fx_launch_f32(int kind, int log2R, dim3 grid, dim3 block, size_t smem, cudaStream_t st, void* data,

@@ -150,6 +150,33 @@ def test_config_m1_3x2p28_complex128(orc):
     _free()
 
 
+def test_mixed_3x2p28_complex64_sampled(orc):
+    """N = 3 * 2^28 complex64 (6 GiB): the wide radix-32 first pass at the odd
+    stride 3 * 2^18, the mixed-radix middle pass; sampled bins against the
+    FP64 oracle on the FP64 input (its FP32 rounding is far below the
+    tolerance) and the unnormalised round trip divided by N."""
+    import paper_1409_5757_gb300 as efft
+    from paper_1409_5757_gb300 import inputs
+    N, seed, e = 3 << 28, 9, 30
+    x = torch.empty(N, dtype=torch.complex64, device="cuda")
+    inputs.fill_uniform(x, seed)
+    keep = x.clone()
+    sumsq = inputs.diff_norms(x)[0]
+    efft.fft_(x, -1)
+    torch.cuda.synchronize()
+    ks = np.concatenate([_ks(N, 10, 17), [N // 3, 2 * N // 3 + 5]]).astype(np.int64)
+    got = x[torch.from_numpy(ks).cuda()].cpu().numpy().astype(np.complex128)
+    ref = orc.dft_bins_uniform(seed, N, ks, -1)
+    err = math.sqrt(np.mean(np.abs(got - ref) ** 2)) / math.sqrt(sumsq)
+    assert err <= 2e-6 * e, err
+    efft.fft_(x, +1)
+    x.div_(N)
+    num, den = inputs.diff_norms(x, keep)
+    assert math.sqrt(num / den) <= 4e-6 * e
+    del x, keep
+    _free()
+
+
 def test_config_c4_2p31_complex64_gaussian(orc):
     """N = 2^31 complex64, Gaussian input; error vs the FP64 oracle on the
     FP32-rounded input promoted to FP64."""

@@ -176,16 +176,19 @@ def test_parity_large_full_oracle(orc, name, e):
     check(got, orc.fft_radix2(x, -1), name, N)
 
 
+@pytest.mark.parametrize("name", ["c128", "c64"])
 @pytest.mark.parametrize("sign", [-1, 1])
-def test_parity_2p28_wide_first_pass(orc, sign):
-    """complex128 2^28 = 2^10 * 2^8 * 2^10: the first pass runs on
-    8192-element tiles (from 2^28 on); against the full oracle."""
+def test_parity_2p28_wide_first_pass(orc, name, sign):
+    """2^28 = 2^10 * 2^8 * 2^10: from 2^28 on the first pass runs on wide
+    tiles (complex128: 8192 elements; complex64: the radix-32 kernel on
+    16384 elements, 16 columns); against the full oracle."""
     import paper_1409_5757_gb300 as efft
     N = 1 << 28
-    assert efft.Plan(N, efft.EFFT_C128, sign).radices() == [10, 8, 10]
-    x = host_input(orc, "c128", N, seed=2828)
-    got = gpu_fft(x, "c128", sign)
-    check(got, orc.fft_radix2(x, sign), "c128", N)
+    code = efft.EFFT_C128 if name == "c128" else efft.EFFT_C64
+    assert efft.Plan(N, code, sign).radices() == [10, 8, 10]
+    x = host_input(orc, name, N, seed=2828)
+    got = gpu_fft(x, name, sign)
+    check(got, orc.fft_radix2(x, sign), name, N)
 
 
 def test_execute_host_entry_point(orc):
