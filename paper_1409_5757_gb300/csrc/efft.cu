@@ -259,9 +259,11 @@ void apply_schedule(efft_plan_s* p, const int* r, int np) {
     else ps.kind = MID;
     // the first pass of a large complex128 array reads rows 2^(e-R) elements
     // apart, each in its own page; wider tiles move twice the bytes per row
-    // (complex64: 16384-element tiles of the radix-32 kernel, R = 2^10 only)
-    ps.wide = ps.kind == FIRST && e >= kWideMinLog2N &&
-              (p->dtype == EFFT_C128 ? (r[j] == 10 || r[j] == 11) : r[j] == 10);
+    // (complex64: 16384-element tiles, the first pass of 2^10 rows on the
+    // radix-32 kernel and the middle pass of 2^11 rows)
+    ps.wide = e >= kWideMinLog2N && (p->dtype == EFFT_C128
+                                         ? ps.kind == FIRST && (r[j] == 10 || r[j] == 11)
+                                         : (ps.kind == FIRST && r[j] == 10) || (ps.kind == MID && r[j] == 11));
     int log2C = (ps.wide ? (p->dtype == EFFT_C128 ? kLog2CtaWide : kLog2CtaWideC64) : log2cta) - r[j];
     if (log2C > e - r[j]) log2C = e - r[j];
     ps.log2C = log2C;
@@ -393,7 +395,7 @@ cudaError_t launch_pass(const efft_plan_s* p, const Pass& ps, void* data, const 
   constexpr int LOG2CTA = (P::kElemBytes == 16) ? kLog2CtaC128 : kLog2CtaC64;
   if (ps.wide) {
     const bool ok = (P::kElemBytes == 16) ? fx_launch_df2_wide(ps.log2R, grid, block, ps.smem, st, data, a)
-                                          : fx_launch_f32_wide(ps.log2R, grid, st, data, a);
+                                          : fx_launch_f32_wide(ps.kind, ps.log2R, grid, st, data, a);
     return ok ? cudaGetLastError() : cudaErrorInvalidConfiguration;
   }
   if (ps.kind != SINGLE && ps.log2R >= 8 && ps.log2R <= 11 && ps.log2R + ps.log2C == LOG2CTA) {

@@ -53,14 +53,26 @@ cudaError_t fx_set_attrs_f32() {
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              fx32_smem_bytes(kLog2CtaWideC64 - 10));
   if (w != cudaSuccess && err == cudaSuccess) err = w;
+  constexpr int elems = 1 << kLog2CtaWideC64;
+  const cudaError_t m = cudaFuncSetAttribute(efft_pass_fx<PolicyF32, MID, 11, kLog2CtaWideC64 - 11, 1>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (elems + elems / 16 + 1) * 8);
+  if (m != cudaSuccess && err == cudaSuccess) err = m;
   return err;
 }
 
-bool fx_launch_f32_wide(int log2R, dim3 grid, cudaStream_t st, void* data, const PassArgs& a) {
-  constexpr int LC = kLog2CtaWideC64 - 10;
-  if (log2R != 10 || a.log2C != LC) return false;
-  efft_pass_fx32<FIRST, LC, 1><<<grid, 32 << LC, fx32_smem_bytes(LC), st>>>(data, a);
-  return true;
+bool fx_launch_f32_wide(int kind, int log2R, dim3 grid, cudaStream_t st, void* data, const PassArgs& a) {
+  if (kind == FIRST && log2R == 10 && a.log2C == kLog2CtaWideC64 - 10) {
+    constexpr int LC = kLog2CtaWideC64 - 10;
+    efft_pass_fx32<FIRST, LC, 1><<<grid, 32 << LC, fx32_smem_bytes(LC), st>>>(data, a);
+    return true;
+  }
+  if (kind == MID && log2R == 11 && a.log2C == kLog2CtaWideC64 - 11) {
+    constexpr int LC = kLog2CtaWideC64 - 11;
+    constexpr int elems = 1 << kLog2CtaWideC64;
+    efft_pass_fx<PolicyF32, MID, 11, LC, 1><<<grid, elems / 16, (elems + elems / 16 + 1) * 8, st>>>(data, a);
+    return true;
+  }
+  return false;
 }
 
 bool fx_launch_f32(int kind, int log2R, dim3 grid, dim3 block, size_t smem, cudaStream_t st, void* data,

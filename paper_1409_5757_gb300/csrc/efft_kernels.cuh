@@ -647,9 +647,10 @@ bool fx_launch_df2_wide(int log2R, dim3 grid, dim3 block, size_t smem, cudaStrea
 cudaError_t fx_set_attrs_f32();
 bool fx_launch_f32(int kind, int log2R, dim3 grid, dim3 block, size_t smem, cudaStream_t st, void* data,
                    const PassArgs& a);
-// complex64 first pass of R = 2^10 rows on 16384-element tiles (16 columns,
-// 128 bytes per row segment), one CTA of 512 threads per SM.
+// complex64 passes on 16384-element tiles, one CTA per SM: the first pass of
+// R = 2^10 rows (radix-32 kernel, 16 columns, 128 bytes per row segment) and
+// the middle pass of R = 2^11 rows (8 columns, 64 bytes per row segment).
 constexpr int kLog2CtaWideC64 = 14;
-bool fx_launch_f32_wide(int log2R, dim3 grid, cudaStream_t st, void* data, const PassArgs& a);
+bool fx_launch_f32_wide(int kind, int log2R, dim3 grid, cudaStream_t st, void* data, const PassArgs& a);
 
 }  // namespace efft
