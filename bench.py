@@ -94,13 +94,20 @@ def job_rate(world: int, transforms_per_step: int, n: int, ms_per_step: float, r
     return world * transforms_per_step * f / (ms_per_step * 1e-3) / 1e9
 
 
-def kernel_fingerprint(mixed: bool = False) -> str:
-    """sha1 (16 hex digits) of the sources of the power-of-two pass kernels,
-    or with mixed=True of the mixed-radix middle-pass kernel."""
+KERNEL_SOURCES = {
+    "c128": ("efft_kernels.cuh", "efft_arith.cuh", "efft_fx_df2.cu"),
+    "c64": ("efft_kernels.cuh", "efft_arith.cuh", "efft_fx_f32.cu", "efft_fx32.cuh"),
+    "mixed": ("efft_kernels.cuh", "efft_arith.cuh", "efft_mix.cuh", "efft_mix.cu"),
+}
+
+
+def kernel_fingerprint(family: str) -> str:
+    """sha1 (16 hex digits) of the sources of one kernel family: the
+    complex128 or complex64 power-of-two pass kernels, or the mixed-radix
+    middle-pass kernel."""
     import hashlib
     h = hashlib.sha1()
-    files = ("efft_kernels.cuh", "efft_arith.cuh") + (
-        ("efft_mix.cuh", "efft_mix.cu") if mixed else ("efft_fx_df2.cu", "efft_fx_f32.cu", "efft_fx32.cuh"))
+    files = KERNEL_SOURCES[family]
     for f in files:
         with open(os.path.join(ROOT, "paper_1409_5757_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
@@ -112,7 +119,9 @@ def measured_traffic(workload: str, log2n: int, kernel: str):
     or None when there is none for this kernel or the kernel changed since."""
     path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
     try:
-        fp = kernel_fingerprint(mixed=(workload == "m1" and kernel == "pass1"))
+        family = ("mixed" if workload == "m1" and kernel == "pass1"
+                  else WORKLOADS[workload]["dtype"] if workload in WORKLOADS else "c128")
+        fp = kernel_fingerprint(family)
         with open(path) as f:
             for line in f:
                 if not line.strip() or line.startswith("#"):
