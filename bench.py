@@ -71,6 +71,36 @@ def flops(n: int) -> float:
     return 5.0 * n * math.log2(n)
 
 
+# Double-float (complex128) pass kernels: FP32 operations per element of one
+# pass, from the fixed operation counts of the double-float method (FMA
+# counted once; packed FP32x2 instructions count their two lanes):
+#   complex add/sub (TwoSum on both parts, low parts added)     16
+#   complex multiply (TwoProd by FMA, TwoSum, 4 cross terms)    32
+#   multiply by exp(-2*pi*i/8) (add, then a real product)     24
+#   renormalisation before an intermediate store               6
+# A radix-2^LR pass (radix-16 stages, then one of radix 2^(LR mod 4)) does
+# LR complex adds per element, the radix-16 constant multiplies (4 general
+# and 6 by exp(-2*pi*i/8) per 16 elements per radix-16 stage; 2 by
+# exp(-2*pi*i/8) per 8 in a radix-8 stage), 15/16 of a complex multiply per
+# internal twiddle stage, and in strided passes the pass twiddle as two
+# complex multiplies.
+DF_OPS = {"add": 16, "mul": 32, "w8": 24, "norm": 6}
+FP32_PEAK_OPS = 152 * 128 * 2.07e9  # SMs x FP32 lanes x maximum SM clock
+
+
+def df_ops_per_element(log2r: int, kind: str) -> float:
+    nfull, rem = divmod(log2r, 4)
+    nst = nfull + (1 if rem else 0)
+    ops = log2r * DF_OPS["add"]
+    ops += nfull * (4 * DF_OPS["mul"] + 6 * DF_OPS["w8"]) / 16.0
+    if rem == 3:
+        ops += 2 * DF_OPS["w8"] / 8.0
+    ops += (nst - 1) * 15.0 / 16.0 * DF_OPS["mul"]
+    if kind in ("FIRST", "MID"):
+        ops += 2 * DF_OPS["mul"] + DF_OPS["norm"]
+    return ops
+
+
 def flops_real(n: int) -> float:
     """The paper's count for n real points (Eq. 7)."""
     return 2.5 * n * math.log2(n)
@@ -512,6 +542,18 @@ def run_ours(args, wl):
                     "peak_kind": f"{peak_kind} STREAM-style copy (MEASURED_PEAKS.json hbm_gbs)",
                     "per_launch_ms": tot_ms / nl, "algorithmic_bytes_per_launch": alg_bytes,
                     "kernels_ms_per_step": {k: v[0] / K for k, v in prof.items()}}
+        # the second roofline of a double-float power-of-two pass: FP32 arithmetic
+        rad = fwd.radices() if hasattr(fwd, "radices") else []
+        if c128 and name.startswith("pass") and rad and N & (N - 1) == 0 and not real:
+            j = int(name[4:])
+            kind = "SINGLE" if len(rad) == 1 else ("FIRST" if j == 0 else "LAST" if j == len(rad) - 1 else "MID")
+            ope = df_ops_per_element(rad[j], kind)
+            ach = ope * N / per_launch_s
+            roofline["alu_view"] = {
+                "bound": "alu", "achieved": ach / 1e12, "peak": FP32_PEAK_OPS / 1e12,
+                "unit": "T FP32 operations/s (FMA counted once)", "frac": ach / FP32_PEAK_OPS,
+                "ops_per_element": ope, "pass": f"2^{rad[j]} {kind}",
+                "peak_kind": "152 SMs x 128 FP32 lanes x 2070 MHz (maximum SM clock)"}
     launches = sum(v[1] for v in prof.values())
     floor_gbs = world * tps * 2 * N * S / (ms_per_step * 1e-3) / 1e9
 
