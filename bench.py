@@ -8,7 +8,7 @@ Default workload (the headline configuration): one step = a forward DFT
 (sign -1, Eq. 1) followed by the normalised inverse (sign +1, times 1/N) of
 N = 2^30 complex128 points in place (16 GiB), input uniform[-1,1) re/im plus
 64 seeded tones.  value = 5*N*log2(N) flop per transform x transforms / time
-(GFLOP/s, BASELINE metric), whole job.  The input (16 GiB) is larger than the
+(GFLOP/s), whole job.  The input (16 GiB) is larger than the
 129 MB L2, so no flush is needed between timed iterations.
 
 Workload c5 (batched, mixed sizes): 256 complex64 transforms of 2^12..2^24
@@ -18,7 +18,7 @@ launch); a step = forward + normalised conjugate-sign transform of all 256.
 --impl reference times the CPU oracle (the FP64 radix-2 FFT, as it stands)
 on the host cores on a bounded sample of the same workload.
 
-Multi-GPU: the transform does not shard across GPUs in this build (one FFT
+Multi-GPU: the transform does not shard across GPUs (one FFT
 per GPU); under torchrun every rank runs an independent replica ("replicas
 only") and value is the sum over ranks divided by the max time over ranks.
 """

@@ -57,7 +57,7 @@ enum efft_status {
   EFFT_ERR_ALLOC = 6,          /* device or host allocation failed              */
   EFFT_ERR_LAUNCH = 7,         /* a kernel launch or async copy was rejected    */
   EFFT_ERR_TIMEOUT = 8,        /* reserved: a bounded device wait expired       */
-  EFFT_ERR_UNSUPPORTED = 9,    /* valid request this build does not implement   */
+  EFFT_ERR_UNSUPPORTED = 9,    /* valid request the library does not implement  */
   EFFT_ERR_INVALID_PLAN = 10,  /* NULL, destroyed or foreign plan handle        */
   EFFT_ERR_CUDA = 11,          /* CUDA runtime error (no device, bad context)   */
   EFFT_ERR_INVALID_FLAGS = 12  /* unknown bits in flags                         */
