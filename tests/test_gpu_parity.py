@@ -191,6 +191,23 @@ def test_parity_2p28_wide_first_pass(orc, name, sign):
     check(got, orc.fft_radix2(x, sign), name, N)
 
 
+def test_parity_c64_2p29_middle_pass_2p11(orc):
+    """complex64 2^29 with the schedule 2^9 * 2^11 * 2^9: from 2^28 on the
+    2^11-row middle pass runs on 8-column tiles (16384 elements, one
+    1024-thread CTA per SM); against the full oracle."""
+    import paper_1409_5757_gb300 as efft
+    N = 1 << 29
+    x = host_input(orc, "c64", N, seed=2929)
+    t = torch.from_numpy(x.astype(np.complex64)).cuda()
+    p = efft.Plan(N, efft.EFFT_C64, -1, radices=[9, 11, 9])
+    assert p.radices() == [9, 11, 9]
+    p.execute(t.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    got = t.cpu().numpy().astype(np.complex128)
+    del t
+    check(got, orc.fft_radix2(x, -1), "c64", N)
+
+
 def test_execute_host_entry_point(orc):
     import paper_1409_5757_gb300 as efft
     N = 1 << 18
