@@ -334,6 +334,22 @@ int efft_execute_noalloc(void* data, uint64_t n, int dtype, int sign, uint32_t f
  *   the device pointer array and state); at most EFFT_BATCH_INFLIGHT of them
  *   are outstanding: the next one first waits on the host for the oldest.
  *   Errors: INVALID_PLAN (not a live batch), INVALID_PTR, MISALIGNED, LAUNCH.
+ * efft_batch_execute_host_stream: host data through a chain of nbatches
+ *   batches of the same sizes (in the same order, one device), applied in
+ *   chain order (e.g. a forward batch, then an inverse one): transform i is
+ *   copied from host_in[i] to the device buffer dev[i] (the rules of
+ *   efft_execute; no two overlapping), transformed by every batch of the
+ *   chain, and copied to host_out[i] (host_out[i] may equal host_in[i]).
+ *   The transforms go group by group (largest size first) in chunks of
+ *   about 256 MiB; the copies in, the launches and the copies out run on
+ *   three streams ordered by events (the launches on `stream`), so the
+ *   copies of one chunk overlap the transforms of the previous ones.  The
+ *   host arrays should be pinned (cudaHostAlloc) for the copies to overlap.
+ *   Synchronous: returns when every result is in host memory.  The graph
+ *   is not used (the launches of each chunk are enqueued directly).
+ *   Errors: INVALID_PLAN (a batch not live), INVALID_SIZE (nbatches < 1 or
+ *   batches of different sizes, dtype or device), INVALID_PTR / MISALIGNED
+ *   (host or device pointers), LAUNCH, CUDA.
  * efft_batch_info: *ngroups = number of distinct sizes; *kernels = kernel
  *   nodes in the graph (kernel launches per execute).  Either may be NULL.
  * efft_batch_destroy: waits for the batch's outstanding executes, then
@@ -344,6 +360,8 @@ typedef struct efft_batch_s* efft_batch_t;
 int efft_batch_create(efft_batch_t* out, const uint64_t* sizes, int count, int dtype, int sign,
                       uint32_t flags);
 int efft_batch_execute(efft_batch_t batch, void* const* data, void* stream);
+int efft_batch_execute_host_stream(const efft_batch_t* batches, int nbatches, void* const* host_in,
+                                   void* const* host_out, void* const* dev, void* stream);
 int efft_batch_info(efft_batch_t batch, int* ngroups, int* kernels);
 int efft_batch_destroy(efft_batch_t batch);
 

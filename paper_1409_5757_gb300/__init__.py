@@ -65,6 +65,8 @@ _SIGNATURES = {
     "efft_batch_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.POINTER(ctypes.c_uint64), ctypes.c_int,
                                          ctypes.c_int, ctypes.c_int, ctypes.c_uint32]),
     "efft_batch_execute": (ctypes.c_int, [_vp, ctypes.POINTER(_vp), _vp]),
+    "efft_batch_execute_host_stream": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, ctypes.POINTER(_vp),
+                                                      ctypes.POINTER(_vp), ctypes.POINTER(_vp), _vp]),
     "efft_batch_info": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     "efft_batch_destroy": (ctypes.c_int, [_vp]),
     "efft_plan_create_real": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_uint64, ctypes.c_int, ctypes.c_int,
@@ -236,6 +238,23 @@ class Batch:
             pass
 
 
+def batch_execute_host_stream(batches, host_in, host_out, dev_ptrs, stream: int = 0) -> None:
+    """efft_batch_execute_host_stream: transform i copied from host_in[i] to
+    dev_ptrs[i], transformed by every batch in order, copied to host_out[i];
+    copies overlapped with the transforms chunk by chunk; synchronous."""
+    n = len(batches[0].sizes) if batches else 0
+    if not batches or any(len(b.sizes) != n for b in batches):
+        raise ValueError("efft: batches of one size list expected")
+    if len(host_in) != n or len(host_out) != n or len(dev_ptrs) != n:
+        raise ValueError(f"efft: {n} transforms need {n} host inputs, outputs and device buffers")
+    B = (_vp * len(batches))(*[b._h for b in batches])
+    HI = (_vp * n)(*[_vp(int(x)) for x in host_in])
+    HO = (_vp * n)(*[_vp(int(x)) for x in host_out])
+    DP = (_vp * n)(*[_vp(int(x)) for x in dev_ptrs])
+    _check(_lib().efft_batch_execute_host_stream(B, len(batches), HI, HO, DP, _vp(stream)),
+           "efft_batch_execute_host_stream")
+
+
 def execute_host_stream(plans, host_in, host_out, dev_bufs, stream: int = 0) -> None:
     """efft_execute_host_stream: host arrays (data pointers) through the plans
     in order, copies overlapped with the transforms; synchronous."""
@@ -394,5 +413,5 @@ def version() -> int:
 
 __all__ = ["Plan", "Batch", "EfftError", "fft_", "fft", "fft_batch_", "rfft_", "irfft_", "get_plan", "get_batch",
            "clear_plans", "version", "EFFT_REAL_FORWARD", "EFFT_REAL_INVERSE",
-           "lib_path", "execute_host_stream", "EFFT_C64", "EFFT_C128", "EFFT_FLAG_DIGIT_REVERSED_OUT",
+           "lib_path", "execute_host_stream", "batch_execute_host_stream", "EFFT_C64", "EFFT_C128", "EFFT_FLAG_DIGIT_REVERSED_OUT",
            "EFFT_FLAG_NORMALIZE", "EFFT_FLAG_AUTOTUNE"]

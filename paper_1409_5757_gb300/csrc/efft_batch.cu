@@ -228,6 +228,130 @@ int efft_batch_execute(efft_batch_t b, void* const* data, void* stream) {
   return EFFT_OK;
 }
 
+// Host data through a chain of batches of the same sizes: the transforms are
+// taken group by group (largest size first) in chunks of about
+// kHostChunkBytes; a chunk's copies in, its launches for every batch of the
+// chain and its copies out run on three streams ordered by events, so the
+// copies of one chunk overlap the transforms of the previous ones.
+int efft_batch_execute_host_stream(const efft_batch_t* batches, int nbatches, void* const* host_in,
+                                   void* const* host_out, void* const* dev, void* stream) {
+  constexpr size_t kHostChunkBytes = 256ull << 20;
+  if (!batches || nbatches < 1) return EFFT_ERR_INVALID_SIZE;
+  for (int j = 0; j < nbatches; ++j)
+    if (!batch_is_live(batches[j])) return EFFT_ERR_INVALID_PLAN;
+  efft_batch_s* b0 = batches[0];
+  // every batch of the chain: same device, dtype, sizes and slot layout
+  for (int j = 1; j < nbatches; ++j) {
+    const efft_batch_s* b = batches[j];
+    if (b->device != b0->device || b->count != b0->count || b->gstart != b0->gstart || b->slot != b0->slot ||
+        b->plans.size() != b0->plans.size())
+      return EFFT_ERR_INVALID_SIZE;
+    for (size_t g = 0; g < b->plans.size(); ++g)
+      if (b->plans[g]->n != b0->plans[g]->n || b->plans[g]->dtype != b0->plans[g]->dtype)
+        return EFFT_ERR_INVALID_SIZE;
+  }
+  if (!host_in || !host_out || !dev) return EFFT_ERR_INVALID_PTR;
+  const int count = b0->count;
+  DeviceGuard dg(b0->device);
+  if (!dg.ok) return EFFT_ERR_CUDA;
+  std::vector<std::pair<uintptr_t, uintptr_t>> spans(count);
+  std::vector<int> by_slot(count);
+  for (int i = 0; i < count; ++i) {
+    if (!host_in[i] || !host_out[i]) return EFFT_ERR_INVALID_PTR;
+    const efft_plan_s* p = b0->plans[b0->group[i]];
+    int rc = check_buffer(p, dev[i]);
+    if (rc != EFFT_OK) return rc;
+    const uintptr_t a = reinterpret_cast<uintptr_t>(dev[i]);
+    spans[i] = {a, a + plan_bytes(p)};
+    by_slot[b0->slot[i]] = i;
+  }
+  std::sort(spans.begin(), spans.end());
+  for (int i = 1; i < count; ++i)
+    if (spans[i].first < spans[i - 1].second) return EFFT_ERR_INVALID_PTR;
+  if (fault_injected("launch")) return EFFT_ERR_LAUNCH;
+
+  // chunks: runs of slots inside one group of about kHostChunkBytes
+  struct Chunk {
+    int g, s0, s1;
+  };
+  std::vector<Chunk> chunks;
+  for (size_t g = 0; g + 1 < b0->gstart.size(); ++g) {
+    const size_t bytes = plan_bytes(b0->plans[g]);
+    const int per = (int)std::max<size_t>(1, kHostChunkBytes / bytes);
+    for (int s = b0->gstart[g]; s < b0->gstart[g + 1]; s += per)
+      chunks.push_back({(int)g, s, std::min(s + per, b0->gstart[g + 1])});
+  }
+
+  cudaStream_t sc = reinterpret_cast<cudaStream_t>(stream);
+  cudaStream_t sin = nullptr, sout = nullptr;
+  std::vector<cudaEvent_t> ev_in(chunks.size(), nullptr), ev_comp(chunks.size(), nullptr);
+  int rc = EFFT_OK;
+  if (cudaStreamCreateWithFlags(&sin, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&sout, cudaStreamNonBlocking) != cudaSuccess)
+    rc = EFFT_ERR_CUDA;
+  for (size_t c = 0; rc == EFFT_OK && c < chunks.size(); ++c)
+    if (cudaEventCreateWithFlags(&ev_in[c], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ev_comp[c], cudaEventDisableTiming) != cudaSuccess)
+      rc = EFFT_ERR_CUDA;
+  // the pointer arrays of every batch (staging slots as in efft_batch_execute)
+  std::vector<int> ring(nbatches, 0);
+  for (int j = 0; rc == EFFT_OK && j < nbatches; ++j) {
+    efft_batch_s* b = batches[j];
+    const int k = b->next;
+    if (cudaEventSynchronize(b->done[k]) != cudaSuccess) {
+      rc = EFFT_ERR_CUDA;
+      break;
+    }
+    void** stage = b->stage + (size_t)k * count;
+    for (int i = 0; i < count; ++i) stage[b->slot[i]] = dev[i];
+    if (cudaMemcpyAsync(b->dptrs, stage, sizeof(void*) * count, cudaMemcpyHostToDevice, sc) != cudaSuccess)
+      rc = EFFT_ERR_CUDA;
+    ring[j] = k;
+    b->next = (k + 1) % EFFT_BATCH_INFLIGHT;
+  }
+  for (size_t c = 0; rc == EFFT_OK && c < chunks.size(); ++c) {
+    const Chunk& ch = chunks[c];
+    const size_t bytes = plan_bytes(b0->plans[ch.g]);
+    for (int s = ch.s0; rc == EFFT_OK && s < ch.s1; ++s) {
+      const int i = by_slot[s];
+      if (cudaMemcpyAsync(dev[i], host_in[i], bytes, cudaMemcpyHostToDevice, sin) != cudaSuccess) rc = EFFT_ERR_CUDA;
+    }
+    if (rc != EFFT_OK || cudaEventRecord(ev_in[c], sin) != cudaSuccess ||
+        cudaStreamWaitEvent(sc, ev_in[c], 0) != cudaSuccess) {
+      rc = EFFT_ERR_CUDA;
+      break;
+    }
+    for (int j = 0; rc == EFFT_OK && j < nbatches; ++j) {
+      efft_batch_s* b = batches[j];
+      const Batch bt{reinterpret_cast<void* const*>(b->dptrs + ch.s0), (unsigned)(ch.s1 - ch.s0),
+                     b->state + 4 * (size_t)ch.s0};
+      rc = enqueue_batch(b->plans[ch.g], nullptr, bt, sc);
+    }
+    if (rc != EFFT_OK) break;
+    if (cudaEventRecord(ev_comp[c], sc) != cudaSuccess || cudaStreamWaitEvent(sout, ev_comp[c], 0) != cudaSuccess) {
+      rc = EFFT_ERR_CUDA;
+      break;
+    }
+    for (int s = ch.s0; rc == EFFT_OK && s < ch.s1; ++s) {
+      const int i = by_slot[s];
+      if (cudaMemcpyAsync(host_out[i], dev[i], bytes, cudaMemcpyDeviceToHost, sout) != cudaSuccess) rc = EFFT_ERR_CUDA;
+    }
+  }
+  for (int j = 0; j < nbatches; ++j) cudaEventRecord(batches[j]->done[ring[j]], sc);
+  // drain everything that was enqueued, even after an error
+  if (sin) cudaStreamSynchronize(sin);
+  cudaStreamSynchronize(sc);
+  if (sout && cudaStreamSynchronize(sout) != cudaSuccess && rc == EFFT_OK) rc = EFFT_ERR_CUDA;
+  for (size_t c = 0; c < chunks.size(); ++c) {
+    if (ev_in[c]) cudaEventDestroy(ev_in[c]);
+    if (ev_comp[c]) cudaEventDestroy(ev_comp[c]);
+  }
+  if (sin) cudaStreamDestroy(sin);
+  if (sout) cudaStreamDestroy(sout);
+  if (rc != EFFT_OK) cudaGetLastError();
+  return rc;
+}
+
 int efft_batch_info(efft_batch_t b, int* ngroups, int* kernels) {
   if (!batch_is_live(b)) return EFFT_ERR_INVALID_PLAN;
   if (ngroups) *ngroups = (int)b->plans.size();

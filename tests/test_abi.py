@@ -191,6 +191,10 @@ def test_batch_and_autotune_handle_checks(libs):
     assert L.efft_batch_execute(None, None, None) == 10
     assert L.efft_batch_execute(bp, None, None) == 10
     assert L.efft_batch_info(None, None, None) == 10
+    assert L.efft_batch_execute_host_stream(None, 1, None, None, None, None) == 1   # no batch list
+    arr = (ctypes.c_void_p * 1)(bp.value)
+    assert L.efft_batch_execute_host_stream(arr, 0, None, None, None, None) == 1    # nbatches < 1
+    assert L.efft_batch_execute_host_stream(arr, 1, None, None, None, None) == 10   # foreign handle
     assert L.efft_plan_autotune(None, None, None, None, None, 0, None) == 10
     assert L.efft_plan_autotune(bp, None, None, None, None, 0, None) == 10
 

@@ -191,6 +191,53 @@ def test_batch_fault_injection(monkeypatch, name):
     torch.cuda.synchronize()
 
 
+@pytest.mark.parametrize("name", ["c128", "c64"])
+def test_batch_host_stream_chain(orc, name):
+    """efft_batch_execute_host_stream: host arrays through a chain of batches,
+    chunk by chunk (ten 2^22 transforms make several chunks of one group).
+    A one-batch chain equals single plans bit for bit; forward then the
+    normalised inverse returns the input; mismatched batches are rejected."""
+    import paper_1409_5757_gb300 as efft
+    from paper_1409_5757_gb300 import inputs
+    es = [22] * 10 + [0, 3, 12, 16, 16, 20, 12]
+    sizes = [1 << e for e in es]
+    tdt = torch.complex128 if name == "c128" else torch.complex64
+    offs = np.concatenate([[0], np.cumsum(sizes)])
+    total = int(offs[-1])
+    hin = inputs.PinnedHost(total, tdt)
+    hout = inputs.PinnedHost(total, tdt)
+    for i, n in enumerate(sizes):
+        inputs_t = torch.empty(n, dtype=tdt, device="cuda")
+        inputs.fill_uniform(inputs_t, 7100 + i)
+        hin.tensor[offs[i]:offs[i + 1]].copy_(inputs_t.cpu())
+    esz = hin.tensor.element_size()
+    dev = torch.empty(total, dtype=tdt, device="cuda")
+    hp_in = [hin.ptr + int(o) * esz for o in offs[:-1]]
+    hp_out = [hout.ptr + int(o) * esz for o in offs[:-1]]
+    dp = [dev.data_ptr() + int(o) * esz for o in offs[:-1]]
+    fwd = efft.Batch(sizes, _code(name), -1)
+    inv = efft.Batch(sizes, _code(name), +1, efft.EFFT_FLAG_NORMALIZE)
+    s = torch.cuda.current_stream().cuda_stream
+    efft.batch_execute_host_stream([fwd], hp_in, hp_out, dp, s)
+    for i, n in enumerate(sizes):
+        ref = hin.tensor[offs[i]:offs[i + 1]].cuda()
+        efft.fft_(ref, -1)
+        assert torch.equal(hout.tensor[offs[i]:offs[i + 1]], ref.cpu()), f"N=2^{es[i]}"
+    efft.batch_execute_host_stream([fwd, inv], hp_in, hp_out, dp, s)
+    for i, n in enumerate(sizes):
+        got = hout.tensor[offs[i]:offs[i + 1]].numpy().astype(np.complex128)
+        x = hin.tensor[offs[i]:offs[i + 1]].numpy().astype(np.complex128)
+        assert oracle.rel_l2(got, x) <= 2 * TOL[name] * max(es[i], 1), f"round trip N=2^{es[i]}"
+    other = efft.Batch(sizes[:-1] + [1 << 13], _code(name), -1)
+    with pytest.raises(efft.EfftError) as ei:
+        efft.batch_execute_host_stream([fwd, other], hp_in, hp_out, dp, s)
+    assert ei.value.status == 1
+    for b in (fwd, inv, other):
+        b.destroy()
+    hin.free()
+    hout.free()
+
+
 def test_batch_of_256_uneven_c64(orc):
     """256 complex64 transforms, N = 2^e with e uniform in {12..24} (seed 5):
     bit-identical to single plans for all, the oracle for the smallest and
