@@ -310,13 +310,14 @@ int efft_plan_create_real(efft_plan_t* out, uint64_t n, int precision, int direc
 int efft_execute_noalloc(void* data, uint64_t n, int dtype, int sign, uint32_t flags, void* stream);
 
 /*
- * Batches: `count` independent in-place transforms of mixed power-of-two
- * sizes run by one CUDA graph launch.  The paper's many sub-FFTs of one
+ * Batches: `count` independent in-place transforms of mixed sizes run by
+ * one CUDA graph launch.  The paper's many sub-FFTs of one
  * split (Sec. 3.3), whose order is left to the Cilk scheduler, become one
  * user-level batch whose order is fixed once, at creation.
  *
- * efft_batch_create: transform i has sizes[i] points (a power of two,
- *   1 <= sizes[i] <= 2^EFFT_MAX_LOG2N); all share dtype, sign and flags
+ * efft_batch_create: transform i has sizes[i] points (a supported length
+ *   of efft_plan_create: M * 2^e, M odd <= EFFT_MAX_ODD, at most
+ *   2^EFFT_MAX_LOG2N); all share dtype, sign and flags
  *   (EFFT_FLAG_AUTOTUNE applies per distinct size).  Transforms of equal
  *   size share one plan and run in the same kernel launches (one grid row
  *   per transform); distinct sizes run as parallel branches of one CUDA

@@ -204,7 +204,7 @@ class Plan:
 
 class Batch:
     """Owning wrapper of an efft_batch_t: `len(sizes)` in-place transforms of
-    mixed power-of-two sizes, one CUDA graph launch per execute."""
+    mixed sizes (N = M * 2^e), one CUDA graph launch per execute."""
 
     def __init__(self, sizes, dtype: int = EFFT_C64, sign: int = -1, flags: int = 0):
         self.sizes = [int(v) for v in sizes]
@@ -339,7 +339,7 @@ def fft_(t, sign: int = -1, flags: int = 0, stream=None):
 
 def fft_batch_(tensors, sign: int = -1, flags: int = 0, stream=None):
     """In-place DFTs of a list of contiguous 1-D CUDA complex tensors of one
-    dtype and device (power-of-two lengths, not overlapping) by one batch
+    dtype and device (supported lengths, not overlapping) by one batch
     execute; returns the list."""
     import torch
     if not tensors:

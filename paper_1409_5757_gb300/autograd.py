@@ -58,7 +58,7 @@ def dft(x: torch.Tensor, sign: int = -1, normalize: bool = False) -> torch.Tenso
 
 def dft_batch(xs, sign: int = -1, normalize: bool = False) -> list:
     """Differentiable DFTs of a list of 1-D CUDA complex tensors (mixed
-    power-of-two lengths, one dtype) by one batch execute forward and one
+    supported lengths, one dtype) by one batch execute forward and one
     (opposite sign) backward."""
     return list(_BatchDFT.apply(sign, normalize, *xs))
 

@@ -1,5 +1,6 @@
 // efft_batch.cu -- batches of independent in-place transforms of mixed
-// power-of-two sizes behind one CUDA graph (efft_batch_* in include/efft.h).
+// sizes behind one CUDA graph (efft_batch_* in include/efft.h), and host data
+// through a chain of batches with the copies overlapped.
 // Transforms of one size share a plan and run in the same launches (grid.y
 // selects the transform); the sizes run as parallel branches of the graph.
 #include <cuda_runtime.h>
