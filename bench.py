@@ -158,8 +158,9 @@ def measured_traffic(workload: str, log2n: int, kernel: str):
                     continue
                 w, e, k, b, fma, issue, src_fp, *src = line.split()
                 if w == workload and int(e) == log2n and k == kernel and src_fp == fp:
-                    return {"bytes": float(b), "fma_pipe_pct": float(fma), "issue_pct": float(issue),
-                            "source": " ".join(src)}
+                    # '-': the capture took DRAM bytes only
+                    return {"bytes": float(b), "fma_pipe_pct": None if fma == "-" else float(fma),
+                            "issue_pct": None if issue == "-" else float(issue), "source": " ".join(src)}
     except (OSError, ValueError):
         pass
     return None
@@ -538,7 +539,7 @@ def run_ours(args, wl):
                                    "note": ("the double-float pass kernels are bound by the FP32 pipe, not HBM"
                                             if c128 else "the FP32 pass kernels are bound by the L1/LSU data "
                                             "pipe and load latency, not HBM")}
-                                  if tr else None),
+                                  if tr and tr["fma_pipe_pct"] is not None else None),
                     "peak_kind": f"{peak_kind} STREAM-style copy (MEASURED_PEAKS.json hbm_gbs)",
                     "per_launch_ms": tot_ms / nl, "algorithmic_bytes_per_launch": alg_bytes,
                     "kernels_ms_per_step": {k: v[0] / K for k, v in prof.items()}}
@@ -820,7 +821,8 @@ def main():
             # N = M * 2^e: keep M, scale 2^e (log2n is ceil(log2 N))
             e = (wl["n"] & -wl["n"]).bit_length() - 1
             odd, e_new = wl["n"] >> e, e + args.log2n - wl["log2n"]
-            wl["desc"] = wl["desc"].replace(f"{odd}*2^{e}", f"{odd}*2^{e_new}")
+            wl["desc"] = wl["desc"].replace(f"{odd}*2^{e}", f"{odd}*2^{e_new}").replace(
+                f"{(wl['n'] * 16) >> 30} GiB", f"{((odd << e_new) * 16) / 2**30:g} GiB")
             wl["n"] = odd << e_new
         wl["log2n"] = args.log2n
         wl["desc"] = wl["desc"].replace("2^30", f"2^{args.log2n}").replace("2^33", f"2^{args.log2n}")

@@ -121,14 +121,14 @@ def test_config_c3_2p33_complex128(orc):
 
 
 def test_config_m1_3x2p28_complex128(orc):
-    """N = 3 * 2^28 complex128 (12 GiB), schedule (2^10, 3 * 2^8, 2^10): the
-    first pass on 8192-element tiles at stride 3 * 2^18, the middle pass on the
+    """N = 3 * 2^28 complex128 (12 GiB), schedule (2^11, 3 * 2^6, 2^11): the
+    first pass on 8192-element tiles at stride 3 * 2^17, the middle pass on the
     mixed-radix kernel.  Sampled bins, Parseval, and the unnormalised inverse
     divided by N."""
     import paper_1409_5757_gb300 as efft
     from paper_1409_5757_gb300 import inputs
     N, seed, e = 3 << 28, 8, 30
-    assert efft.Plan(N, efft.EFFT_C128, -1).radices() == [10, 8, 10]
+    assert efft.Plan(N, efft.EFFT_C128, -1).radices() == [11, 6, 11]
     x = torch.empty(N, dtype=torch.complex128, device="cuda")
     inputs.fill_uniform(x, seed)
     keep = x.clone()
@@ -151,10 +151,10 @@ def test_config_m1_3x2p28_complex128(orc):
 
 
 def test_mixed_3x2p28_complex64_sampled(orc):
-    """N = 3 * 2^28 complex64 (6 GiB): the wide radix-32 first pass at the odd
-    stride 3 * 2^18, the mixed-radix middle pass; sampled bins against the
-    FP64 oracle on the FP64 input (its FP32 rounding is far below the
-    tolerance) and the unnormalised round trip divided by N."""
+    """N = 3 * 2^28 complex64 (6 GiB), schedule (2^11, 3 * 2^6, 2^11): the
+    first pass at the odd stride 3 * 2^17, the mixed-radix middle pass;
+    sampled bins against the FP64 oracle on the FP64 input (its FP32 rounding
+    is far below the tolerance) and the unnormalised round trip divided by N."""
     import paper_1409_5757_gb300 as efft
     from paper_1409_5757_gb300 import inputs
     N, seed, e = 3 << 28, 9, 30
