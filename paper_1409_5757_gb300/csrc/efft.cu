@@ -128,12 +128,14 @@ int apply_mixed_schedule(efft_plan_s* p) {
   const int e = __builtin_ctzll(n);
   int np = 1, a = 0;
   if (n > (uint64_t)tile) {
-    // the largest A <= 2^11 whose middle radix B = M * 2^b keeps b >= 4 (the
+    // the largest A whose middle radix B = M * 2^b keeps b >= 4 (the
     // compile-time middle-pass kernel): the power-of-two outer passes are
-    // the efficient ones; failing that, the A minimising the larger radix
+    // the efficient ones; failing that, the A minimising the larger radix.
+    // A <= 2^11 for complex128, <= 2^10 for complex64 (its radix-32 kernels)
+    const uint64_t amax = (p->dtype == EFFT_C128) ? 2048 : 1024;
     for (int c = 1; 2 * c <= e; ++c) {
       const uint64_t A = 1ull << c, B = n / (A * A);
-      if (A > 2048 || A > (uint64_t)tile || B > (uint64_t)tile) continue;
+      if (A > amax || A > (uint64_t)tile || B > (uint64_t)tile) continue;
       if (__builtin_ctzll(B) >= 4) a = c;
     }
     uint64_t best = 0;

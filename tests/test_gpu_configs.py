@@ -151,8 +151,9 @@ def test_config_m1_3x2p28_complex128(orc):
 
 
 def test_mixed_3x2p28_complex64_sampled(orc):
-    """N = 3 * 2^28 complex64 (6 GiB), schedule (2^11, 3 * 2^6, 2^11): the
-    first pass at the odd stride 3 * 2^17, the mixed-radix middle pass;
+    """N = 3 * 2^28 complex64 (6 GiB), schedule (2^10, 3 * 2^8, 2^10): the
+    wide radix-32 first pass at the odd stride 3 * 2^18, the mixed-radix
+    middle pass;
     sampled bins against the FP64 oracle on the FP64 input (its FP32 rounding
     is far below the tolerance) and the unnormalised round trip divided by N."""
     import paper_1409_5757_gb300 as efft

@@ -90,7 +90,7 @@ def test_mixed_large(orc, name, N):
 
 
 @pytest.mark.parametrize("name,N,a", [("c128", 5 << 20, 8), ("c64", 11 << 20, 8), ("c128", 9 << 22, 9),
-                                      ("c64", 13 << 22, 9), ("c64", 3 << 26, 11)])
+                                      ("c64", 13 << 22, 9), ("c64", 3 << 26, 10)])
 def test_mixed_outer_passes_on_specialised_kernels(orc, name, N, a):
     """(2^a, M 2^b, 2^a) with a in 8..11: the outer passes run on the
     power-of-two pass kernels (first pass at stride M * 2^(e-a)), the middle
