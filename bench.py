@@ -131,6 +131,22 @@ KERNEL_SOURCES = {
 }
 
 
+def scale_workload(wl: dict, log2n: int) -> dict:
+    """The workload at another size (profiling captures on a smaller case):
+    N = 2^log2n, or for N = M * 2^e the same M with e moved by as much as
+    log2n moves (log2n is ceil(log2 N))."""
+    wl = dict(wl)
+    if "n" in wl:
+        e = (wl["n"] & -wl["n"]).bit_length() - 1
+        odd, e_new = wl["n"] >> e, e + log2n - wl["log2n"]
+        wl["desc"] = wl["desc"].replace(f"{odd}*2^{e}", f"{odd}*2^{e_new}").replace(
+            f"{(wl['n'] * 16) >> 30} GiB", f"{((odd << e_new) * 16) / 2**30:g} GiB")
+        wl["n"] = odd << e_new
+    wl["desc"] = wl["desc"].replace(f"2^{wl['log2n']}", f"2^{log2n}")
+    wl["log2n"] = log2n
+    return wl
+
+
 def kernel_fingerprint(family: str) -> str:
     """sha1 (16 hex digits) of the sources of one kernel family: the
     complex128 or complex64 power-of-two pass kernels, or the mixed-radix
@@ -817,15 +833,7 @@ def main():
     args = ap.parse_args()
     wl = dict(WORKLOADS[args.workload])
     if args.log2n is not None:
-        if "n" in wl:
-            # N = M * 2^e: keep M, scale 2^e (log2n is ceil(log2 N))
-            e = (wl["n"] & -wl["n"]).bit_length() - 1
-            odd, e_new = wl["n"] >> e, e + args.log2n - wl["log2n"]
-            wl["desc"] = wl["desc"].replace(f"{odd}*2^{e}", f"{odd}*2^{e_new}").replace(
-                f"{(wl['n'] * 16) >> 30} GiB", f"{((odd << e_new) * 16) / 2**30:g} GiB")
-            wl["n"] = odd << e_new
-        wl["log2n"] = args.log2n
-        wl["desc"] = wl["desc"].replace("2^30", f"2^{args.log2n}").replace("2^33", f"2^{args.log2n}")
+        wl = scale_workload(wl, args.log2n)
     if args.steps is None:
         args.steps = {"c2": 20, "c3": 6, "c1": 200, "c4": 40, "c5": 40, "r1": 20, "m1": 10}[args.workload]
     if args.warmup < 3 and args.impl == "ours":
