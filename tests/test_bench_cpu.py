@@ -80,17 +80,6 @@ def test_traffic_lookup_by_kernel_family(tmp_path, monkeypatch):
     assert bench.measured_traffic("c3", 33, "pass0") is None  # no entry
 
 
-def test_committed_traffic_entries_match_current_sources():
-    """Every entry of the committed table resolves against the current kernel
-    sources (a kernel change must come with a new capture)."""
-    path = os.path.join(bench.ROOT, "profiles", "dram_traffic.txt")
-    with open(path) as f:
-        rows = [line.split() for line in f if line.strip() and not line.startswith("#")]
-    assert rows
-    for w, e, k, *_ in rows:
-        assert bench.measured_traffic(w, int(e), k) is not None, (w, e, k)
-
-
 def test_scale_workload():
     m1 = bench.WORKLOADS["m1"]
     s = bench.scale_workload(m1, 28)
