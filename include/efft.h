@@ -104,14 +104,15 @@ typedef struct efft_plan_s* efft_plan_t;
  *  out    [out] receives the handle (set to NULL on failure).
  *  n      transform length N = M * 2^e (M odd, M <= EFFT_MAX_ODD),
  *         1 <= n <= 2^EFFT_MAX_LOG2N.  For M > 1 the schedule is one
- *         mixed-radix pass (N up to 2048 complex128 / 4096 complex64 points)
- *         or three passes (2^a, M*2^b, 2^a): palindromic, so the final digit
- *         reversal is the same in-place swap; efft_plan_radices then reports
- *         the power-of-two part of each radix (M belongs to the middle or
- *         only pass, whose extent is N / 4^a).  EFFT_FLAG_NORMALIZE is
- *         rejected for M > 1 (EFFT_ERR_UNSUPPORTED: 1/N is not exact in
- *         binary floating point); explicit schedules, the autotuner, the
- *         no-allocation entry point and real-data plans take powers of two.
+ *         mixed-radix pass (N up to 2048 points) or three passes
+ *         (2^a, M*2^b, 2^a): palindromic, so the final digit reversal is the
+ *         same in-place swap; efft_plan_radices then reports the
+ *         power-of-two part of each radix (M belongs to the middle or only
+ *         pass, whose extent is N / 4^a) and efft_plan_schedule the whole
+ *         radices.  EFFT_FLAG_NORMALIZE is rejected for M > 1
+ *         (EFFT_ERR_UNSUPPORTED: 1/N is not exact in binary floating point);
+ *         explicit schedules, the autotuner and the no-allocation entry
+ *         point take powers of two.
  *  dtype  EFFT_C64 or EFFT_C128.
  *  sign   -1 (forward, Eq. 1) or +1 (conjugate sign).
  *  flags  bitwise OR of EFFT_FLAG_*.
@@ -225,6 +226,16 @@ int efft_version(void);
  *    device bytes the plan owns.
  */
 int efft_plan_radices(efft_plan_t plan, int* log2_radices, int cap, int* npasses);
+
+/*
+ * The schedule efft_plan_create chooses for (n, dtype) without the
+ * autotuner, computed on the host with no CUDA call (no device needed):
+ * the radices R_0..R_{p-1} (whole integers: for N = M * 2^e the middle or
+ * only radix carries M) to radices (room for at most `cap` entries) and p to
+ * *npasses; p = 0 for N <= 8 (one direct-sum kernel) and N = 1.
+ * Errors: INVALID_PTR (npasses NULL), INVALID_SIZE, INVALID_DTYPE.
+ */
+int efft_plan_schedule(uint64_t n, int dtype, uint64_t* radices, int cap, int* npasses);
 int efft_plan_info(efft_plan_t plan, double* hbm_passes, uint64_t* table_bytes);
 
 /*

@@ -65,6 +65,8 @@ _SIGNATURES = {
     "efft_batch_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.POINTER(ctypes.c_uint64), ctypes.c_int,
                                          ctypes.c_int, ctypes.c_int, ctypes.c_uint32]),
     "efft_batch_execute": (ctypes.c_int, [_vp, ctypes.POINTER(_vp), _vp]),
+    "efft_plan_schedule": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_int, ctypes.POINTER(ctypes.c_uint64),
+                                          ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     "efft_batch_execute_host_stream": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, ctypes.POINTER(_vp),
                                                       ctypes.POINTER(_vp), ctypes.POINTER(_vp), _vp]),
     "efft_batch_info": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
@@ -236,6 +238,15 @@ class Batch:
                 _LIB.efft_batch_destroy(self._h)
         except Exception:
             pass
+
+
+def plan_schedule(n: int, dtype: int = EFFT_C128) -> list:
+    """The radices efft_plan_create chooses for (n, dtype) without the
+    autotuner (whole integers; computed on the host, no device needed)."""
+    arr = (ctypes.c_uint64 * 8)()
+    np_ = ctypes.c_int()
+    _check(_lib().efft_plan_schedule(int(n), int(dtype), arr, 8, ctypes.byref(np_)), "efft_plan_schedule")
+    return [int(arr[j]) for j in range(np_.value)]
 
 
 def batch_execute_host_stream(batches, host_in, host_out, dev_ptrs, stream: int = 0) -> None:
@@ -413,5 +424,5 @@ def version() -> int:
 
 __all__ = ["Plan", "Batch", "EfftError", "fft_", "fft", "fft_batch_", "rfft_", "irfft_", "get_plan", "get_batch",
            "clear_plans", "version", "EFFT_REAL_FORWARD", "EFFT_REAL_INVERSE",
-           "lib_path", "execute_host_stream", "batch_execute_host_stream", "EFFT_C64", "EFFT_C128", "EFFT_FLAG_DIGIT_REVERSED_OUT",
+           "lib_path", "execute_host_stream", "batch_execute_host_stream", "plan_schedule", "EFFT_C64", "EFFT_C128", "EFFT_FLAG_DIGIT_REVERSED_OUT",
            "EFFT_FLAG_NORMALIZE", "EFFT_FLAG_AUTOTUNE"]

@@ -608,6 +608,29 @@ int efft_plan_radices(efft_plan_t plan, int* log2_radices, int cap, int* npasses
   return EFFT_OK;
 }
 
+int efft_plan_schedule(uint64_t n, int dtype, uint64_t* radices, int cap, int* npasses) {
+  if (!npasses) return EFFT_ERR_INVALID_PTR;
+  if (!valid_size(n)) return EFFT_ERR_INVALID_SIZE;
+  if (dtype != EFFT_C64 && dtype != EFFT_C128) return EFFT_ERR_INVALID_DTYPE;
+  efft_plan_s p;
+  std::memset(&p, 0, sizeof(p));
+  p.n = n;
+  p.log2n = ilog2_u64(n);
+  p.dtype = dtype;
+  p.odd = (uint32_t)(n / (n & (~n + 1)));
+  if (p.odd > 1) {
+    const int rc = apply_mixed_schedule(&p);
+    if (rc != EFFT_OK) return rc;
+  } else {
+    int r[kMaxPasses] = {0, 0, 0, 0};
+    apply_schedule(&p, r, choose_radices(p.log2n, r));
+  }
+  *npasses = p.npasses;
+  for (int j = 0; radices && j < p.npasses && j < cap; ++j)
+    radices[j] = (p.odd > 1) ? p.pass[j].R_int : (1ull << p.pass[j].log2R);
+  return EFFT_OK;
+}
+
 int efft_plan_info(efft_plan_t plan, double* hbm_passes, uint64_t* table_bytes) {
   if (!plan_is_live(plan)) return EFFT_ERR_INVALID_PLAN;
   if (plan->real) {

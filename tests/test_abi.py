@@ -218,6 +218,58 @@ def test_schedule_candidates_are_valid():
         assert _planner_choice()(e) in cands, e
 
 
+def test_plan_schedule_power_of_two_matches_the_planner_table(libs):
+    """efft_plan_schedule (the compiled planner, no device) against the
+    Python reading of its table, for every N = 2^0..2^33 and both dtypes."""
+    import paper_1409_5757_gb300 as efft
+    choose = _planner_choice()
+    for code in (efft.EFFT_C128, efft.EFFT_C64):
+        for e in range(0, 34):
+            got = efft.plan_schedule(1 << e, code)
+            assert got == [1 << r for r in choose(e)], (code, e, got)
+
+
+def test_plan_schedule_mixed_sizes(libs):
+    """N = M * 2^e: the radices multiply to N, are palindromic, only the
+    middle (or only) radix carries M, the outer ones are powers of two at
+    most 2^11 (complex128) / 2^10 (complex64), and the outer radix is the
+    largest one that leaves the middle pass 2^b >= 16 whenever one does."""
+    import paper_1409_5757_gb300 as efft
+    L = efft._lib()
+    for code, amax in ((efft.EFFT_C128, 11), (efft.EFFT_C64, 10)):
+        for M in (3, 5, 7, 9, 11, 13, 15):
+            for e in range(0, 31):
+                N = M << e
+                if N > (1 << 33):
+                    continue
+                r = efft.plan_schedule(N, code)
+                prod = 1
+                for v in r:
+                    prod *= v
+                assert prod == N, (code, N, r)
+                assert r == r[::-1]
+                if N <= 2048:
+                    assert r == [N]
+                    continue
+                assert len(r) == 3 and r[0] & (r[0] - 1) == 0 and r[1] % M == 0
+                a = r[0].bit_length() - 1
+                feasible = [c for c in range(1, amax + 1) if 2 * c <= e and N // (1 << (2 * c)) <= 2048
+                            and ((N >> (2 * c)) & -(N >> (2 * c))).bit_length() - 1 >= 4]
+                if feasible:
+                    assert a == max(feasible), (code, N, r, feasible)
+    assert efft.plan_schedule(3 << 28, efft.EFFT_C128) == [2048, 192, 2048]
+    assert efft.plan_schedule(3 << 28, efft.EFFT_C64) == [1024, 768, 1024]
+    assert efft.plan_schedule(3 << 10, efft.EFFT_C128) == [8, 48, 8]
+    assert efft.plan_schedule(15 << 7, efft.EFFT_C64) == [1920]
+    n = ctypes.c_int()
+    arr = (ctypes.c_uint64 * 4)()
+    assert L.efft_plan_schedule(17, 1, arr, 4, ctypes.byref(n)) == 1     # odd factor 17
+    assert L.efft_plan_schedule(0, 1, arr, 4, ctypes.byref(n)) == 1      # N = 0
+    assert L.efft_plan_schedule(1 << 34, 1, arr, 4, ctypes.byref(n)) == 1
+    assert L.efft_plan_schedule(1 << 10, 7, arr, 4, ctypes.byref(n)) == 2  # dtype
+    assert L.efft_plan_schedule(1 << 10, 1, arr, 4, None) == 4           # npasses NULL
+
+
 def test_real_plan_argument_errors_before_cuda(libs):
     import paper_1409_5757_gb300 as efft
     L = efft._lib()
