@@ -416,4 +416,36 @@ def pin_mixed_closed_forms(o):
         assert abs(np.sum(np.abs(Y) ** 2) / (N * np.sum(np.abs(y) ** 2)) - 1) <= 1e-13, N
 
 
+# --------------------------------------------------------------------------
+# The accuracy metric (Eq. 9, Sec. 5.3, read with complex moduli)
+# --------------------------------------------------------------------------
+def pin_rel_l2_hand_values(o):
+    """Values computed by hand: Fe = (3, 4i), F = (3, 1 + 4i) differ by 1 in
+    one component and ||Fe|| = 5, so the error is exactly 1/5; F = 0 gives 1;
+    F = Fe gives 0; a difference only in the imaginary part counts."""
+    Fe = np.array([3.0, 4.0j])
+    assert o.rel_l2(np.array([3.0, 1.0 + 4.0j]), Fe) == 0.2
+    assert o.rel_l2(np.array([3.0, 4.0j + 1.0j]), Fe) == 0.2
+    assert o.rel_l2(np.zeros(2, np.complex128), Fe) == 1.0
+    assert o.rel_l2(Fe.copy(), Fe) == 0.0
+    # two components off: sqrt(1^2 + 2^2) / sqrt(1 + 1 + 4 + 4) = sqrt(5/10)
+    Fe2 = np.array([1.0, 1.0j, 2.0, 2.0j])
+    F2 = Fe2 + np.array([1.0, 0.0, 2.0j, 0.0])
+    assert abs(o.rel_l2(F2, Fe2) - np.sqrt(0.5)) <= 4e-16
+
+
+def pin_rel_l2_relative_perturbation(o):
+    """F = Fe (1 + delta) for one complex delta gives |delta| at any size and
+    any magnitude of the values (the ratio does not depend on the scale),
+    including values near the binary64 limits (1e+-300)."""
+    g = _rng(11)
+    for N in (1, 7, 4096):
+        Fe = g.uniform(-1, 1, N) + 1j * g.uniform(-1, 1, N)
+        for delta in (1e-3 * (0.6 + 0.8j), 2.5e-9j, -0.125):
+            want = abs(delta)
+            for scale in (1.0, 1e300, 1e-300):
+                got = o.rel_l2(Fe * scale * (1 + delta), Fe * scale)
+                assert abs(got - want) <= 1e-12 * want + 1e-15, (N, delta, scale, got)
+
+
 ALL_PINS = [v for k, v in sorted(globals().items()) if k.startswith("pin_")]

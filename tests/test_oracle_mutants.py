@@ -117,3 +117,55 @@ def test_mixed_mistake_is_caught(orc, kind):
             caught = True
             break
     assert caught, f"mixed-radix mistake {kind} passed every pin"
+
+
+# Planted mistakes in the accuracy metric (Eq. 9), on the CPU: each replaces
+# rel_l2 on a fresh oracle object and must fail a metric pin.
+def _norms(F, Fe):
+    F = np.asarray(F, np.complex128)
+    Fe = np.asarray(Fe, np.complex128)
+    return np.sum(np.abs(F - Fe) ** 2), np.sum(np.abs(Fe) ** 2), np.sum(np.abs(F) ** 2)
+
+
+def _rel_squared(F, Fe):          # the ratio of the squared norms
+    d, e, _ = _norms(F, Fe)
+    return float(d / e)
+
+
+def _rel_no_sqrt_num(F, Fe):      # sqrt dropped in the numerator
+    d, e, _ = _norms(F, Fe)
+    return float(d / np.sqrt(e))
+
+
+def _rel_norm_of_F(F, Fe):        # normalised by ||F|| instead of ||Fe||
+    d, _, f = _norms(F, Fe)
+    return float(np.sqrt(d) / np.sqrt(f)) if f > 0 else float("inf")
+
+
+def _rel_real_part(F, Fe):        # (F - Fe)^2 read on the real parts only
+    F = np.asarray(F, np.complex128)
+    Fe = np.asarray(Fe, np.complex128)
+    return float(np.sqrt(np.sum((F.real - Fe.real) ** 2)) / np.sqrt(np.sum(Fe.real ** 2) + 1e-300))
+
+
+def _rel_unscaled(F, Fe):         # no scaling: overflows / underflows near 1e+-300
+    d, e, _ = _norms(F, Fe)
+    return float(np.sqrt(d) / np.sqrt(e)) if e > 0 else float(np.sqrt(d))
+
+
+@pytest.mark.parametrize("fn", [_rel_squared, _rel_no_sqrt_num, _rel_norm_of_F, _rel_real_part, _rel_unscaled],
+                         ids=["squared", "no-sqrt", "norm-of-F", "real-part", "unscaled"])
+def test_metric_mistake_is_caught(orc, fn):
+    o = oracle.Oracle()
+    o.rel_l2 = fn
+    caught = False
+    for pin in ALL_PINS:
+        if "rel_l2" not in pin.__name__:
+            continue
+        try:
+            with np.errstate(all="ignore"):
+                pin(o)
+        except AssertionError:
+            caught = True
+            break
+    assert caught, f"metric mistake {fn.__name__} passed every pin"
