@@ -23,8 +23,9 @@
  * S = 8 (EFFT_C64: two binary32; torch.complex64).
  *
  * Threading: apart from its profiling records, a plan is immutable after
- * creation and may be shared by host threads; executes of one plan must be
- * stream-ordered (they share the plan's 16-byte device state word), and two
+ * creation and may be shared by host threads.  Executes of one plan on
+ * different buffers may run concurrently on unordered streams: each execute
+ * has a 16-byte device state word of its own (see efft_execute).  Two
  * executes that touch the same buffer concurrently race.
  * All entry points return an efft_status code; none aborts the process.
  */
@@ -127,15 +128,33 @@ int efft_plan_create(efft_plan_t* out, uint64_t n, int dtype, int sign, uint32_t
  * Enqueue one in-place transform of the n elements at `data` on `stream`
  * (a cudaStream_t; NULL = the legacy default stream).  Asynchronous: returns
  * after enqueueing; the result is ready when the stream reaches that point.
+ * This is the paper's EFFT_Transform::RunTransform() (Sec. 4, Listings 12-13),
+ * in place on a caller buffer instead of out of place on plan-owned arrays.
  *  data   device pointer (cudaMalloc / torch CUDA tensor storage) on the
  *         plan's device, aligned to the element size, n*S bytes, owned by
  *         the caller.  Its contents are replaced by X.
- * The plan's device state is used by the launched kernels: executes of one
- * plan must be ordered (same stream, or events), or they race on that state.
+ * Device state: a complex128 execute records the largest binary64 exponent
+ * of its input in a 16-byte state word that its later launches read.  The
+ * plan keeps a ring of 16 such words; an execute takes the next one and its
+ * launches first wait (on the device, through an event) for the execute that
+ * used that word before, so executes on different buffers never share a
+ * word while they run.  An execute enqueued while `stream` is being captured
+ * into a CUDA graph instead gets a word from the stream-ordered allocator,
+ * allocated and freed inside the graph (each launch of the graph has its own).
  * Errors: INVALID_PLAN, INVALID_PTR, MISALIGNED before any launch; LAUNCH if
- * CUDA rejects a launch (the buffer may then be partly transformed).
- * Non-finite inputs (Inf/NaN) give NaN in every output; subnormal complex128
- * inputs are treated as zero.
+ * CUDA rejects a launch (the buffer may then be partly transformed); CUDA if
+ * the stream's capture state cannot be read or the capture was invalidated;
+ * ALLOC if the graph allocation of a captured execute fails.
+ * Special values: non-finite inputs (Inf/NaN) give NaN in every output.
+ * complex128 data are scaled by a power of two so that the largest input
+ * magnitude lies in [1, 2) and carried as pairs of binary32 numbers.  So an
+ * input component whose binary64 exponent is more than 126 below the
+ * largest input exponent is treated as zero (this includes every subnormal
+ * input), and one whose exponent is more than 74 below it keeps 24 of its
+ * 53 significand bits; either change is below 2^-74 of the largest input,
+ * far under the transform's rounding error.  This is not binary64
+ * behaviour.  Outputs whose magnitude falls below the smallest normal
+ * binary64 number are flushed to zero.
  */
 int efft_execute(efft_plan_t plan, void* data, void* stream);
 
@@ -206,11 +225,15 @@ int efft_plan_create_with_radices(efft_plan_t* out, uint64_t n, int dtype, int s
 int efft_plan_autotune(efft_plan_t plan, void* scratch, void* stream, int* cand_log2r, double* cand_ms,
                        int cap, int* ncand);
 
-/* Destroy a plan and free its device tables.  NULL is accepted (no-op).
+/* Destroy a plan and free its device tables, after waiting for the
+ * executes still using its state words.  The paper's ~EFFT_Transform()
+ * (Sec. 4, Listings 12-13); the caller's data buffers are not touched.  NULL is
+ * accepted (no-op).
  * Errors: INVALID_PLAN for a handle that is not a live plan. */
 int efft_plan_destroy(efft_plan_t plan);
 
-/* Static, human-readable text for a status code (never NULL). */
+/* Static, human-readable text for a status code (never NULL).  The paper has
+ * no counterpart (its C++ interface reports no errors). */
 const char* efft_strerror(int status);
 
 /* Library version (EFFT_VERSION of the build). */

@@ -293,10 +293,61 @@ void set_smem_attr() {
                        (int)((CTA + CTA / 16 + 1) * P::kElemBytes));
 }
 
-int init_kernels() {
+// The calling thread's current context: its device ordinal and the driver's
+// context ID (unique for the life of the process, so a context destroyed and
+// created again, e.g. after cudaDeviceReset, gets a new one).  The driver
+// functions come through the runtime's entry-point query, so the library
+// needs no link-time libcuda.  cudaSetDevice makes the device's primary
+// context current (it creates it if there is none yet).
+int current_context(int* dev, unsigned long long* ctx_id) {
+  typedef int (*GetCurrent)(void**);
+  typedef int (*GetId)(void*, unsigned long long*);
   static std::once_flag once;
-  static cudaError_t err = cudaSuccess;
+  static GetCurrent get_current = nullptr;
+  static GetId get_id = nullptr;
   std::call_once(once, [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_current = reinterpret_cast<GetCurrent>(f);
+    f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<GetId>(f);
+    cudaGetLastError();
+  });
+  if (cudaGetDevice(dev) != cudaSuccess || cudaSetDevice(*dev) != cudaSuccess) {
+    cudaGetLastError();
+    return EFFT_ERR_CUDA;
+  }
+  *ctx_id = 0;
+  void* ctx = nullptr;
+  if (get_current && get_id && get_current(&ctx) == 0 && ctx) {
+    unsigned long long id = 0;
+    if (get_id(ctx, &id) == 0) *ctx_id = id;
+  }
+  return EFFT_OK;
+}
+
+// Kernel attributes (the dynamic shared-memory limits) are set once per
+// context: a context of another device, or a new context after a reset,
+// gets them set again.  A failure is not remembered, so the next call
+// retries.
+int init_kernels() {
+  constexpr int kSlots = 64;
+  static std::mutex mu;
+  static int done_dev[kSlots];
+  static unsigned long long done_ctx[kSlots];
+  static int ndone = 0;
+  int dev = 0;
+  unsigned long long ctx = 0;
+  if (current_context(&dev, &ctx) != EFFT_OK) return EFFT_ERR_CUDA;
+  std::lock_guard<std::mutex> lk(mu);
+  for (int i = 0; i < ndone; ++i)
+    if (done_dev[i] == dev && done_ctx[i] == ctx) return EFFT_OK;
+  cudaGetLastError();  // a non-sticky error left by earlier calls is not ours
+  {
     set_smem_attr<PolicyDF, FIRST, 1 << kLog2CtaC128>();
     set_smem_attr<PolicyDF, MID, 1 << kLog2CtaC128>();
     set_smem_attr<PolicyDF, LAST, 1 << kLog2CtaC128>();
@@ -308,10 +359,22 @@ int init_kernels() {
     cudaError_t e0 = mix_set_attrs();
     cudaError_t e1 = fx_set_attrs_df2();
     cudaError_t e2 = fx_set_attrs_f32();
-    err = cudaGetLastError();
+    cudaError_t err = cudaGetLastError();
     if (err == cudaSuccess) err = (e0 != cudaSuccess) ? e0 : (e1 != cudaSuccess) ? e1 : e2;
-  });
-  return err == cudaSuccess ? EFFT_OK : EFFT_ERR_CUDA;
+    if (err != cudaSuccess) return EFFT_ERR_CUDA;
+  }
+  // the table is small: when full, the oldest entry makes room
+  if (ndone == kSlots) {
+    for (int i = 1; i < kSlots; ++i) {
+      done_dev[i - 1] = done_dev[i];
+      done_ctx[i - 1] = done_ctx[i];
+    }
+    --ndone;
+  }
+  done_dev[ndone] = dev;
+  done_ctx[ndone] = ctx;
+  ++ndone;
+  return EFFT_OK;
 }
 
 int gen_table(float4* out, uint64_t count, uint64_t stride, uint64_t N, cudaStream_t st) {
@@ -341,6 +404,15 @@ void free_plan_memory(efft_plan_s* p) {
     for (cudaEvent_t e : *p->pool) cudaEventDestroy(e);
     delete p->pool;
     p->pool = nullptr;
+  }
+  if (p->ring) {
+    for (int k = 0; k < kStateRing; ++k)
+      if (p->ring->done[k]) {
+        cudaEventSynchronize(p->ring->done[k]);
+        cudaEventDestroy(p->ring->done[k]);
+      }
+    delete p->ring;
+    p->ring = nullptr;
   }
   if (p->w2048) cudaFree(p->w2048);
   if (p->tw_lo) cudaFree(p->tw_lo);
@@ -512,15 +584,14 @@ int plan_create_impl(efft_plan_t* out, uint64_t n, int dtype, int sign, uint32_t
   int rc = EFFT_OK;
   if (cudaMalloc(&p->w2048, 2048 * sizeof(float4)) != cudaSuccess ||
       cudaMalloc(&p->tw_lo, nlo * sizeof(float4)) != cudaSuccess ||
-      cudaMalloc(&p->tw_hi, nhi * sizeof(float4)) != cudaSuccess ||
-      cudaMalloc(&p->state, 16) != cudaSuccess) {
+      cudaMalloc(&p->tw_hi, nhi * sizeof(float4)) != cudaSuccess) {
     rc = EFFT_ERR_ALLOC;
   }
   if (rc == EFFT_OK && cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) rc = EFFT_ERR_CUDA;
   if (rc == EFFT_OK) rc = gen_table(p->w2048, 2048, 1, 2048, st);
   if (rc == EFFT_OK) rc = gen_table(p->tw_lo, nlo, 1, n, st);
   if (rc == EFFT_OK) rc = gen_table(p->tw_hi, nhi, nlo, n, st);
-  if (rc == EFFT_OK && cudaMemsetAsync(p->state, 0, 16, st) != cudaSuccess) rc = EFFT_ERR_CUDA;
+  if (rc == EFFT_OK) rc = ring_create(p, st);
   if (rc == EFFT_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = EFFT_ERR_CUDA;
   p->recs = new (std::nothrow) std::vector<efft_plan_s::Rec>();
   p->pool = new (std::nothrow) std::vector<cudaEvent_t>();
@@ -542,7 +613,7 @@ int plan_create_impl(efft_plan_t* out, uint64_t n, int dtype, int sign, uint32_t
     delete p;
     return rc;
   }
-  p->table_bytes = (2048 + nlo + nhi) * sizeof(float4) + 16;
+  p->table_bytes = (2048 + nlo + nhi) * sizeof(float4) + 16 * kStateRing;
   p->magic = kMagic;
   register_plan(p);
   *out = p;
@@ -743,10 +814,63 @@ int enqueue_batch(efft_plan_s* p, void* data, const Batch& bt, cudaStream_t st) 
   return EFFT_OK;
 }
 
-int enqueue(efft_plan_s* p, void* data, cudaStream_t st) {
-  if (p->real) return enqueue_real(p, data, st);
-  const Batch one{nullptr, 1u, p->state};
+int enqueue_state(efft_plan_s* p, void* data, uint32_t* state, cudaStream_t st) {
+  if (p->real) return enqueue_real(p, data, state, st);
+  const Batch one{nullptr, 1u, state};
   return enqueue_batch(p, data, one, st);
+}
+
+int ring_create(efft_plan_s* p, cudaStream_t st) {
+  p->ring = new (std::nothrow) StateRing();
+  if (!p->ring) return EFFT_ERR_ALLOC;
+  if (cudaMalloc(&p->state, 16 * (size_t)kStateRing) != cudaSuccess) return EFFT_ERR_ALLOC;
+  for (int k = 0; k < kStateRing; ++k)
+    if (cudaEventCreateWithFlags(&p->ring->done[k], cudaEventDisableTiming) != cudaSuccess) return EFFT_ERR_CUDA;
+  return cudaMemsetAsync(p->state, 0, 16 * (size_t)kStateRing, st) == cudaSuccess ? EFFT_OK : EFFT_ERR_CUDA;
+}
+
+// Every execute has a state word of its own, so executes of one plan on
+// different buffers may overlap.  Eager executes take the ring's next word,
+// first waiting (on the device) for the execute that used it before.  An
+// execute captured into a CUDA graph gets a word allocated in the graph by
+// the stream-ordered allocator (an allocation node and a free node around
+// its launches), so every launch of the graph has its own word and the ring
+// is not touched by replays.
+int enqueue(efft_plan_s* p, void* data, cudaStream_t st) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
+    cudaGetLastError();
+    return EFFT_ERR_CUDA;
+  }
+  if (cs == cudaStreamCaptureStatusInvalidated) return EFFT_ERR_CUDA;
+  if (cs == cudaStreamCaptureStatusActive) {
+    void* word = nullptr;
+    if (cudaMallocAsync(&word, 16, st) != cudaSuccess) {
+      cudaGetLastError();
+      return EFFT_ERR_ALLOC;
+    }
+    int rc = enqueue_state(p, data, static_cast<uint32_t*>(word), st);
+    if (cudaFreeAsync(word, st) != cudaSuccess && rc == EFFT_OK) rc = EFFT_ERR_CUDA;
+    return rc;
+  }
+  StateRing& r = *p->ring;
+  std::lock_guard<std::mutex> lk(r.mu);
+  const int k = r.next;
+  if (r.used[k] && cudaStreamWaitEvent(st, r.done[k], 0) != cudaSuccess) {
+    cudaGetLastError();
+    return EFFT_ERR_CUDA;
+  }
+  int rc = enqueue_state(p, data, p->state + 4 * k, st);
+  // recorded even after a failed enqueue: the launches already made are
+  // behind it
+  if (cudaEventRecord(r.done[k], st) != cudaSuccess) {
+    cudaGetLastError();
+    if (rc == EFFT_OK) rc = EFFT_ERR_CUDA;
+  } else {
+    r.used[k] = true;
+  }
+  r.next = (k + 1) % kStateRing;
+  return rc;
 }
 
 }  // namespace host
@@ -960,5 +1084,5 @@ int efft_internal_run_in_scratch(void* scratch, size_t scratch_bytes, bool regen
     if ((rc = gen_table(p.tw_lo, nlo, 1, n, st)) != EFFT_OK) return rc;
     if ((rc = gen_table(p.tw_hi, nhi, nlo, n, st)) != EFFT_OK) return rc;
   }
-  return enqueue(&p, data, st);
+  return enqueue_state(&p, data, p.state, st);
 }

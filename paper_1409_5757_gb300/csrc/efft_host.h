@@ -53,6 +53,18 @@ struct Batch {
   uint32_t* state;
 };
 
+// Range-scan state words of a plan's executes: a ring of kStateRing 16-byte
+// words (one per execute) in device memory, each reused only after the
+// execute that used it last has finished (an event recorded behind it), so
+// that executes of one plan on different buffers need no ordering.
+constexpr int kStateRing = 16;
+struct StateRing {
+  std::mutex mu;
+  cudaEvent_t done[kStateRing] = {};
+  bool used[kStateRing] = {};
+  int next = 0;
+};
+
 // A radix schedule (log2 R_0 .. log2 R_{np-1}).
 struct Tuned {
   int np;
@@ -95,7 +107,8 @@ struct efft_plan_s {
   float4* w2048;
   float4* tw_lo;
   float4* tw_hi;
-  uint32_t* state;
+  uint32_t* state;        // kStateRing words of 16 bytes (efft::host::StateRing)
+  efft::host::StateRing* ring;
   uint64_t table_bytes;
   // profiling: CUDA event pairs recorded around each launch
   bool profiling;
@@ -116,6 +129,10 @@ struct efft_plan_s {
 
 namespace efft {
 namespace host {
+
+// The calling thread's device and current context ID (0 when the driver
+// cannot report it); makes the device's primary context current.
+int current_context(int* dev, unsigned long long* ctx_id);
 
 // Registry of live handles (plans here, batches in efft_batch.cu).
 std::mutex& registry_mutex();
@@ -162,9 +179,16 @@ void prof_end(efft_plan_s* p, int rec, cudaStream_t st);
 cudaError_t mix_set_attrs();
 cudaError_t launch_mix(const efft_plan_s* p, const Pass& ps, void* data, const Batch& bt, cudaStream_t st);
 // The real-data launch sequence (efft_real.cu).
-int enqueue_real(efft_plan_s* p, void* data, cudaStream_t st);
+// `state`: the execute's 16-byte device state word.
+int enqueue_real(efft_plan_s* p, void* data, uint32_t* state, cudaStream_t st);
 int enqueue_batch(efft_plan_s* p, void* data, const Batch& bt, cudaStream_t st);
+// One transform with the given state word (the caller owns its ordering).
+int enqueue_state(efft_plan_s* p, void* data, uint32_t* state, cudaStream_t st);
+// One transform with a state word of the plan's ring (or, while `st` is
+// being captured into a CUDA graph, one allocated in that graph).
 int enqueue(efft_plan_s* p, void* data, cudaStream_t st);
+// Device state of a plan: kStateRing zeroed words and their events.
+int ring_create(efft_plan_s* p, cudaStream_t st);
 
 }  // namespace host
 }  // namespace efft

@@ -9,7 +9,7 @@
 //
 // The array is a device symbol: in host code its name is only a stand-in, so
 // the host obtains its device address with cudaGetSymbolAddress (once per
-// device, on the first call with that device current) and hands that
+// context, on the first call with that context current) and hands that
 // address to the kernels.  Every GPU that loads the library holds the array
 // until the process exits.
 #include <cuda_runtime.h>
@@ -24,6 +24,11 @@
 // tables first when `regen` is set.
 int efft_internal_run_in_scratch(void* scratch, size_t scratch_bytes, bool regen, void* data, uint64_t n,
                                  int dtype, int sign, uint32_t flags, cudaStream_t st);
+namespace efft {
+namespace host {
+int current_context(int* dev, unsigned long long* ctx_id);
+}  // namespace host
+}  // namespace efft
 
 namespace {
 
@@ -31,11 +36,32 @@ namespace {
 constexpr size_t kScratchBytes = (2048 + 4096 + 4096) * 16 + 256;
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
-constexpr int kMaxDevices = 64;
+// What the host knows about the array in one context: its device address
+// and the log2 N whose tables it holds (-1: none, or not known to be
+// complete).  A context is identified by its device and the driver's
+// context ID, so a context created after a device reset starts afresh.
+struct Known {
+  int dev;
+  unsigned long long ctx;
+  void* addr;
+  int tables_log2n;
+};
+constexpr int kMaxContexts = 64;
 std::mutex g_mu;
-void* g_addr[kMaxDevices] = {};
-int g_tables_log2n[kMaxDevices];
-bool g_init_done = false;
+Known g_known[kMaxContexts];
+int g_nknown = 0;
+
+Known* find_or_add(int dev, unsigned long long ctx) {
+  for (int i = 0; i < g_nknown; ++i)
+    if (g_known[i].dev == dev && g_known[i].ctx == ctx) return &g_known[i];
+  if (g_nknown == kMaxContexts) {  // full: drop the oldest context's entry
+    for (int i = 1; i < kMaxContexts; ++i) g_known[i - 1] = g_known[i];
+    --g_nknown;
+  }
+  Known* k = &g_known[g_nknown++];
+  *k = Known{dev, ctx, nullptr, -1};
+  return k;
+}
 
 }  // namespace
 
@@ -44,12 +70,17 @@ extern "C" int efft_execute_noalloc(void* data, uint64_t n, int dtype, int sign,
   if (dtype != EFFT_C64 && dtype != EFFT_C128) return EFFT_ERR_INVALID_DTYPE;
   if (sign != -1 && sign != 1) return EFFT_ERR_INVALID_SIGN;
   if (flags & ~(EFFT_FLAG_DIGIT_REVERSED_OUT | EFFT_FLAG_NORMALIZE)) return EFFT_ERR_INVALID_FLAGS;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) {
+  unsigned long long ctx = 0;
+  if (efft::host::current_context(&dev, &ctx) != EFFT_OK) return EFFT_ERR_CUDA;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
     cudaGetLastError();
     return EFFT_ERR_CUDA;
   }
-  if (dev < 0 || dev >= kMaxDevices) return EFFT_ERR_UNSUPPORTED;
+  if (cs == cudaStreamCaptureStatusInvalidated) return EFFT_ERR_CUDA;
+  const bool capturing = (cs == cudaStreamCaptureStatusActive);
   int log2n = 0;
   while ((1ull << log2n) < n) ++log2n;
 
@@ -57,30 +88,36 @@ extern "C" int efft_execute_noalloc(void* data, uint64_t n, int dtype, int sign,
   bool regen = false;
   {
     std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_init_done) {
-      for (int i = 0; i < kMaxDevices; ++i) g_tables_log2n[i] = -1;
-      g_init_done = true;
-    }
-    if (!g_addr[dev]) {
+    Known* k = find_or_add(dev, ctx);
+    if (!k->addr) {
       void* ptr = nullptr;
       cudaError_t err = cudaGetSymbolAddress(&ptr, g_scratch);
       if (err != cudaSuccess || !ptr) {
         cudaGetLastError();
         return EFFT_ERR_CUDA;
       }
-      g_addr[dev] = ptr;
+      k->addr = ptr;
     }
-    base = g_addr[dev];
-    regen = (g_tables_log2n[dev] != log2n);
-    // The tables are enqueued on this call's stream; a later call with the same
-    // N reuses them (calls that overlap on the GPU race, as documented).
-    if (regen) g_tables_log2n[dev] = log2n;
+    base = k->addr;
+    if (capturing) {
+      // A captured call runs when its graph is launched, after any number of
+      // other calls: it regenerates its own tables at every launch, and the
+      // next eager call rebuilds them too (the graph's launches overwrite
+      // whatever the array held).
+      regen = true;
+      k->tables_log2n = -1;
+    } else {
+      regen = (k->tables_log2n != log2n);
+      // the tables are enqueued on this call's stream; a later call with the
+      // same N reuses them (calls that overlap on the GPU race, as documented)
+      if (regen) k->tables_log2n = log2n;
+    }
   }
-  int rc = efft_internal_run_in_scratch(base, kScratchBytes, regen, data, n, dtype, sign, flags,
-                                        reinterpret_cast<cudaStream_t>(stream));
-  if (rc != EFFT_OK && regen) {
+  int rc = efft_internal_run_in_scratch(base, kScratchBytes, regen, data, n, dtype, sign, flags, st);
+  if (rc != EFFT_OK && regen && !capturing) {
     std::lock_guard<std::mutex> lk(g_mu);
-    g_tables_log2n[dev] = -1;  // tables may be incomplete: rebuild next time
+    Known* k = find_or_add(dev, ctx);
+    k->tables_log2n = -1;  // tables may be incomplete: rebuild next time
   }
   return rc;
 }

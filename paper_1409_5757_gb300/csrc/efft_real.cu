@@ -185,33 +185,35 @@ namespace host {
 // complex output is at most (N/2) sqrt(2) times the largest input, or
 // sqrt(2) times it when normalised by 2/N).  Inverse: a range scan of the
 // perm array, the pairs (|A|, |D| <= 2 max|F|), then the complex transform.
-int enqueue_real(efft_plan_s* p, void* data, cudaStream_t st) {
+// One state word serves the whole execute: the complex transform's range
+// scan writes it and the pair kernel then reads it (forward), or the pair
+// kernel reads the perm array's scan before the complex transform rescans.
+int enqueue_real(efft_plan_s* p, void* data, uint32_t* state, cudaStream_t st) {
   if (fault_injected("launch")) return EFFT_ERR_LAUNCH;
   efft_plan_s* in = p->inner;
   const bool c128 = (p->dtype == EFFT_C128);
   if (p->real == EFFT_REAL_FORWARD) {
-    int rc = enqueue(in, data, st);
+    int rc = enqueue_state(in, data, state, st);
     if (rc != EFFT_OK) return rc;
     const int grow = 2 + ((p->flags & EFFT_FLAG_NORMALIZE) ? 0 : in->log2n);
     if (c128 && in->log2n == 0) {
       // N = 2: the one-point complex transform launches nothing, so no scan ran
       int rec = prof_begin(p, 0, st);
-      rc = launch_range_scan(data, 1, p->state, nullptr, 1, st);
+      rc = launch_range_scan(data, 1, state, nullptr, 1, st);
       prof_end(p, rec, st);
       if (rc != EFFT_OK) return rc;
-      return launch_pairs(p, data, p->state, grow, st);
     }
-    return launch_pairs(p, data, c128 ? in->state : nullptr, grow, st);
+    return launch_pairs(p, data, c128 ? state : nullptr, grow, st);
   }
   if (c128) {
     int rec = prof_begin(p, 0, st);
-    const int rc = launch_range_scan(data, p->n >> 1, p->state, nullptr, 1, st);
+    const int rc = launch_range_scan(data, p->n >> 1, state, nullptr, 1, st);
     prof_end(p, rec, st);
     if (rc != EFFT_OK) return rc;
   }
-  int rc = launch_pairs(p, data, c128 ? p->state : nullptr, 2, st);
+  int rc = launch_pairs(p, data, c128 ? state : nullptr, 2, st);
   if (rc != EFFT_OK) return rc;
-  return enqueue(in, data, st);
+  return enqueue_state(in, data, state, st);
 }
 
 }  // namespace host
@@ -255,12 +257,12 @@ extern "C" int efft_plan_create_real(efft_plan_t* out, uint64_t n, int precision
   const uint64_t nlo = 1ull << p->rtwB, nhi = 1ull << (em - p->rtwB);
   cudaStream_t st = nullptr;
   if (fault_injected("alloc") || cudaMalloc(&p->rtw_lo, nlo * sizeof(float4)) != cudaSuccess ||
-      cudaMalloc(&p->rtw_hi, nhi * sizeof(float4)) != cudaSuccess || cudaMalloc(&p->state, 16) != cudaSuccess)
+      cudaMalloc(&p->rtw_hi, nhi * sizeof(float4)) != cudaSuccess)
     rc = EFFT_ERR_ALLOC;
   if (rc == EFFT_OK && cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) rc = EFFT_ERR_CUDA;
   if (rc == EFFT_OK) rc = gen_table(p->rtw_lo, nlo, 1, n, st);
   if (rc == EFFT_OK) rc = gen_table(p->rtw_hi, nhi, nlo, n, st);
-  if (rc == EFFT_OK && cudaMemsetAsync(p->state, 0, 16, st) != cudaSuccess) rc = EFFT_ERR_CUDA;
+  if (rc == EFFT_OK) rc = ring_create(p, st);
   if (rc == EFFT_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = EFFT_ERR_CUDA;
   if (st) cudaStreamDestroy(st);
   p->recs = new (std::nothrow) std::vector<efft_plan_s::Rec>();
@@ -272,7 +274,7 @@ extern "C" int efft_plan_create_real(efft_plan_t* out, uint64_t n, int precision
     delete p;
     return rc;
   }
-  p->table_bytes = (nlo + nhi) * sizeof(float4) + 16;
+  p->table_bytes = (nlo + nhi) * sizeof(float4) + 16 * kStateRing;
   p->magic = kMagic;
   register_plan(p);
   *out = p;
