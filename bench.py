@@ -4,19 +4,27 @@
     python bench.py [--gpus N] [--steps K] [--warmup W] [--workload c2|c3|c1|c4|c5|r1|m1]
                     [--impl ours|reference]
 
-Default workload (the headline configuration): one step = a forward DFT
-(sign -1, Eq. 1) followed by the normalised inverse (sign +1, times 1/N) of
-N = 2^30 complex128 points in place (16 GiB), input uniform[-1,1) re/im plus
-64 seeded tones.  value = 5*N*log2(N) flop per transform x transforms / time
-(GFLOP/s), whole job.  The input (16 GiB) is larger than the
-129 MB L2, so no flush is needed between timed iterations.
+Default workload (the headline configuration, c3): one step = one in-place
+transform of N = 2^33 complex128 points (128 GiB in HBM, no out-of-place
+buffer), the forward (sign -1, Eq. 1) and the normalised inverse (sign +1,
+times 1/N) alternating, input uniform[-1,1) re/im.  value = 5*N*log2(N)
+flop per transform x transforms / time (GFLOP/s), whole job.  The input is
+larger than the 129 MB L2, so no flush is needed between timed iterations.
+The default line also carries `fp32_form`: the complex64 form at N = 2^31
+(Gaussian input) against the complex128 form at the same N, timed, with the
+complex64 error against the FP64 oracle on sampled bins and against the
+complex128 result over the whole array.
+Workload c2: forward then normalised inverse of N = 2^30 complex128 points
+(16 GiB), uniform[-1,1) re/im plus 64 seeded tones.
 
 Workload c5 (batched, mixed sizes): 256 complex64 transforms of 2^12..2^24
 points in one arena, each direction one efft_batch_execute (one CUDA graph
 launch); a step = forward + normalised conjugate-sign transform of all 256.
 
 --impl reference times the CPU oracle (the FP64 radix-2 FFT, as it stands)
-on the host cores on a bounded sample of the same workload.
+on the host cores; each step is a bounded sample of the workload's step
+(the same transforms at a smaller N, named in `sample_of_step`), and
+ms_per_step is the time that sample step took.
 
 Multi-GPU: the transform does not shard across GPUs (one FFT
 per GPU); under torchrun every rank runs an independent replica ("replicas
@@ -336,20 +344,23 @@ def oracle_batch_time(wl, budget_s: float):
 def run_reference_batch(args, wl):
     K, W = args.steps, args.warmup
     budget = 150.0 / max(K + W, 1)
-    rates, cores, k = [], None, 0
+    rates, step_s, cores, k = [], [], None, 0
     for i in range(W + K):
+        t0 = time.perf_counter()
         fl, el, k, cores = oracle_batch_time(wl, budget)
         if i >= W:
             rates.append(fl / el)
+            step_s.append(time.perf_counter() - t0)
     value = statistics.mean(rates) / 1e9
-    total = sum(2 * flops(1 << e) for e in batch_sizes(wl))
-    ms = total / (value * 1e9) * 1e3
+    ms = 1e3 * statistics.mean(step_s)
     sample = (f"FP64 radix-2 oracle, forward transforms of the first {k} arrays of the batch (in batch order) "
-              f"per step, about {budget:.0f} s of host time; a full step is 2 x 256 transforms")
+              f"per step, about {budget:.0f} s of host time; a full step is 2 x 256 transforms; ms_per_step is "
+              f"that sample step's time")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": args.gpus,
         "steps": K, "warmup": W, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config_of(wl),
+        "sample_of_step": {"transforms": k, "of": 2 * len(batch_sizes(wl))},
         "cpu_baseline": {"value": value, "unit": "GFLOP/s", "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -364,25 +375,36 @@ def run_reference(args, wl):
         return 0
     if wl.get("batch"):
         return run_reference_batch(args, wl)
+    import oracle
+    o = oracle.get()
     K, W = args.steps, args.warmup
-    budget = 150.0 / max(K + W, 1)
+    tps = 2 if wl["fwd_inv"] else 1
+    budget = 150.0 / max(K + W, 1) / tps
     e = oracle_sample_log2n(budget, wl["log2n"])
+    x = o.gen_uniform(wl["seed"], 1 << e)
     times = []
-    cores = None
     for i in range(W + K):
-        dt, cores = oracle_time(e, wl["seed"])
+        # one step of the workload at N = 2^e: the forward transform, and for
+        # forward-inverse workloads the conjugate-sign transform of its result
+        t0 = time.perf_counter()
+        y = o.fft_radix2(x, -1)
+        if tps == 2:
+            o.fft_radix2(y, +1)
+        dt = time.perf_counter() - t0
         if i >= W:
             times.append(dt)
-    tps = 2 if wl["fwd_inv"] else 1
-    ms = 1e3 * sum(times) / len(times) * tps
+    cores = o.threads
+    ms = 1e3 * statistics.mean(times)
     value = tps * flops(1 << e) / (ms * 1e-3) / 1e9
-    sample = (f"FP64 radix-2 oracle, forward transform of N=2^{e} (of the 2^{wl['log2n']} workload), "
-              f"seeded uniform input, timed per transform; a step = {tps} transform(s)")
+    sample = (f"each step: {'forward then conjugate-sign' if tps == 2 else 'one forward'} FP64 radix-2 oracle "
+              f"transform{'s' if tps == 2 else ''} of N=2^{e} (the workload's step at N=2^{wl['log2n']} scaled "
+              f"down to about {budget * tps:.0f} s of host time), seeded uniform input; ms_per_step is that "
+              f"sample step's time")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": args.gpus,
         "steps": K, "warmup": W, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": config_of(wl),
+        "config": config_of(wl), "sample_of_step": {"log2N": e, "N": 1 << e, "transforms": tps},
         "cpu_baseline": {"value": value, "unit": "GFLOP/s", "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -530,13 +552,29 @@ def run_ours(args, wl):
         step(done)  # untimed: complete the last forward / inverse pair
         done += 1
     round_trips = done if wl["fwd_inv"] else done // 2
+    tol_rt = 2e-14 * wl["log2n"] if c128 else 4e-6 * wl["log2n"]
     if keep is not None:
         # forward then inverse, round_trips times: x returns (times N per
         # round trip when the inverse is unnormalised)
         scale = 1.0 if wl.get("normalize", True) else float(N) ** (-round_trips)
         num, den = inputs.diff_norms(x, keep, scale)
         accuracy = {"roundtrip_rel_l2_after_all_steps": math.sqrt(num / den), "round_trips": round_trips,
-                    "tolerance_per_round_trip": 2e-14 * wl["log2n"] if c128 else 4e-6 * wl["log2n"]}
+                    "tolerance_per_round_trip": tol_rt}
+    elif not wl["tones"] and not wl["gauss"] and not real and wl.get("normalize", True):
+        # no room for a copy: the input regenerated chunk by chunk (the same
+        # seeded stream) and compared with the buffer
+        chunk = min(N, 1 << 28)
+        y = torch.empty(chunk, dtype=tdt, device=dev)
+        num = den = 0.0
+        for c0 in range(0, N, chunk):
+            inputs.fill_uniform(y, wl["seed"], n0=c0)
+            a_, b_ = inputs.diff_norms(x[c0:c0 + chunk], y)
+            num += a_
+            den += b_
+        del y
+        accuracy = {"roundtrip_rel_l2_after_all_steps": math.sqrt(num / den), "round_trips": round_trips,
+                    "tolerance_per_round_trip": tol_rt,
+                    "reference": "the seeded input regenerated in 2^28-element chunks"}
 
     # roofline of the dominant kernel
     peak, peak_kind = peaks()
@@ -572,6 +610,7 @@ def run_ours(args, wl):
                 "ops_per_element": ope, "pass": f"2^{rad[j]} {kind}",
                 "peak_kind": "152 SMs x 128 FP32 lanes x 2070 MHz (maximum SM clock)"}
     launches = sum(v[1] for v in prof.values())
+    radices_now = fwd.radices()
     floor_gbs = world * tps * 2 * N * S / (ms_per_step * 1e-3) / 1e9
 
     # the FP32 form against the FP64 form at the same N (complex64 workloads)
@@ -604,7 +643,31 @@ def run_ours(args, wl):
     # its input from pinned host memory, transforms, copies the result back;
     # copies of neighbouring steps overlap the transforms of this one)
     e2e = None
-    if N * S <= (32 << 30) and not args.no_e2e:
+    host_room = mem_available()
+    if N * S > (32 << 30) and not args.no_e2e and host_room is not None and host_room >= N * S + (24 << 30):
+        # the whole array does not fit twice in HBM: one device buffer (the
+        # timed one) and one pinned host array that is both input and output,
+        # so each step copies 2^33 x 16 B in, transforms, copies it back
+        torch.cuda.synchronize(dev)
+        t_pin = time.perf_counter()
+        hbuf = inputs.PinnedHost(N, tdt)
+        t_pin = time.perf_counter() - t_pin
+        hbuf.tensor.copy_(x)
+        Ke = 2
+        efft.execute_host_stream([fwd], [hbuf.ptr], [hbuf.ptr], [x.data_ptr()], sp)  # warm
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        efft.execute_host_stream([fwd], [hbuf.ptr] * Ke, [hbuf.ptr] * Ke, [x.data_ptr()], sp)
+        dt = (time.perf_counter() - t0) / Ke
+        hbuf.free()
+        del hbuf
+        e2e = {"value": world * fpt / dt / 1e9, "unit": "GFLOP/s",
+               "h2d_bytes_per_step": N * S, "d2h_bytes_per_step": N * S,
+               "ms_per_step": dt * 1e3, "steps": Ke, "pin_seconds": t_pin,
+               "api": "efft_execute_host_stream (one cudaHostAlloc host array as input and output, the one "
+                      "device buffer; copy in, transform, copy out in sequence: a second 128 GiB device "
+                      "buffer does not fit)"}
+    elif N * S <= (32 << 30) and not args.no_e2e:
         src = keep if keep is not None else x
         hin = inputs.PinnedHost(N, tdt)
         hout = inputs.PinnedHost(N, tdt)
@@ -628,7 +691,9 @@ def run_ours(args, wl):
         del hin, hout, bufs
     elif not args.no_e2e:
         e2e = {"value": None, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0,
-               "skipped": "pinned host copy of the 128 GiB array is not made on this host"}
+               "skipped": f"a pinned host copy of the {N * S >> 30} GiB array needs {(N * S >> 30) + 24} GiB of "
+                          f"host memory; MemAvailable is "
+                          f"{'unknown' if host_room is None else str(host_room >> 30) + ' GiB'}"}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -644,6 +709,18 @@ def run_ours(args, wl):
                "nproc": os.cpu_count(), "cpu_model": cpu_model(),
                "single_core": oracle_single_core(min(e, 24), wl["seed"])}
 
+    for p in (fwd, inv):
+        p.destroy()
+    fwd = inv = None
+    fp32 = None
+    if args.workload == "c3" and not args.no_fp32_form and args.log2n is None:
+        del x
+        keep = None
+        import gc
+        gc.collect()
+        torch.cuda.empty_cache()
+        fp32 = fp32_form(dev, stream, rank == 0 and world == 1 and not args.no_cpu)
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": K, "warmup": W,
@@ -651,18 +728,110 @@ def run_ours(args, wl):
             "dtype": (DTYPE_NAME_REAL if real else DTYPE_NAME)[wl["dtype"]], "data": "synthetic",
             "config": config_of(wl),
             "hbm_gbs": hbm_gbs, "hbm_passes_per_transform": hbm_passes, "floor_equivalent_gbs": floor_gbs,
-            "radices_log2": fwd.radices(),
-            "fp64_form_same_n": same_n_c128,
+            "radices_log2": radices_now,
+            "fp64_form_same_n": same_n_c128, "fp32_form": fp32,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "clocks": clocks, "accuracy": accuracy, "impl": "ours",
         }
         print(json.dumps(line), flush=True)
-    for p in (fwd, inv):
-        p.destroy()
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
     return 0
+
+
+def mem_available():
+    """Host memory the kernel reports as available (bytes), or None."""
+    try:
+        with open("/proc/meminfo") as f:
+            for line in f:
+                if line.startswith("MemAvailable:"):
+                    return int(line.split()[1]) * 1024
+    except OSError:
+        pass
+    return None
+
+
+def fp32_form(dev, stream, with_oracle: bool):
+    """The precision form against the FP64 form on the same GPU at the same
+    N: complex64 (FP32 butterflies, FP64-generated twiddles, compensated
+    products) and complex128 transforms of N = 2^31 points, Gaussian(0,1)
+    re/im (seed 4), each timed over alternating forward / normalised inverse
+    transforms (CUDA events); the complex64 forward result's error against
+    the complex128 result of the same (FP32-rounded) input over the whole
+    array, and against the FP64 oracle at sampled bins."""
+    import torch
+
+    import paper_1409_5757_gb300 as efft
+    from paper_1409_5757_gb300 import inputs
+    wl = WORKLOADS["c4"]
+    e = wl["log2n"]
+    N = 1 << e
+    sp = stream.cuda_stream
+
+    def timed(plans, buf, k):
+        for i in range(3):
+            plans[i % 2].execute(buf.data_ptr(), sp)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for i in range(k):
+            plans[(i + 1) % 2].execute(buf.data_ptr(), sp)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1) / k
+
+    out = {"workload": wl["desc"], "N": N, "log2N": e}
+    x = torch.empty(N, dtype=torch.complex64, device=dev)
+    inputs.fill_gaussian(x, wl["seed"])
+    p64 = [efft.Plan(N, efft.EFFT_C64, -1), efft.Plan(N, efft.EFFT_C64, +1, efft.EFFT_FLAG_NORMALIZE)]
+    ms64 = timed(p64, x, 10)
+    inputs.fill_gaussian(x, wl["seed"])
+    y = x.to(torch.complex128)  # the same FP32 values, promoted
+    sumsq = inputs.diff_norms(y)[0]
+    p128 = [efft.Plan(N, efft.EFFT_C128, -1), efft.Plan(N, efft.EFFT_C128, +1, efft.EFFT_FLAG_NORMALIZE)]
+    p64[0].execute(x.data_ptr(), sp)
+    p128[0].execute(y.data_ptr(), sp)
+    xx = x.to(torch.complex128)
+    num, den = inputs.diff_norms(xx, y)
+    del xx
+    ks = None
+    if with_oracle:
+        import numpy as np
+        import oracle
+        room = mem_available()
+        if room is None or room >= 3 * N * 16 + (8 << 30):
+            g = np.random.default_rng(44)
+            ks = sorted({0, 1, N // 2, N - 1} | {int(v) for v in g.integers(0, N, 4)})
+            got = x[torch.tensor(ks, device=dev)].cpu().numpy().astype(np.complex128)
+            z = torch.empty(N, dtype=torch.complex64, device=dev)
+            inputs.fill_gaussian(z, wl["seed"])
+            zin = z.cpu().numpy()
+            del z
+            t0 = time.perf_counter()
+            ref = oracle.get().dft_bins(zin.astype(np.complex128), np.array(ks, np.int64), -1)
+            t_or = time.perf_counter() - t0
+            del zin
+            err_s = math.sqrt(float(np.mean(np.abs(got - ref) ** 2)) / sumsq)
+            out["error_vs_fp64_oracle_sampled"] = {
+                "rel_l2_estimate": err_s, "bins": ks, "oracle_seconds": t_or,
+                "estimator": "sqrt(mean_k |F_k - Fe_k|^2 / sum_n |x_n|^2) (Eq. 9 with Parseval)"}
+    inputs.fill_gaussian(y, wl["seed"])
+    ms128 = timed(p128, y, 6)
+    for p in p64 + p128:
+        p.destroy()
+    del x, y
+    torch.cuda.empty_cache()
+    out.update({
+        "complex64": {"ms_per_transform": ms64, "gflops": flops(N) / (ms64 * 1e-3) / 1e9,
+                      "hbm_gbs_floor_equivalent": 2 * N * 8 / (ms64 * 1e-3) / 1e9},
+        "complex128": {"ms_per_transform": ms128, "gflops": flops(N) / (ms128 * 1e-3) / 1e9,
+                       "hbm_gbs_floor_equivalent": 2 * N * 16 / (ms128 * 1e-3) / 1e9},
+        "speedup_of_complex64": ms128 / ms64,
+        "error_vs_complex128_full": math.sqrt(num / den),
+        "tolerance_stated": 2e-6 * e,
+    })
+    return out
 
 
 def run_batch(args, wl):
@@ -818,7 +987,7 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=None)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="c3", choices=sorted(WORKLOADS))
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg")
@@ -828,6 +997,8 @@ def main():
                     help="explicit schedule, log2 radices comma-separated (profiling of one kernel variant)")
     ap.add_argument("--no-compare", action="store_true",
                     help="complex64 workloads: skip the complex128 run at the same N")
+    ap.add_argument("--no-fp32-form", action="store_true",
+                    help="c3: skip the complex64-vs-complex128 comparison at N = 2^31")
     ap.add_argument("--log2n", type=int, default=None,
                     help="override the workload's size (profiling captures on a smaller case)")
     args = ap.parse_args()

@@ -70,6 +70,33 @@ def test_grad_finite_differences(orc, sign):
             assert abs(d - want) <= 1e-7 * max(1.0, abs(want)), (j, unit, d, want)
 
 
+@pytest.mark.parametrize("e", [10, 16])
+def test_grad_finite_differences_c64(orc, e):
+    """complex64: the gradient of the FP32 transform against central
+    differences of the loss evaluated in FP64 by the oracle on the FP32
+    input promoted to FP64 (h = 1e-3), within the FP32 tolerance relative to
+    the gradient's RMS."""
+    from paper_1409_5757_gb300.autograd import dft
+    N = 1 << e
+    x = orc.gen_uniform(78, N).astype(np.complex64).astype(np.complex128)
+    w2 = np.random.default_rng(4).uniform(0, 1, N) ** 2
+    xt = torch.from_numpy(x.astype(np.complex64)).cuda().requires_grad_(True)
+    L = _loss(dft(xt, -1), torch.from_numpy(w2).float().cuda())
+    L.backward()
+    grad = xt.grad.cpu().numpy().astype(np.complex128)
+    rms = float(np.sqrt(np.mean(np.abs(grad) ** 2)))
+    h = 1e-3
+    for j in (0, 1, 333, N // 2, N - 1):
+        for unit in (1.0, 1j):
+            xp = x.copy()
+            xm = x.copy()
+            xp[j] += unit * h
+            xm[j] -= unit * h
+            d = (np.sum(w2 * np.abs(orc.dft(xp, -1)) ** 2) - np.sum(w2 * np.abs(orc.dft(xm, -1)) ** 2)) / (2 * h)
+            want = grad[j].real if unit == 1.0 else grad[j].imag
+            assert abs(d - want) <= 2e-6 * 2 * e * 10 * rms, (j, unit, d, want, rms)
+
+
 def test_normalised_grad(orc):
     from paper_1409_5757_gb300.autograd import dft
     N = 1 << 14

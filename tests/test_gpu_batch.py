@@ -303,3 +303,53 @@ def test_batch_grad_finite_differences(orc):
             gj = xt[ti].grad[j].item()
             want = gj.real if unit == 1.0 else gj.imag
             assert abs(d - want) <= 1e-7 * max(1.0, abs(want)), (ti, j, unit, d, want)
+
+
+def test_batch_grad_256_uneven_c64_at_config_scale(orc):
+    """The batched, differentiated configuration at full scale: 256 complex64
+    transforms of 2^e points, e uniform in {12..24} (numpy default_rng(5)),
+    inputs the seed-5 uniform stream laid end to end, one graph launch
+    forward and one backward through autograd.dft_batch; loss
+    L = sum_t sum_k w_tk^2 |X_tk|^2 with w uniform[0,1).
+    For the smallest and the largest member: the gradient against the closed
+    form 2 F^H(|w|^2 X) (F, F^H from the FP64 oracle on the FP32 input
+    promoted to FP64), and central finite differences of L evaluated by the
+    FP64 oracle (h = 1e-3) at sampled coordinates, real and imaginary."""
+    from paper_1409_5757_gb300 import inputs
+    from paper_1409_5757_gb300.autograd import dft_batch
+    es = [int(e) for e in np.random.default_rng(5).integers(12, 25, 256)]
+    offs = np.concatenate([[0], np.cumsum([1 << e for e in es])]).astype(np.int64)
+    arena = torch.empty(int(offs[-1]), dtype=torch.complex64, device="cuda")
+    inputs.fill_uniform(arena, 5)
+    xt = [arena[int(offs[i]):int(offs[i + 1])].clone().requires_grad_(True) for i in range(256)]
+    del arena
+    g = np.random.default_rng(55)
+    ws = [g.uniform(0, 1, 1 << e) for e in es]
+    w2t = [torch.from_numpy(w ** 2).float().cuda() for w in ws]
+    Xs = dft_batch(xt, -1)
+    L = sum(torch.sum(w2.double() * (X.real.double() ** 2 + X.imag.double() ** 2)) for w2, X in zip(w2t, Xs))
+    L.backward()
+    del Xs, w2t
+    for i in (int(np.argmin(es)), int(np.argmax(es))):
+        N = 1 << es[i]
+        x = orc.gen_uniform(5, N, n0=int(offs[i])).astype(np.complex64).astype(np.complex128)
+        assert np.array_equal(x, xt[i].detach().cpu().numpy().astype(np.complex128)), "input stream"
+        w2 = ws[i] ** 2
+        X = orc.fft_radix2(x, -1)
+        ref = 2 * orc.fft_radix2(w2 * X, +1)
+        got = xt[i].grad.cpu().numpy().astype(np.complex128)
+        assert oracle.rel_l2(got, ref) <= TOL["c64"] * 2 * es[i], (N, oracle.rel_l2(got, ref))
+        # central differences of the FP64 loss, coordinate by coordinate
+        rms = float(np.sqrt(np.mean(np.abs(ref) ** 2)))
+        h = 1e-3
+        for j in (0, 1, N // 2 + 1, N - 1):
+            for unit in (1.0, 1j):
+                xp = x.copy()
+                xm = x.copy()
+                xp[j] += unit * h
+                xm[j] -= unit * h
+                lp = float(np.sum(w2 * np.abs(orc.fft_radix2(xp, -1)) ** 2))
+                lm = float(np.sum(w2 * np.abs(orc.fft_radix2(xm, -1)) ** 2))
+                d = (lp - lm) / (2 * h)
+                want = got[j].real if unit == 1.0 else got[j].imag
+                assert abs(d - want) <= TOL["c64"] * 2 * es[i] * 10 * rms, (N, j, unit, d, want, rms)

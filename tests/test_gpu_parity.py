@@ -191,6 +191,27 @@ def test_parity_2p28_wide_first_pass(orc, name, sign):
     check(got, orc.fft_radix2(x, sign), name, N)
 
 
+@pytest.mark.parametrize("sign", [-1, 1])
+def test_parity_2p28_wide_first_pass_2p11_c128(orc, sign):
+    """complex128 2^28 with the schedule 2^11 * 2^6 * 2^11: the first pass is
+    the wide 2^11-row kernel (8192-element tiles, 4 columns, one 512-thread
+    CTA per SM) at a power-of-two stride, the kernel variant that the 2^33
+    schedule 2^11 * 2^11 * 2^11 runs; element by element against the full
+    oracle."""
+    import paper_1409_5757_gb300 as efft
+    N = 1 << 28
+    x = host_input(orc, "c128", N, seed=2811)
+    t = torch.from_numpy(x).cuda()
+    p = efft.Plan(N, efft.EFFT_C128, sign, radices=[11, 6, 11])
+    assert p.radices() == [11, 6, 11]
+    p.execute(t.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    got = t.cpu().numpy()
+    del t
+    p.destroy()
+    check(got, orc.fft_radix2(x, sign), "c128", N)
+
+
 def test_parity_c64_2p29_middle_pass_2p11(orc):
     """complex64 2^29 with the schedule 2^9 * 2^11 * 2^9: from 2^28 on the
     2^11-row middle pass runs on 8-column tiles (16384 elements, one
