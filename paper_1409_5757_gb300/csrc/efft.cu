@@ -285,6 +285,33 @@ void apply_schedule(efft_plan_s* p, const int* r, int np) {
   p->permute = (np >= 2) && !(p->flags & EFFT_FLAG_DIGIT_REVERSED_OUT);
   p->perm_log2A = (np >= 2) ? r[0] : 0;
   p->perm_B = (np == 3) ? (1u << r[1]) : 1u;
+  // complex128 (a, b, a): the middle pass swaps the outer digits in place
+  // (pairs of T x T column tiles held by the two CTAs of a cluster), so the
+  // array reaches natural order without a separate swap sweep; the last pass
+  // then transforms the columns of the swapped layout, strided like the
+  // first pass, on 8192-element tiles.
+  if (p->permute && np == 3 && p->dtype == EFFT_C128 && e >= kFuseMinLog2N && r[0] >= 9 && r[0] <= 11 &&
+      (r[1] == 8 || r[1] == 10 || r[1] == 11)) {
+    Pass& m = p->pass[1];
+    m.swap = (r[1] == 8) ? 2 : 1;
+    m.log2C = 2 * m.swap;
+    m.wide = false;
+    m.grid = 1ull << (e - r[1] - m.log2C);
+    m.threads = 1 << (r[1] + m.log2C - 4);
+    const size_t me = 1ull << (r[1] + m.log2C);
+    m.smem = (me + me / 16 + 1) * eb;
+    Pass& l = p->pass[2];
+    l.kind = LASTS;
+    l.log2s = e - r[2];
+    l.log2L = e;
+    l.wide = true;
+    l.log2C = kLog2CtaWide - r[2];
+    l.grid = 1ull << (e - kLog2CtaWide);
+    l.threads = 1 << (kLog2CtaWide - 4);
+    const size_t le = 1ull << kLog2CtaWide;
+    l.smem = (le + le / 16 + 1) * eb;
+    p->permute = false;
+  }
 }
 
 template <class P, int KIND, int CTA>
@@ -470,11 +497,20 @@ cudaError_t launch_pass(const efft_plan_s* p, const Pass& ps, void* data, const 
   a.ptrs = bt.ptrs;
   const uint32_t conj = (p->sign > 0) ? 1u : 0u;
   a.conj_in = (ps.kind == FIRST || ps.kind == SINGLE) ? conj : 0u;
-  a.conj_out = (ps.kind == LAST || ps.kind == SINGLE) ? conj : 0u;
-  a.out_shift = ((p->flags & EFFT_FLAG_NORMALIZE) && (ps.kind == LAST || ps.kind == SINGLE)) ? p->log2n : 0;
+  const bool last = (ps.kind == LAST || ps.kind == SINGLE || ps.kind == LASTS);
+  a.conj_out = last ? conj : 0u;
+  a.out_shift = ((p->flags & EFFT_FLAG_NORMALIZE) && last) ? p->log2n : 0;
   a.s_odd = (ps.kind == FIRST && p->odd > 1) ? p->odd : 1u;
   dim3 grid((unsigned)ps.grid, bt.count), block(ps.threads);
   constexpr int LOG2CTA = (P::kElemBytes == 16) ? kLog2CtaC128 : kLog2CtaC64;
+  if (P::kElemBytes == 16 && ps.swap) {
+    const bool ok = fx_launch_df2_swap(ps.log2R, ps.log2C, grid, block, ps.smem, st, data, a);
+    return ok ? cudaGetLastError() : cudaErrorInvalidConfiguration;
+  }
+  if (P::kElemBytes == 16 && ps.kind == LASTS) {
+    const bool ok = fx_launch_df2_lasts(ps.log2R, grid, block, ps.smem, st, data, a);
+    return ok ? cudaGetLastError() : cudaErrorInvalidConfiguration;
+  }
   if (ps.wide) {
     const bool ok = (P::kElemBytes == 16) ? fx_launch_df2_wide(ps.log2R, grid, block, ps.smem, st, data, a)
                                           : fx_launch_f32_wide(ps.kind, ps.log2R, grid, st, data, a);

@@ -44,6 +44,42 @@ void attrs_wide(cudaError_t& err) {
     if (x != cudaSuccess && err == cudaSuccess) err = x;
 }
 
+// Swapping middle passes (clusters of two CTAs): R = 2^11 and 2^10 on 2 x 2
+// column tiles (8192 and 4096 elements), R = 2^8 on 4 x 4 (4096 elements).
+template <int LR, int SWLT, int MINB>
+constexpr auto swap_kernel() {
+  return efft_pass_fx<PolicyDF2, MID, LR, 2 * SWLT, MINB, SWLT>;
+}
+// Strided last passes on 8192-element tiles, one CTA per SM.
+template <int LR>
+constexpr auto lasts_kernel() {
+  return efft_pass_fx<PolicyDF2, LASTS, LR, kLog2CtaWide - LR, 1>;
+}
+
+template <class K>
+void set_smem(K k, int elems, cudaError_t& err) {
+  const cudaError_t x = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)((elems + elems / 16 + 1) * PolicyDF2::kElemBytes));
+  if (x != cudaSuccess && err == cudaSuccess) err = x;
+}
+
+template <class K>
+cudaError_t launch_cluster2(K k, dim3 grid, dim3 block, size_t smem, cudaStream_t st, void* data, const PassArgs& a) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 2;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k, data, a);
+}
+
 }  // namespace
 
 cudaError_t fx_set_attrs_df2() {
@@ -52,7 +88,33 @@ cudaError_t fx_set_attrs_df2() {
   attrs<MID>(err);
   attrs<LAST>(err);
   attrs_wide(err);
+  set_smem(swap_kernel<11, 1, 1>(), 8192, err);
+  set_smem(swap_kernel<10, 1, 2>(), 4096, err);
+  set_smem(swap_kernel<8, 2, 2>(), 4096, err);
+  set_smem(lasts_kernel<9>(), 8192, err);
+  set_smem(lasts_kernel<10>(), 8192, err);
+  set_smem(lasts_kernel<11>(), 8192, err);
   return err;
+}
+
+bool fx_launch_df2_swap(int log2R, int log2C, dim3 grid, dim3 block, size_t smem, cudaStream_t st, void* data,
+                        const PassArgs& a) {
+  cudaError_t e;
+  if (log2R == 11 && log2C == 2) e = launch_cluster2(swap_kernel<11, 1, 1>(), grid, block, smem, st, data, a);
+  else if (log2R == 10 && log2C == 2) e = launch_cluster2(swap_kernel<10, 1, 2>(), grid, block, smem, st, data, a);
+  else if (log2R == 8 && log2C == 4) e = launch_cluster2(swap_kernel<8, 2, 2>(), grid, block, smem, st, data, a);
+  else return false;
+  return e == cudaSuccess;
+}
+
+bool fx_launch_df2_lasts(int log2R, dim3 grid, dim3 block, size_t smem, cudaStream_t st, void* data,
+                         const PassArgs& a) {
+  switch (log2R) {
+    case 9: lasts_kernel<9>()<<<grid, block, smem, st>>>(data, a); return true;
+    case 10: lasts_kernel<10>()<<<grid, block, smem, st>>>(data, a); return true;
+    case 11: lasts_kernel<11>()<<<grid, block, smem, st>>>(data, a); return true;
+    default: return false;
+  }
 }
 
 bool fx_launch_df2_wide(int log2R, dim3 grid, dim3 block, size_t smem, cudaStream_t st, void* data,

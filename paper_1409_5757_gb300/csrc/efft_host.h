@@ -21,11 +21,17 @@ constexpr int kLog2CtaC128 = 12;   // 4096 complex128 elements per CTA (64 KiB)
 constexpr int kLog2CtaC64 = 13;    // 8192 complex64 elements per CTA (64 KiB)
 constexpr int kMaxPasses = 4;
 constexpr int kWideMinLog2N = 28;  // complex128 first passes on 8192-element tiles from 2^28
+// complex128 three-pass schedules (a, b, a) with a in 9..11 and b in {8, 10,
+// 11} fold the digit swap into the middle pass (and run a strided last pass)
+// from this size on
+constexpr int kFuseMinLog2N = 26;
 
 // One pass of the schedule and its launch shape.
 struct Pass {
   int log2R, log2s, log2L, log2C, kind;
   bool wide;  // complex128 first pass on 8192-element tiles
+  int swap;   // middle pass that also swaps the outer digits: log2 of its
+              // T x T column tile side (0: no swap)
   uint64_t grid;
   int threads;
   size_t smem;

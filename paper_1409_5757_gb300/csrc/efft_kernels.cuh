@@ -24,7 +24,10 @@ namespace efft {
 // Pass kinds for complex128 (double-float intermediate kept in the buffer):
 //   FIRST  binary64 in  -> df out      MID  df in -> df out
 //   LAST   df in        -> binary64    SINGLE binary64 in -> binary64 out
-enum PassKind { FIRST = 0, MID = 1, LAST = 2, SINGLE = 3 };
+//   LASTS  df in        -> binary64, the last pass of a three-pass schedule
+//          whose middle pass already swapped the outer digits: its columns
+//          are strided like the first pass's (stride N / R), no twiddle.
+enum PassKind { FIRST = 0, MID = 1, LAST = 2, SINGLE = 3, LASTS = 4 };
 
 struct PassArgs {
   int log2R;        // radix of this pass, 4 <= log2R <= 11
@@ -134,7 +137,7 @@ struct Mem<PolicyDF, KIND> {
   }
   static __device__ __forceinline__ void store(void* base, uint64_t idx, cdf x, int D, uint32_t conj,
                                                bool nonfinite) {
-    if (KIND == LAST || KIND == SINGLE) {
+    if (KIND == LAST || KIND == SINGLE || KIND == LASTS) {
       uint4 o;
       df_to_f64bits(x.re, D, 0u, o.x, o.y);
       df_to_f64bits(x.im, D, conj ? 0x80000000u : 0u, o.z, o.w);
@@ -162,7 +165,7 @@ struct Mem<PolicyDF2, KIND> {
   }
   static __device__ __forceinline__ void store(void* base, uint64_t idx, cdf2 x, int D, uint32_t conj,
                                                bool nonfinite) {
-    if (KIND == LAST || KIND == SINGLE) {
+    if (KIND == LAST || KIND == SINGLE || KIND == LASTS) {
       uint4 o;
       df_to_f64bits(df{x.h.x, x.l.x}, D, 0u, o.x, o.y);
       df_to_f64bits(df{x.h.y, x.l.y}, D, conj ? 0x80000000u : 0u, o.z, o.w);
@@ -184,7 +187,7 @@ struct Mem<PolicyF32, KIND> {
   }
   // D carries the output exponent shift for this policy: x * 2^-D
   static __device__ __forceinline__ void store(void* base, uint64_t idx, float2 x, int D, uint32_t conj, bool) {
-    if (KIND == LAST || KIND == SINGLE) {
+    if (KIND == LAST || KIND == SINGLE || KIND == LASTS) {
       if (conj) x.y = -x.y;
       if (D) {
         const float sc = __uint_as_float((uint32_t)(127 - D) << 23);
@@ -400,9 +403,41 @@ __device__ __forceinline__ void dif_groups(typename P::V* v) {
   for (int g = 0; g < 16; g += (1 << LOG)) dif_regs<P, LOG>(v + g);
 }
 
+// Cluster-wide split barrier (all threads of both CTAs of a pair arrive,
+// then wait): the hardware barrier of a thread-block cluster, whose CTAs are
+// always resident together.
+__device__ __forceinline__ void cluster_arrive() { asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory"); }
+__device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory"); }
+
+// The tile of a swapping middle pass (SWLT > 0).  The array is viewed as
+// (i0, i1, i2) with i0 < A (stride L), i1 < R (stride A), i2 < A; a tile is
+// the T x T block of columns i0 in [I T, I T + T), i2 in [J T, J T + T).  The
+// CTA pair (cluster) z handles tiles (I, J) and (J, I), I < J, for
+// z < nt (nt - 1) / 2 (nt = A / T), and the diagonal tiles (2d, 2d) and
+// (2d + 1, 2d + 1), d = z - nt (nt - 1) / 2, after that.
+__device__ __forceinline__ void swap_tile(uint32_t z, uint32_t rank, uint32_t nt, uint32_t& I, uint32_t& J) {
+  const uint32_t P = nt * (nt - 1) / 2;
+  if (z < P) {
+    uint32_t j = (uint32_t)((1.0f + sqrtf(1.0f + 8.0f * (float)z)) * 0.5f);
+    while (j * (j - 1) / 2 > z) --j;
+    while ((j + 1) * j / 2 <= z) ++j;
+    const uint32_t i = z - j * (j - 1) / 2;
+    I = rank ? j : i;
+    J = rank ? i : j;
+  } else {
+    I = J = 2 * (z - P) + rank;
+  }
+}
+
 // The specialised pass kernel (R = 2^LR rows, C = 2^LC columns per CTA,
 // MINB CTAs per SM); grid.y selects the transform of a batched launch.
-template <class P, int KIND, int LR, int LC, int MINB = 2>
+// SWLT > 0 (middle pass only, C = T^2 with T = 2^SWLT, launched as clusters
+// of two CTAs): the pass also exchanges the outer digits, i.e. the result of
+// column (i0, *, i2) is written to column (i2, *, i0), so that no separate
+// digit-reversal sweep is needed.  The two CTAs of a cluster hold each
+// other's destination tiles; a cluster barrier between their loads and their
+// stores keeps the exchange in place.
+template <class P, int KIND, int LR, int LC, int MINB = 2, int SWLT = 0>
 __global__ void __launch_bounds__(1 << (LR + LC - 4), MINB)
 efft_pass_fx(void* __restrict__ data, const PassArgs a) {
   typedef typename P::V V;
@@ -411,7 +446,10 @@ efft_pass_fx(void* __restrict__ data, const PassArgs a) {
   constexpr int R = 1 << LR, C = 1 << LC, TPC = R >> 4, NT = (R * C) / 16;
   constexpr int NFULL = LR / 4, REM = LR % 4, NST = NFULL + (REM ? 1 : 0);
   constexpr int NMID = NST - 2;  // radix-16 stages between the first and the last
-  constexpr bool STRIDED = (KIND == FIRST || KIND == MID);
+  constexpr bool SWAP = SWLT > 0;
+  static_assert(!SWAP || (KIND == MID && LC == 2 * SWLT), "a swapping pass is a middle pass of T x T columns");
+  constexpr bool STRIDED = (KIND == FIRST || KIND == MID || KIND == LASTS);
+  constexpr bool TWID = (KIND == FIRST || KIND == MID);  // the pass twiddle of Eq. 4
   // Thread mapping: c runs fastest (a warp covers C columns x 32/C rows) and
   // shared memory is row-major, raw index p*C + c.  The last pass reads C
   // whole contiguous blocks: when a warp's run per column, 32/C elements,
@@ -424,7 +462,7 @@ efft_pass_fx(void* __restrict__ data, const PassArgs a) {
   static_assert(LR >= 5 && LR <= 12, "radix range");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V* sm = reinterpret_cast<V*>(smem_raw);
-  __shared__ typename P::TW vtw[STRIDED ? 16 * C : 1];
+  __shared__ typename P::TW vtw[TWID ? 16 * C : 1];
   // column-major last pass: lanes hold different t, so the stage-0 twiddles
   // exp(-2*pi*i*t*q/R) come from a shared copy of the R-th roots of unity
   // (root k at k + k/8: lanes reading k = 8t or 4t stay on different banks)
@@ -438,10 +476,20 @@ efft_pass_fx(void* __restrict__ data, const PassArgs a) {
   const int c = CM ? (tid >> (LR - 4)) : (tid & (C - 1));
   const int t = CM ? (tid & (TPC - 1)) : (tid >> LC);
   const uint64_t jcol = (uint64_t)blockIdx.x * C + c;
-  uint64_t m = 0, colbase, step;
-  if (KIND == FIRST) {
-    // the first pass spans the whole array (L = N): column j starts at j
-    step = (uint64_t)a.s_odd << a.log2s;
+  uint64_t m = 0, colbase, step, outbase = 0;
+  uint32_t tI = 0, tJ = 0;  // swapping pass: this CTA's tile
+  if (SWAP) {
+    constexpr int T = 1 << SWLT;
+    swap_tile(blockIdx.x >> 1, blockIdx.x & 1, 1u << (a.log2s - SWLT), tI, tJ);
+    const uint64_t i0 = (uint64_t)tI * T + (c >> SWLT), i2 = (uint64_t)tJ * T + (c & (T - 1));
+    step = 1ull << a.log2s;
+    m = i2;
+    colbase = (i0 << a.log2L) + i2;
+    outbase = (i2 << a.log2L) + i0;
+  } else if (KIND == FIRST || KIND == LASTS) {
+    // the first pass spans the whole array (L = N): column j starts at j;
+    // so does the strided last pass (the columns of the swapped layout)
+    step = (KIND == FIRST ? (uint64_t)a.s_odd : 1ull) << a.log2s;
     m = jcol;
     colbase = jcol;
   } else if (STRIDED) {
@@ -464,12 +512,13 @@ efft_pass_fx(void* __restrict__ data, const PassArgs a) {
 
   const int kt = digit_rev_c(t << 4, LR);
   typename P::TW wt;
-  if (STRIDED) {
+  if (TWID) {
     const int sh = (KIND == FIRST) ? 0 : a.log2N - a.log2L;
     // V_c[u] stored as [u][c]: the columns of one warp read consecutive entries
     if (tid < 16 * C) {
       const int cc = tid >> 4, u = tid & 15;
-      const uint64_t mc = ((uint64_t)blockIdx.x * C + cc) & (KIND == FIRST ? ~0ull : step - 1);
+      const uint64_t mc = SWAP ? (uint64_t)tJ * (1u << SWLT) + (cc & ((1 << SWLT) - 1))
+                               : ((uint64_t)blockIdx.x * C + cc) & (KIND == FIRST ? ~0ull : step - 1);
       const int kc = digit_rev_c(last_pos_c(u, REM), LR);
       vtw[u * C + cc] = P::expand(twiddle_N(a, (mc * (uint64_t)kc) << sh));
     }
@@ -488,6 +537,8 @@ efft_pass_fx(void* __restrict__ data, const PassArgs a) {
     __syncthreads();
   }
   dif_regs<P, 4>(v);
+  // the stage-0 loads are consumed: the partner CTA may overwrite this tile
+  if (SWAP) cluster_arrive();
   {
     // exp(-2*pi*i * t*q / R), q = bitrev4(u), to positions t + TPC*q
 #pragma unroll
@@ -530,11 +581,15 @@ efft_pass_fx(void* __restrict__ data, const PassArgs a) {
   }
 
   if (STRIDED && (KIND != FIRST || a.s_odd == 1)) {
+    // swapping pass: the partner CTA has consumed its loads of this CTA's
+    // destination tile
+    if (SWAP) cluster_wait();
+    const uint64_t ob = SWAP ? outbase : colbase;
 #pragma unroll
     for (int u = 0; u < 16; ++u) {
       const int k = kt | digit_rev_c(last_pos_c(u, REM), LR);
-      v[u] = P::pass_tw(v[u], wt, vtw[u * C + c]);
-      Mem<P, KIND>::store(data, colbase + ((uint64_t)k << a.log2s), v[u], Dout, a.conj_out, nonfinite);
+      if (TWID) v[u] = P::pass_tw(v[u], wt, vtw[u * C + c]);
+      Mem<P, KIND>::store(data, ob + ((uint64_t)k << a.log2s), v[u], Dout, a.conj_out, nonfinite);
     }
   } else if (STRIDED) {
     // first pass of N = M * 2^e: output k at k * M * 2^log2s
@@ -644,6 +699,14 @@ bool fx_launch_df2(int kind, int log2R, dim3 grid, dim3 block, size_t smem, cuda
 constexpr int kLog2CtaWide = 13;
 bool fx_launch_df2_wide(int log2R, dim3 grid, dim3 block, size_t smem, cudaStream_t st, void* data,
                         const PassArgs& a);
+// complex128 passes of a three-pass schedule whose middle pass swaps the
+// outer digits (clusters of two CTAs) and whose last pass is strided:
+// the middle pass of R = 2^log2R rows on T x T column tiles and the last
+// pass of R = 2^9..2^11 rows on 8192-element tiles (one CTA per SM).
+bool fx_launch_df2_swap(int log2R, int log2C, dim3 grid, dim3 block, size_t smem, cudaStream_t st, void* data,
+                        const PassArgs& a);
+bool fx_launch_df2_lasts(int log2R, dim3 grid, dim3 block, size_t smem, cudaStream_t st, void* data,
+                         const PassArgs& a);
 cudaError_t fx_set_attrs_f32();
 bool fx_launch_f32(int kind, int log2R, dim3 grid, dim3 block, size_t smem, cudaStream_t st, void* data,
                    const PassArgs& a);

@@ -119,20 +119,23 @@ def test_config_c2_2p30_elementwise_full_oracle(orc):
     del xin
     scale = float(np.max(np.abs(ref)))
     num = den = 0.0
-    worst = 0.0
     chunk = 1 << 26
     for c in range(N // chunk):
-        got = x[c * chunk:(c + 1) * chunk].cpu().numpy()
-        r = ref[c * chunk:(c + 1) * chunk]
-        d = np.abs(got - r) / scale
-        num += float(np.sum(d * d))
-        den += float(np.sum(np.abs(r / scale) ** 2))
-        worst = max(worst, float(np.max(d)))
+        r = ref[c * chunk:(c + 1) * chunk] / scale
+        num += float(np.sum(np.abs(x[c * chunk:(c + 1) * chunk].cpu().numpy() / scale - r) ** 2))
+        den += float(np.sum(np.abs(r) ** 2))
     err = math.sqrt(num / den)
     lim = 1e-14 * e
     assert err <= lim, err
+    # no outlier: every bin within 50 times the tolerance of the larger of its
+    # own magnitude (the 64 tone bins are 10^4 times the others) and the RMS
     rms = math.sqrt(den / N)
-    assert worst <= 50 * lim * max(rms, 1e-300), (worst, rms)
+    worst = 0.0
+    for c in range(N // chunk):
+        r = ref[c * chunk:(c + 1) * chunk] / scale
+        d = np.abs(x[c * chunk:(c + 1) * chunk].cpu().numpy() / scale - r)
+        worst = max(worst, float(np.max(d / np.maximum(np.abs(r), rms))))
+    assert worst <= 50 * lim, worst
     del x, ref
     _free()
 

@@ -305,3 +305,67 @@ def test_c128_tiles_of_different_scales(orc, e, pattern):
     x = orc.gen_uniform(60 + e, N) * np.ldexp(1.0, shift)
     got = gpu_fft(x, "c128", -1)
     check(got, orc.dft(x, -1), "c128", N, pattern)
+
+
+@pytest.mark.parametrize("radices,sign,flags", [
+    ([9, 8, 9], -1, 0), ([9, 8, 9], 1, 2), ([9, 10, 9], -1, 0), ([10, 8, 10], 1, 0), ([9, 8, 9], -1, 1)],
+    ids=["9-8-9", "9-8-9-inv-norm", "9-10-9", "10-8-10-inv", "9-8-9-digit-reversed"])
+def test_parity_fused_digit_swap(orc, radices, sign, flags):
+    """complex128 three-pass schedules (a, b, a) with a in 9..11 and b in
+    {8, 10, 11} from 2^26 on: the middle pass swaps the outer digits itself
+    (pairs of column tiles on the two CTAs of a cluster) and the last pass is
+    strided, so no digit-swap sweep runs (efft_plan_info counts 3.5 sweeps).
+    Element by element against the full oracle; with
+    EFFT_FLAG_DIGIT_REVERSED_OUT the unfused passes run and the output is the
+    digit-reversed order of the oracle's."""
+    import paper_1409_5757_gb300 as efft
+    e = sum(radices)
+    N = 1 << e
+    x = host_input(orc, "c128", N, seed=4000 + e + radices[0])
+    t = torch.from_numpy(x).cuda()
+    p = efft.Plan(N, efft.EFFT_C128, sign, flags, radices=radices)
+    fused = not (flags & efft.EFFT_FLAG_DIGIT_REVERSED_OUT)
+    # 3 passes + the half sweep of the range scan (an unfused natural-order
+    # plan would add the swap sweep: 4.5)
+    assert p.info()["hbm_passes"] == 3.5
+    p.execute(t.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    got = t.cpu().numpy()
+    del t
+    p.destroy()
+    ref = orc.fft_radix2(x, sign)
+    if flags & efft.EFFT_FLAG_NORMALIZE:
+        ref = ref / N
+    if not fused:
+        a, b = radices[0], radices[1]
+        P = np.arange(N, dtype=np.int64)
+        q0, q1, q2 = P >> (a + b), (P >> a) & ((1 << b) - 1), P & ((1 << a) - 1)
+        ref = ref[q0 + (q1 << a) + (q2 << (a + b))]
+    check(got, ref, "c128", N)
+
+
+def test_fused_digit_swap_in_a_batch_is_bit_identical():
+    """Two 2^28 transforms (default schedule 10 * 8 * 10, fused swap) in one
+    batch launch (grid.y selects the transform, clusters along x) equal
+    single-plan executes bit for bit."""
+    import paper_1409_5757_gb300 as efft
+    from paper_1409_5757_gb300 import inputs
+    N = 1 << 28
+    p = efft.Plan(N, efft.EFFT_C128, -1)
+    assert p.radices() == [10, 8, 10] and p.info()["hbm_passes"] == 3.5
+    xs = [torch.empty(N, dtype=torch.complex128, device="cuda") for _ in range(2)]
+    for i, x in enumerate(xs):
+        inputs.fill_uniform(x, seed=60 + i)
+    want = []
+    for x in xs:
+        y = x.clone()
+        p.execute(y.data_ptr(), torch.cuda.current_stream().cuda_stream)
+        want.append(y)
+    b = efft.Batch([N, N], efft.EFFT_C128, -1)
+    b.execute([x.data_ptr() for x in xs], torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    for x, w in zip(xs, want):
+        assert torch.equal(x, w)
+    b.destroy()
+    p.destroy()
+    del want, xs
