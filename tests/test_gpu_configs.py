@@ -127,15 +127,20 @@ def test_config_c2_2p30_elementwise_full_oracle(orc):
     err = math.sqrt(num / den)
     lim = 1e-14 * e
     assert err <= lim, err
-    # no outlier: every bin within 50 times the tolerance of the larger of its
-    # own magnitude (the 64 tone bins are 10^4 times the others) and the RMS
-    rms = math.sqrt(den / N)
+    # no outlier: the largest error of any bin within the tolerance relative
+    # to the largest bin (the L-infinity form of Eq. 9; the 64 tone bins are
+    # 10^4 times the others, and rounding leaks about eps times their
+    # magnitude into every bin), and each tone bin within the tolerance of
+    # its own value
     worst = 0.0
     for c in range(N // chunk):
         r = ref[c * chunk:(c + 1) * chunk] / scale
-        d = np.abs(x[c * chunk:(c + 1) * chunk].cpu().numpy() / scale - r)
-        worst = max(worst, float(np.max(d / np.maximum(np.abs(r), rms))))
-    assert worst <= 50 * lim, worst
+        worst = max(worst, float(np.max(np.abs(x[c * chunk:(c + 1) * chunk].cpu().numpy() / scale - r))))
+    assert worst <= lim, worst
+    ft = torch.from_numpy(f.astype(np.int64)).cuda()
+    gt = x[ft].cpu().numpy()
+    rt = ref[f.astype(np.int64)]
+    assert np.max(np.abs(gt - rt) / np.abs(rt)) <= lim
     del x, ref
     _free()
 
