@@ -207,16 +207,28 @@ int efft_plan_create_with_radices(efft_plan_t* out, uint64_t n, int dtype, int s
                                   const int* log2_radices, int npasses);
 
 /*
- * Time every accepted schedule (above) for the plan's n and switch the plan
- * to the fastest; the choice is cached for (device, n, dtype) and used by
- * later plans created with EFFT_FLAG_AUTOTUNE.  Each candidate is run on
- * `scratch` (n*S bytes of the caller's device memory on the plan's device;
- * its contents are overwritten) on `stream`, twice untimed and then a few
- * times between CUDA events; its time is the median.  Synchronous.  No
- * execute of the plan may be in flight, and the plan must not be used by
- * another host thread meanwhile.
+ * Measure the plan's schedules and kernel variants and switch the plan to
+ * the fastest (the GPU counterpart of the paper's scan over the split depth s
+ * and the worker count, Sec. 5.2, Figs. 6-7); the choice is cached for
+ * (device, n, dtype) and used by later plans created with
+ * EFFT_FLAG_AUTOTUNE.  Candidates, in order:
+ *  - n a power of two: every accepted schedule (above) with the built-in
+ *    variant rules; then, for the fastest schedule, each kernel variant
+ *    switched the other way where it changes the passes (kept when faster):
+ *    the tile width of the strided first pass (complex64: also of the 2^11
+ *    middle pass) doubled or not, the digit swap folded into the middle pass
+ *    or not, the persistent prefetching pass kernels or not (the last two
+ *    complex128 only);
+ *  - n = M * 2^e, M > 1: every outer radix 2^a of the (2^a, M * 2^b, 2^a)
+ *    schedule that efft_plan_create accepts, and one pass when n <= 2048.
+ * Each candidate is run on `scratch` (n*S bytes of the caller's device
+ * memory on the plan's device; its contents are overwritten) on `stream`,
+ * twice untimed and then a few times between CUDA events; its time is the
+ * median.  Synchronous.  No execute of the plan may be in flight, and the
+ * plan must not be used by another host thread meanwhile.
  *  cand_log2r  [out, may be NULL] room for cap*4 ints: candidate c's
- *              log2 radices at [4c, 4c+4), unused entries 0.
+ *              log2 radices at [4c, 4c+4), unused entries 0 (for M > 1 the
+ *              power-of-two part of each radix).
  *  cand_ms     [out, may be NULL] room for cap doubles: candidate c's time.
  *  ncand       [out, may be NULL] number of candidates (may exceed cap).
  * For n <= 8 there is nothing to tune (*ncand = 1, the direct-sum kernel).
@@ -224,6 +236,38 @@ int efft_plan_create_with_radices(efft_plan_t* out, uint64_t n, int dtype, int s
  */
 int efft_plan_autotune(efft_plan_t plan, void* scratch, void* stream, int* cand_log2r, double* cand_ms,
                        int cap, int* ncand);
+
+/* One candidate measured by efft_plan_autotune_candidates. */
+typedef struct efft_candidate {
+  int npasses;          /* p (0: the direct-sum kernel)                         */
+  uint64_t radices[4];  /* R_0 .. R_{p-1} (whole: M included for N = M * 2^e)   */
+  int wide;             /* 1: the wide strided tiles (see efft_plan_autotune)   */
+  int fused_swap;       /* 1: digit swap folded into the middle pass            */
+  int persistent;       /* 1: persistent prefetching pass kernels               */
+  double ms;            /* median time of one execute (milliseconds)            */
+} efft_candidate;
+
+/* efft_plan_autotune with the full record of every candidate:
+ *  out    [out, may be NULL] room for cap records, in measuring order.
+ *  ncand  [out, may be NULL] number of candidates (may exceed cap).
+ * The plan ends on the fastest; efft_plan_autotune's other rules apply.
+ * Errors: as efft_plan_autotune. */
+int efft_plan_autotune_candidates(efft_plan_t plan, void* scratch, void* stream, efft_candidate* out, int cap,
+                                  int* ncand);
+
+/* The kernel variant a plan runs (each 0 or 1; see efft_candidate).  Any
+ * pointer may be NULL.  Errors: INVALID_PLAN. */
+int efft_plan_variant(efft_plan_t plan, int* wide, int* fused_swap, int* persistent);
+
+/* Switch a plan's kernel variant, keeping its schedule (e.g. to pin a choice
+ * an earlier efft_plan_autotune_candidates measured).  Each knob: -1 the
+ * built-in rule (by size), 0 off, 1 on wherever the pass shapes allow it
+ * (efft_plan_variant reports what took effect).  Results are unchanged up to
+ * rounding.  No execute of the plan may be in flight.
+ * A real-data plan switches its complex plan.
+ * Errors: INVALID_PLAN; INVALID_FLAGS for a knob outside -1..1;
+ * UNSUPPORTED for a plan of N = M * 2^e (M > 1) with a knob other than -1. */
+int efft_plan_set_variant(efft_plan_t plan, int wide, int fused_swap, int persistent);
 
 /* Destroy a plan and free its device tables, after waiting for the
  * executes still using its state words.  The paper's ~EFFT_Transform()

@@ -7,6 +7,7 @@
 // word; an execute enqueues the pass kernels on the caller's stream.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 #include <cstdlib>
 #include <cstring>
@@ -121,13 +122,38 @@ bool valid_size(uint64_t n) {
 // passes (A, B, A) with A = 2^a and B = M * 2^(e - 2a) (palindromic, so the
 // digit reversal is still the swap of the outer digits), choosing a to make
 // the larger of A and B smallest.
-int apply_mixed_schedule(efft_plan_s* p) {
+// Whether (2^a, M * 2^b, 2^a) (a >= 1), or one pass (a = 0), is a schedule
+// the mixed-radix kernels run for p.
+static bool mixed_ok(const efft_plan_s* p, int a) {
+  const uint64_t n = p->n;
+  const int tile = (p->dtype == EFFT_C128) ? kMixTileC128 : kMixTileC64;
+  const int e = __builtin_ctzll(n);
+  if (a == 0) return n <= (uint64_t)tile;
+  if (2 * a > e) return false;
+  const uint64_t A = 1ull << a, B = n / (A * A);
+  return A <= (uint64_t)tile && B <= (uint64_t)tile;
+}
+
+int mixed_candidates(const efft_plan_s* p, int* a, int cap) {
+  int k = 0;
+  for (int c = 0; 2 * c <= __builtin_ctzll(p->n); ++c)
+    if (mixed_ok(p, c)) {
+      if (k < cap) a[k] = c;
+      ++k;
+    }
+  return k;
+}
+
+int apply_mixed_schedule(efft_plan_s* p, int force_a) {
   const uint64_t n = p->n;
   const int tile = (p->dtype == EFFT_C128) ? kMixTileC128 : kMixTileC64;
   const size_t eb = (p->dtype == EFFT_C128) ? 16 : 8;
   const int e = __builtin_ctzll(n);
   int np = 1, a = 0;
-  if (n > (uint64_t)tile) {
+  if (force_a >= 0 && mixed_ok(p, force_a)) {
+    a = force_a;
+    np = (a == 0) ? 1 : 3;
+  } else if (n > (uint64_t)tile) {
     // the largest A whose middle radix B = M * 2^b keeps b >= 4 (the
     // compile-time middle-pass kernel): the power-of-two outer passes are
     // the efficient ones; failing that, the A minimising the larger radix.
@@ -248,13 +274,18 @@ bool valid_schedule(int e, const int* r, int np) {
 }
 
 // Fills the pass table of p (log2n, dtype and flags already set) for the
-// radix list r[0..np).
-void apply_schedule(efft_plan_s* p, const int* r, int np) {
+// radix list r[0..np) and the kernel variant v (-1 knobs: the size rules).
+void apply_schedule(efft_plan_s* p, const int* r, int np, const Variant& v) {
   const int e = p->log2n;
+  const bool c128 = (p->dtype == EFFT_C128);
+  auto on = [](int knob, bool rule) { return knob < 0 ? rule : knob != 0; };
+  const bool wide_on = on(v.wide, e >= kWideMinLog2N) && e >= (c128 ? kLog2CtaWide : kLog2CtaWideC64);
+  const bool fuse_on = on(v.fuse, e >= kFuseMinLog2N && e <= kFuseMaxLog2N);
+  const int pf = v.pf;  // -1: per-pass rules below
   p->npasses = np;
   p->small = (e >= 1 && e <= 3);
-  const int log2cta = (p->dtype == EFFT_C128) ? kLog2CtaC128 : kLog2CtaC64;
-  const size_t eb = (p->dtype == EFFT_C128) ? 16 : 8;
+  const int log2cta = c128 ? kLog2CtaC128 : kLog2CtaC64;
+  const size_t eb = c128 ? 16 : 8;
   int rest = e;
   for (int j = 0; j < kMaxPasses; ++j) p->pass[j] = Pass();
   for (int j = 0; j < np; ++j) {
@@ -271,10 +302,9 @@ void apply_schedule(efft_plan_s* p, const int* r, int np) {
     // apart, each in its own page; wider tiles move twice the bytes per row
     // (complex64: 16384-element tiles, the first pass of 2^10 rows on the
     // radix-32 kernel and the middle pass of 2^11 rows)
-    ps.wide = e >= kWideMinLog2N && (p->dtype == EFFT_C128
-                                         ? ps.kind == FIRST && (r[j] == 10 || r[j] == 11)
-                                         : (ps.kind == FIRST && r[j] == 10) || (ps.kind == MID && r[j] == 11));
-    int log2C = (ps.wide ? (p->dtype == EFFT_C128 ? kLog2CtaWide : kLog2CtaWideC64) : log2cta) - r[j];
+    ps.wide = wide_on && (c128 ? ps.kind == FIRST && (r[j] == 10 || r[j] == 11)
+                               : (ps.kind == FIRST && r[j] == 10) || (ps.kind == MID && r[j] == 11));
+    int log2C = (ps.wide ? (c128 ? kLog2CtaWide : kLog2CtaWideC64) : log2cta) - r[j];
     if (log2C > e - r[j]) log2C = e - r[j];
     ps.log2C = log2C;
     ps.grid = 1ull << (e - r[j] - log2C);
@@ -290,7 +320,7 @@ void apply_schedule(efft_plan_s* p, const int* r, int np) {
   // array reaches natural order without a separate swap sweep; the last pass
   // then transforms the columns of the swapped layout, strided like the
   // first pass, on 8192-element tiles.
-  if (p->permute && np == 3 && p->dtype == EFFT_C128 && e >= kFuseMinLog2N && r[0] >= 9 && r[0] <= 11 &&
+  if (fuse_on && p->permute && np == 3 && c128 && r[0] >= 9 && r[0] <= 11 &&
       (r[1] == 8 || r[1] == 10 || r[1] == 11)) {
     Pass& m = p->pass[1];
     m.swap = (r[1] == 8) ? 2 : 1;
@@ -304,7 +334,7 @@ void apply_schedule(efft_plan_s* p, const int* r, int np) {
     l.kind = LASTS;
     l.log2s = e - r[2];
     l.log2L = e;
-    l.wide = true;
+    l.wide = false;  // always on 8192-element tiles (not a variant of its own)
     l.log2C = kLog2CtaWide - r[2];
     l.grid = 1ull << (e - kLog2CtaWide);
     l.threads = 1 << (kLog2CtaWide - 4);
@@ -312,6 +342,42 @@ void apply_schedule(efft_plan_s* p, const int* r, int np) {
     l.smem = (le + le / 16 + 1) * eb;
     p->permute = false;
   }
+  // persistent prefetching kernels for the complex128 strided passes with a
+  // tile shape they are built for.  The rule (measured, 2^28..2^33): they
+  // pay for the one-CTA-per-SM passes -- the strided last pass at every
+  // size, the wide first pass up to 2^31 (beyond, its burst of copies meets
+  // address-translation misses) -- and not for the two-CTA-per-SM middle
+  // passes or the swapping ones.
+  if (c128 && pf != 0 && e >= kPersistMinLog2N) {
+    for (int j = 0; j < np; ++j) {
+      Pass& ps = p->pass[j];
+      const int lr = ps.log2R, lc = ps.log2C;
+      bool shape = false, rule = false;
+      if (ps.swap) {
+        shape = (lr == 11 && lc == 2) || (lr == 10 && lc == 2) || (lr == 8 && lc == 4);
+      } else if (ps.kind == FIRST) {
+        shape = ps.wide && ((lr == 10 && lc == 3) || (lr == 11 && lc == 2));
+        rule = e <= kPersistFirstMaxLog2N;
+      } else if (ps.kind == MID) {
+        shape = (lr >= 8 && lr <= 11 && lr + lc == kLog2CtaC128);
+      } else if (ps.kind == LASTS) {
+        shape = (lr >= 9 && lr <= 11 && lr + lc == kLog2CtaWide);
+        rule = true;
+      }
+      ps.pf = shape && (pf > 0 || rule);
+    }
+  }
+}
+
+Variant realised_variant(const efft_plan_s* p) {
+  Variant v;
+  v.wide = v.fuse = v.pf = 0;
+  for (int j = 0; j < p->npasses; ++j) {
+    if (p->pass[j].wide) v.wide = 1;
+    if (p->pass[j].swap) v.fuse = 1;
+    if (p->pass[j].pf) v.pf = 1;
+  }
+  return v;
 }
 
 template <class P, int KIND, int CTA>
@@ -503,6 +569,17 @@ cudaError_t launch_pass(const efft_plan_s* p, const Pass& ps, void* data, const 
   a.s_odd = (ps.kind == FIRST && p->odd > 1) ? p->odd : 1u;
   dim3 grid((unsigned)ps.grid, bt.count), block(ps.threads);
   constexpr int LOG2CTA = (P::kElemBytes == 16) ? kLog2CtaC128 : kLog2CtaC64;
+  if (P::kElemBytes == 16 && ps.pf) {
+    // persistent: at most as many CTAs (CTA pairs) as can be resident
+    const int minb = (ps.log2R + ps.log2C == kLog2CtaWide) ? 1 : 2;
+    const uint64_t cap = (uint64_t)(p->sms > 0 ? p->sms : 152) * minb;
+    const uint64_t ntiles = ps.swap ? ps.grid / 2 : ps.grid;
+    const uint64_t g = ps.swap ? 2 * std::min<uint64_t>(ntiles, cap / 2) : std::min<uint64_t>(ntiles, cap);
+    a.ntiles = ntiles;
+    const bool ok = fx_launch_df2_pf(ps.kind, ps.log2R, ps.log2C, ps.swap, dim3((unsigned)g, bt.count), block,
+                                     ps.smem, st, data, a);
+    return ok ? cudaGetLastError() : cudaErrorInvalidConfiguration;
+  }
   if (P::kElemBytes == 16 && ps.swap) {
     const bool ok = fx_launch_df2_swap(ps.log2R, ps.log2C, grid, block, ps.smem, st, data, a);
     return ok ? cudaGetLastError() : cudaErrorInvalidConfiguration;
@@ -584,30 +661,34 @@ int plan_create_impl(efft_plan_t* out, uint64_t n, int dtype, int sign, uint32_t
   p->dtype = dtype;
   p->sign = sign;
   p->flags = flags;
+  if (cudaDeviceGetAttribute(&p->sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    p->sms = 0;
+  }
 
   const int e = p->log2n;  // ceil(log2 N)
   const size_t eb = (dtype == EFFT_C128) ? 16 : 8;
   p->odd = (uint32_t)(n / (n & (~n + 1)));
   bool tune = false;
+  Tuned t;
+  const bool cached = (flags & EFFT_FLAG_AUTOTUNE) && !r_explicit && tuned_lookup(dev, n, dtype, &t);
   if (p->odd > 1) {
-    // N = M * 2^e: the mixed-radix schedule (neither tuned nor cached)
-    const int rc0 = apply_mixed_schedule(p);
+    // N = M * 2^e: the mixed-radix schedule (the tuned outer radix if cached)
+    const int rc0 = apply_mixed_schedule(p, cached ? t.mixed_a : -1);
     if (rc0 != EFFT_OK) {
       delete p;
       return rc0;
     }
+    tune = (flags & EFFT_FLAG_AUTOTUNE) && !cached && n > 2048 && n * eb <= EFFT_AUTOTUNE_MAX_BYTES;
   } else if (r_explicit) {
     apply_schedule(p, r_explicit, np_explicit);
+  } else if (cached) {
+    apply_schedule(p, t.r, t.np, t.v);
   } else {
-    Tuned t;
-    if ((flags & EFFT_FLAG_AUTOTUNE) && tuned_lookup(dev, e, dtype, &t)) {
-      apply_schedule(p, t.r, t.np);
-    } else {
-      int r[kMaxPasses] = {0, 0, 0, 0};
-      const int np = choose_radices(e, r);
-      apply_schedule(p, r, np);
-      tune = (flags & EFFT_FLAG_AUTOTUNE) && e >= 4 && n * eb <= EFFT_AUTOTUNE_MAX_BYTES;
-    }
+    int r[kMaxPasses] = {0, 0, 0, 0};
+    const int np = choose_radices(e, r);
+    apply_schedule(p, r, np);
+    tune = (flags & EFFT_FLAG_AUTOTUNE) && e >= 4 && n * eb <= EFFT_AUTOTUNE_MAX_BYTES;
   }
   p->twB = (e + 1) / 2;
 
@@ -636,7 +717,7 @@ int plan_create_impl(efft_plan_t* out, uint64_t n, int dtype, int sign, uint32_t
     // a temporary buffer; without room the table's schedule stays
     void* scratch = nullptr;
     if (cudaMalloc(&scratch, n * eb) == cudaSuccess) {
-      rc = autotune_impl(p, scratch, st, nullptr, nullptr, 0, nullptr);
+      rc = autotune_impl(p, scratch, st, nullptr, 0, nullptr);
       cudaFree(scratch);
     } else {
       cudaGetLastError();

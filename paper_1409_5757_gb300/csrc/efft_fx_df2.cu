@@ -80,7 +80,61 @@ cudaError_t launch_cluster2(K k, dim3 grid, dim3 block, size_t smem, cudaStream_
   return cudaLaunchKernelEx(&cfg, k, data, a);
 }
 
+// Persistent prefetching passes: 8192-element tiles (one CTA per SM) for
+// the wide first pass, the strided last pass and the 2^11 swapping middle
+// pass; 4096-element tiles (two CTAs per SM) for the other middle passes.
+template <int KIND, int LR, int LC, int MINB, int SWLT = 0>
+constexpr auto pf_kernel() {
+  return efft_pass_pf<KIND, LR, LC, MINB, SWLT>;
+}
+
+template <class K>
+cudaError_t launch_plain(K k, dim3 grid, dim3 block, size_t smem, cudaStream_t st, void* data, const PassArgs& a) {
+  k<<<grid, block, smem, st>>>(data, a);
+  return cudaGetLastError();
+}
+
 }  // namespace
+
+cudaError_t fx_set_attrs_df2_pf() {
+  cudaError_t err = cudaSuccess;
+  set_smem(pf_kernel<FIRST, 10, 3, 1>(), 8192, err);
+  set_smem(pf_kernel<FIRST, 11, 2, 1>(), 8192, err);
+  set_smem(pf_kernel<MID, 8, 4, 2>(), 4096, err);
+  set_smem(pf_kernel<MID, 9, 3, 2>(), 4096, err);
+  set_smem(pf_kernel<MID, 10, 2, 2>(), 4096, err);
+  set_smem(pf_kernel<MID, 11, 1, 2>(), 4096, err);
+  set_smem(pf_kernel<MID, 11, 2, 1, 1>(), 8192, err);
+  set_smem(pf_kernel<MID, 10, 2, 2, 1>(), 4096, err);
+  set_smem(pf_kernel<MID, 8, 4, 2, 2>(), 4096, err);
+  set_smem(pf_kernel<LASTS, 9, 4, 1>(), 8192, err);
+  set_smem(pf_kernel<LASTS, 10, 3, 1>(), 8192, err);
+  set_smem(pf_kernel<LASTS, 11, 2, 1>(), 8192, err);
+  return err;
+}
+
+bool fx_launch_df2_pf(int kind, int log2R, int log2C, int swap, dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                      void* data, const PassArgs& a) {
+  cudaError_t e = cudaErrorInvalidConfiguration;
+  if (swap) {
+    if (log2R == 11 && log2C == 2) e = launch_cluster2(pf_kernel<MID, 11, 2, 1, 1>(), grid, block, smem, st, data, a);
+    else if (log2R == 10 && log2C == 2) e = launch_cluster2(pf_kernel<MID, 10, 2, 2, 1>(), grid, block, smem, st, data, a);
+    else if (log2R == 8 && log2C == 4) e = launch_cluster2(pf_kernel<MID, 8, 4, 2, 2>(), grid, block, smem, st, data, a);
+  } else if (kind == FIRST) {
+    if (log2R == 10 && log2C == 3) e = launch_plain(pf_kernel<FIRST, 10, 3, 1>(), grid, block, smem, st, data, a);
+    else if (log2R == 11 && log2C == 2) e = launch_plain(pf_kernel<FIRST, 11, 2, 1>(), grid, block, smem, st, data, a);
+  } else if (kind == MID) {
+    if (log2R == 8 && log2C == 4) e = launch_plain(pf_kernel<MID, 8, 4, 2>(), grid, block, smem, st, data, a);
+    else if (log2R == 9 && log2C == 3) e = launch_plain(pf_kernel<MID, 9, 3, 2>(), grid, block, smem, st, data, a);
+    else if (log2R == 10 && log2C == 2) e = launch_plain(pf_kernel<MID, 10, 2, 2>(), grid, block, smem, st, data, a);
+    else if (log2R == 11 && log2C == 1) e = launch_plain(pf_kernel<MID, 11, 1, 2>(), grid, block, smem, st, data, a);
+  } else if (kind == LASTS) {
+    if (log2R == 9 && log2C == 4) e = launch_plain(pf_kernel<LASTS, 9, 4, 1>(), grid, block, smem, st, data, a);
+    else if (log2R == 10 && log2C == 3) e = launch_plain(pf_kernel<LASTS, 10, 3, 1>(), grid, block, smem, st, data, a);
+    else if (log2R == 11 && log2C == 2) e = launch_plain(pf_kernel<LASTS, 11, 2, 1>(), grid, block, smem, st, data, a);
+  }
+  return e == cudaSuccess;
+}
 
 cudaError_t fx_set_attrs_df2() {
   cudaError_t err = cudaSuccess;
@@ -94,6 +148,8 @@ cudaError_t fx_set_attrs_df2() {
   set_smem(lasts_kernel<9>(), 8192, err);
   set_smem(lasts_kernel<10>(), 8192, err);
   set_smem(lasts_kernel<11>(), 8192, err);
+  const cudaError_t e2 = fx_set_attrs_df2_pf();
+  if (e2 != cudaSuccess && err == cudaSuccess) err = e2;
   return err;
 }
 

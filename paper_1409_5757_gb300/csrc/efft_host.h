@@ -23,8 +23,16 @@ constexpr int kMaxPasses = 4;
 constexpr int kWideMinLog2N = 28;  // complex128 first passes on 8192-element tiles from 2^28
 // complex128 three-pass schedules (a, b, a) with a in 9..11 and b in {8, 10,
 // 11} fold the digit swap into the middle pass (and run a strided last pass)
-// from this size on
+// for 2^26 <= N <= 2^30; measured: 2^28 10.09 vs 11.07 ms, 2^29 22.4 vs
+// 23.1, 2^30 44.7 vs 45.3 per transform; from 2^31 on the swapping middle
+// pass (one CTA per SM at R = 2^11, or stride 2^21 and more) loses more than
+// the swap sweep costs (2^31: 100.2 vs 94.3 ms per step).
 constexpr int kFuseMinLog2N = 26;
+constexpr int kFuseMaxLog2N = 30;
+// complex128 strided passes run persistent, prefetching the next tile, from
+// this size on (the wide first pass up to kPersistFirstMaxLog2N)
+constexpr int kPersistMinLog2N = 26;
+constexpr int kPersistFirstMaxLog2N = 31;
 
 // One pass of the schedule and its launch shape.
 struct Pass {
@@ -32,6 +40,7 @@ struct Pass {
   bool wide;  // complex128 first pass on 8192-element tiles
   int swap;   // middle pass that also swaps the outer digits: log2 of its
               // T x T column tile side (0: no swap)
+  bool pf;    // complex128 strided pass run by the persistent prefetching kernel
   uint64_t grid;
   int threads;
   size_t smem;
@@ -71,10 +80,25 @@ struct StateRing {
   int next = 0;
 };
 
-// A radix schedule (log2 R_0 .. log2 R_{np-1}).
+// Kernel variants of a power-of-two schedule, each -1 (the built-in rule:
+// by size), 0 (off) or 1 (on wherever the pass shapes allow it):
+//  wide  strided first pass (complex64 also the 2^11 middle pass) on tiles
+//        twice as wide (C doubled: longer row segments per page);
+//  fuse  complex128 (a, b, a): the middle pass swaps the outer digits and the
+//        last pass is strided (no separate swap sweep);
+//  pf    complex128 strided passes as persistent kernels that prefetch the
+//        next tile.
+struct Variant {
+  int wide = -1, fuse = -1, pf = -1;
+};
+
+// A tuned schedule: log2 R_0 .. log2 R_{np-1} and the variant for a power of
+// two; for N = M * 2^e the outer radix 2^mixed_a (0: one pass).
 struct Tuned {
-  int np;
-  int r[kMaxPasses];
+  int np = 0;
+  int r[kMaxPasses] = {0, 0, 0, 0};
+  Variant v;
+  int mixed_a = -1;
 };
 
 // Makes `dev` current for the guard's lifetime.
@@ -110,6 +134,7 @@ struct efft_plan_s {
   uint32_t perm_B;    //   middle extent perm_B
   uint32_t odd;       // N = odd * 2^e
   int twB;
+  int sms;  // multiprocessors of the plan's device (persistent launches)
   float4* w2048;
   float4* tw_lo;
   float4* tw_hi;
@@ -149,25 +174,30 @@ bool fault_injected(const char* what);
 int ilog2_u64(uint64_t n);
 // N = M * 2^e with M odd, M <= kMaxOdd, 1 <= N <= 2^EFFT_MAX_LOG2N.
 bool valid_size(uint64_t n);
-// Schedule of a plan with N = M * 2^e, M > 1 (pass table and swap).
-int apply_mixed_schedule(efft_plan_s* p);
+// Schedule of a plan with N = M * 2^e, M > 1 (pass table and swap); the
+// outer radix 2^force_a when force_a >= 0 is a valid choice (0: one pass).
+int apply_mixed_schedule(efft_plan_s* p, int force_a = -1);
+// The outer-radix exponents apply_mixed_schedule accepts for p (0: one pass).
+int mixed_candidates(const efft_plan_s* p, int* a, int cap);
 
 // Schedules: the planner's table, the accepted set, and filling a plan's
 // pass table from a radix list.
 int choose_radices(int e, int* r);
 bool valid_schedule(int e, const int* r, int np);
 int schedule_candidates(int e, int (*r)[kMaxPasses], int* np);
-void apply_schedule(efft_plan_s* p, const int* r, int np);
-bool tuned_lookup(int dev, int e, int dtype, Tuned* t);
-void tuned_store(int dev, int e, int dtype, const Tuned& t);
+void apply_schedule(efft_plan_s* p, const int* r, int np, const Variant& v = Variant());
+// The variant a plan's pass table realises (each knob 0 or 1).
+Variant realised_variant(const efft_plan_s* p);
+bool tuned_lookup(int dev, uint64_t n, int dtype, Tuned* t);
+void tuned_store(int dev, uint64_t n, int dtype, const Tuned& t);
 
 // A plan whose create arguments have been checked; r_explicit != NULL: the
 // caller's (validated) schedule.
 int plan_create_impl(efft_plan_t* out, uint64_t n, int dtype, int sign, uint32_t flags, const int* r_explicit,
                      int np_explicit);
-// Times every accepted schedule on `scratch` and keeps the fastest.
-int autotune_impl(efft_plan_s* p, void* scratch, cudaStream_t st, int* cand_log2r, double* cand_ms, int cap,
-                  int* ncand);
+// Times every accepted schedule on `scratch` (then the variants of the
+// fastest) and keeps the fastest; out[0..cap) receives the candidates.
+int autotune_impl(efft_plan_s* p, void* scratch, cudaStream_t st, efft_candidate* out, int cap, int* ncand);
 
 // Execution: buffer checks and the launch sequence of one transform or of a
 // batch of same-size transforms.

@@ -47,6 +47,8 @@ struct PassArgs {
   int out_shift;         // output multiplied by 2^-out_shift (1/N normalisation)
   uint32_t s_odd;        // first pass of N = M * 2^e: stride s = s_odd * 2^log2s
                          // (s_odd = M); 1 for power-of-two N
+  uint64_t ntiles;       // persistent kernels: tiles per transform (a swapping
+                         // pass: tile pairs)
 };
 
 // Shared-memory slot of (position p, column c): one pad slot per 16 keeps the
@@ -152,16 +154,19 @@ struct Mem<PolicyDF, KIND> {
 
 template <int KIND>
 struct Mem<PolicyDF2, KIND> {
-  static __device__ __forceinline__ cdf2 load(const void* base, uint64_t idx, int D, uint32_t conj) {
+  // an element's 16 bytes as stored in the buffer -> packed double-float
+  static __device__ __forceinline__ cdf2 convert(uint4 v, int D, uint32_t conj) {
     if (KIND == FIRST || KIND == SINGLE) {
-      uint4 v = __ldcg(reinterpret_cast<const uint4*>(base) + idx);
       df re = f64bits_to_df(v.x, v.y, D, 0u);
       df im = f64bits_to_df(v.z, v.w, D, conj ? 0x80000000u : 0u);
       return cdf2{make_float2(re.h, im.h), make_float2(re.l, im.l)};
     } else {
-      float4 v = __ldcg(reinterpret_cast<const float4*>(base) + idx);
-      return cdf2{make_float2(v.x, v.y), make_float2(v.z, v.w)};
+      return cdf2{make_float2(__uint_as_float(v.x), __uint_as_float(v.y)),
+                  make_float2(__uint_as_float(v.z), __uint_as_float(v.w))};
     }
+  }
+  static __device__ __forceinline__ cdf2 load(const void* base, uint64_t idx, int D, uint32_t conj) {
+    return convert(__ldcg(reinterpret_cast<const uint4*>(base) + idx), D, conj);
   }
   static __device__ __forceinline__ void store(void* base, uint64_t idx, cdf2 x, int D, uint32_t conj,
                                                bool nonfinite) {
@@ -618,6 +623,180 @@ efft_pass_fx(void* __restrict__ data, const PassArgs a) {
 }
 
 // ----------------------------------------------------------------------------
+// Persistent complex128 strided pass with the next tile's loads in flight
+// during the current tile's last stage and epilogue.
+//
+// A strided pass kernel of one CTA per tile loads its tile, then computes;
+// with one or two CTAs per SM (the register file holds only that many
+// 16-value double-float threads) the FP32 pipe idles while a new CTA's loads
+// are outstanding.  Here each CTA walks tiles tile, tile + grid, ...; as soon
+// as every thread has read the last stage's inputs from shared memory the
+// buffer is free, and each thread issues asynchronous copies (cp.async, 16
+// bytes each, cached in L2 only) of its own 16 stage-0 elements of the next
+// tile into their shared-memory slots.  Those copies complete while the last
+// stage, the pass twiddle and the stores run; the next tile then starts from
+// shared memory.  Same arithmetic, same results as efft_pass_fx.
+// Kinds: FIRST (power-of-two N), MID (also swapping, SWLT > 0), LASTS.
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const uint32_t sa = (uint32_t)__cvta_generic_to_shared(smem);
+  const size_t ga = __cvta_generic_to_global(gmem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(ga) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// Column geometry of a strided pass: first element, row step, twiddle index
+// m and output base of column c of tile `tile` (a swapping pass: of the
+// rank-th tile of tile pair `tile`).
+struct Geo {
+  uint64_t colbase, step, m, outbase;
+};
+template <int KIND, int LC, int SWLT>
+__device__ __forceinline__ Geo strided_geo(const PassArgs& a, uint64_t tile, uint32_t rank, int c) {
+  Geo g;
+  g.step = 1ull << a.log2s;
+  if (SWLT > 0) {
+    constexpr int T = 1 << SWLT;
+    uint32_t I, J;
+    swap_tile((uint32_t)tile, rank, 1u << (a.log2s - SWLT), I, J);
+    const uint64_t i0 = (uint64_t)I * T + (c >> SWLT), i2 = (uint64_t)J * T + (c & (T - 1));
+    g.m = i2;
+    g.colbase = (i0 << a.log2L) + i2;
+    g.outbase = (i2 << a.log2L) + i0;
+  } else if (KIND == FIRST || KIND == LASTS) {
+    const uint64_t jcol = (tile << LC) + c;
+    g.m = jcol;
+    g.colbase = g.outbase = jcol;
+  } else {
+    const uint64_t jcol = (tile << LC) + c;
+    g.m = jcol & (g.step - 1);
+    g.colbase = g.outbase = ((jcol >> a.log2s) << a.log2L) + g.m;
+  }
+  return g;
+}
+
+template <int KIND, int LR, int LC, int MINB, int SWLT = 0>
+__global__ void __launch_bounds__(1 << (LR + LC - 4), MINB)
+efft_pass_pf(void* __restrict__ data, const PassArgs a) {
+  typedef PolicyDF2 P;
+  typedef P::V V;
+  if (a.ptrs) data = a.ptrs[blockIdx.y];
+  const uint32_t* state = a.state + (a.ptrs ? 4u * blockIdx.y : 0u);
+  constexpr int R = 1 << LR, C = 1 << LC, TPC = R >> 4;
+  constexpr int NFULL = LR / 4, REM = LR % 4, NST = NFULL + (REM ? 1 : 0);
+  constexpr int NMID = NST - 2;
+  constexpr bool SWAP = SWLT > 0;
+  constexpr bool TWID = (KIND == FIRST || KIND == MID);
+  static_assert(KIND == FIRST || KIND == MID || KIND == LASTS, "strided kinds only");
+  static_assert(!SWAP || (KIND == MID && LC == 2 * SWLT), "a swapping pass is a middle pass of T x T columns");
+  static_assert(LR >= 5 && LR <= 12, "radix range");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  V* sm = reinterpret_cast<V*>(smem_raw);
+  __shared__ P::TW vtw[TWID ? 16 * C : 1];
+  auto slot = [](int p, int col) {
+    const int raw = (p << LC) + col;
+    return raw + (raw >> 4);
+  };
+
+  const int tid = threadIdx.x;
+  const int c = tid & (C - 1);
+  const int t = tid >> LC;
+  const uint32_t emax = __ldg(state);
+  const int D = (int)emax - 127;
+  const int Dout = D - a.out_shift;
+  const bool nonfinite = (emax >= 0x7FFu);
+  const int kt = digit_rev_c(t << 4, LR);
+  const int sb0 = slot(t, c);  // the thread's stage-0 slots: sb0 + pad_off(j * TPC * C)
+
+  const uint32_t rank = SWAP ? (blockIdx.x & 1u) : 0u;
+  const uint64_t stride = SWAP ? (gridDim.x >> 1) : gridDim.x;
+  uint64_t tile = SWAP ? (blockIdx.x >> 1) : blockIdx.x;
+
+  // the thread's 16 stage-0 elements of `tl`, rows t + TPC*j, into their slots
+  auto prefetch = [&](uint64_t tl) {
+    const Geo g = strided_geo<KIND, LC, SWLT>(a, tl, rank, c);
+    const uint64_t b0 = g.colbase + (uint64_t)t * g.step, sj = (uint64_t)TPC * g.step;
+    const uint4* src = reinterpret_cast<const uint4*>(data);
+#pragma unroll
+    for (int j = 0; j < 16; ++j) cp_async16(&sm[sb0 + pad_off(j * TPC * C)], src + b0 + (uint64_t)j * sj);
+    cp_async_commit();
+  };
+  if (tile < a.ntiles) prefetch(tile);
+
+  for (; tile < a.ntiles; tile += stride) {
+    const Geo g = strided_geo<KIND, LC, SWLT>(a, tile, rank, c);
+    __syncthreads();  // the previous tile's epilogue no longer reads vtw
+    P::TW wt;
+    if (TWID) {
+      const int sh = (KIND == FIRST) ? 0 : a.log2N - a.log2L;
+      if (tid < 16 * C) {
+        const int cc = tid >> 4, u = tid & 15;
+        const uint64_t mc = strided_geo<KIND, LC, SWLT>(a, tile, rank, cc).m;
+        const int kc = digit_rev_c(last_pos_c(u, REM), LR);
+        vtw[u * C + cc] = P::expand(twiddle_N(a, (mc * (uint64_t)kc) << sh));
+      }
+      wt = P::expand(twiddle_N(a, (g.m * (uint64_t)kt) << sh));
+    }
+
+    V v[16];
+    // ---- stage 0: the thread's own copies, now in shared memory ----
+    cp_async_wait_all();
+#pragma unroll
+    for (int j = 0; j < 16; ++j)
+      v[j] = Mem<P, KIND>::convert(reinterpret_cast<const uint4*>(sm)[sb0 + pad_off(j * TPC * C)], D, a.conj_in);
+    dif_regs<P, 4>(v);
+    // this tile's global loads are complete: the partner CTA may overwrite it
+    if (SWAP) cluster_arrive();
+#pragma unroll
+    for (int u = 1; u < 16; ++u)
+      v[u] = P::mul_tw(v[u], P::int_tw(a.w2048, nullptr, (uint32_t)(t * bitrev_c(u, 4)) << (11 - LR)));
+#pragma unroll
+    for (int u = 0; u < 16; ++u) sm[sb0 + pad_off(bitrev_c(u, 4) * TPC * C)] = v[u];
+    __syncthreads();
+
+    // ---- middle radix-16 stages ----
+#pragma unroll
+    for (int st = 1; st <= NMID; ++st) {
+      const int log2l = LR - 4 * st;
+      const int log2g = log2l - 4;
+      const int b = t >> log2g, i = t & ((1 << log2g) - 1);
+      const int sb = slot((b << log2l) + i, c);
+      const int gstep = (1 << log2g) * C;
+#pragma unroll
+      for (int j = 0; j < 16; ++j) v[j] = sm[sb + pad_off(j * gstep)];
+      dif_regs<P, 4>(v);
+#pragma unroll
+      for (int u = 1; u < 16; ++u)
+        v[u] = P::mul_tw(v[u], P::int_tw(a.w2048, nullptr, (uint32_t)(i * bitrev_c(u, 4)) << (11 - log2l)));
+#pragma unroll
+      for (int u = 0; u < 16; ++u) sm[sb + pad_off(bitrev_c(u, 4) * gstep)] = v[u];
+      __syncthreads();
+    }
+
+    // ---- last stage; then the buffer is free for the next tile's copies ----
+    {
+      const int sb = slot(t << 4, c);
+#pragma unroll
+      for (int j = 0; j < 16; ++j) v[j] = sm[sb + pad_off(j * C)];
+    }
+    __syncthreads();
+    if (tile + stride < a.ntiles) prefetch(tile + stride);
+    if (REM == 0) dif_regs<P, 4>(v);
+    else dif_groups<P, (REM == 0 ? 4 : REM)>(v);
+
+    if (SWAP) cluster_wait();
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+      const int k = kt | digit_rev_c(last_pos_c(u, REM), LR);
+      if (TWID) v[u] = P::pass_tw(v[u], wt, vtw[u * C + c]);
+      Mem<P, KIND>::store(data, g.outbase + ((uint64_t)k << a.log2s), v[u], Dout, a.conj_out, nonfinite);
+    }
+  }
+  cp_async_wait_all();  // nothing is left in flight when the CTA exits
+}
+
+// ----------------------------------------------------------------------------
 // N <= 8: one thread, Eq. 1 evaluated directly with table twiddles.
 // ----------------------------------------------------------------------------
 template <class P>
@@ -707,6 +886,11 @@ bool fx_launch_df2_swap(int log2R, int log2C, dim3 grid, dim3 block, size_t smem
                         const PassArgs& a);
 bool fx_launch_df2_lasts(int log2R, dim3 grid, dim3 block, size_t smem, cudaStream_t st, void* data,
                          const PassArgs& a);
+// complex128 strided passes as persistent kernels (efft_pass_pf): `grid`
+// CTAs walk a.ntiles tiles (tile pairs for a swapping pass, swap > 0).
+cudaError_t fx_set_attrs_df2_pf();
+bool fx_launch_df2_pf(int kind, int log2R, int log2C, int swap, dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                      void* data, const PassArgs& a);
 cudaError_t fx_set_attrs_f32();
 bool fx_launch_f32(int kind, int log2R, dim3 grid, dim3 block, size_t smem, cudaStream_t st, void* data,
                    const PassArgs& a);

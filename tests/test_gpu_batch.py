@@ -70,7 +70,11 @@ def test_autotune_scans_every_candidate(orc, name, e):
     plan = efft.Plan(N, _code(name), -1)
     scratch = torch.empty(N, dtype=torch.complex128 if name == "c128" else torch.complex64, device="cuda")
     res = plan.autotune(scratch.data_ptr(), torch.cuda.current_stream().cuda_stream)
-    assert [r for r, _ in res] == schedule_candidates(e)
+    ns = len(schedule_candidates(e))
+    # every accepted schedule first, then the fastest schedule's variants
+    assert [r for r, _ in res[:ns]] == schedule_candidates(e)
+    best_schedule = min(res[:ns], key=lambda t: t[1])[0]
+    assert all(r == best_schedule for r, _ in res[ns:])
     assert all(ms > 0 for _, ms in res)
     best = min(res, key=lambda t: t[1])[0]
     assert plan.radices() == best
@@ -81,6 +85,60 @@ def test_autotune_scans_every_candidate(orc, name, e):
     check(t.cpu().numpy().astype(np.complex128), orc.dft(x, -1), name, N, "autotuned")
     # later plans with the flag reuse the cached choice
     assert efft.Plan(N, _code(name), 1, efft.EFFT_FLAG_AUTOTUNE).radices() == best
+
+
+@pytest.mark.parametrize("name,e", [("c128", 26), ("c64", 26), ("c128", 16)])
+def test_autotune_scans_variants(orc, name, e):
+    """The tuner's second stage: for the fastest schedule each kernel
+    variant switched the other way where it changes the launches (the wide
+    strided tiles; complex128 from 2^26 also the folded digit swap and the
+    persistent passes); the plan ends on the fastest candidate and still
+    computes the DFT."""
+    import paper_1409_5757_gb300 as efft
+    N = 1 << e
+    plan = efft.Plan(N, _code(name), -1)
+    scratch = torch.empty(N, dtype=torch.complex128 if name == "c128" else torch.complex64, device="cuda")
+    res = plan.autotune_candidates(scratch.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    ns = len(schedule_candidates(e))
+    assert [[int(r).bit_length() - 1 for r in c["radices"]] for c in res[:ns]] == schedule_candidates(e)
+    best = min(res, key=lambda c: c["ms"])
+    assert plan.radices() == [int(r).bit_length() - 1 for r in best["radices"]]
+    assert plan.variant() == {k: best[k] for k in ("wide", "fused_swap", "persistent")}
+    keys = [(c["wide"], c["fused_swap"], c["persistent"]) for c in res[ns:]]
+    assert len(set(keys)) == len(keys) and len(keys) >= 1
+    if name == "c128" and e >= 26 and best["radices"][0] in (512, 1024, 2048) and len(best["radices"]) == 3:
+        assert any(c["fused_swap"] != res[0]["fused_swap"] for c in res) or len(keys) >= 2
+    x = host_input(orc, name, N, seed=56)
+    t = torch.from_numpy(x.astype(_np(name))).cuda()
+    plan.execute(t.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    check(t.cpu().numpy().astype(np.complex128), orc.dft(x, -1) if N <= (1 << 22) else orc.fft_radix2(x, -1),
+          name, N, "tuned variant")
+
+
+@pytest.mark.parametrize("name,n", [("c128", 3 << 20), ("c64", 5 << 18), ("c128", 15 << 14)])
+def test_autotune_mixed_sizes_scans_outer_radix(orc, name, n):
+    """N = M * 2^e: the tuner times every outer radix 2^a of the
+    (2^a, M 2^b, 2^a) schedule the kernels accept (and one pass when
+    N <= 2048), keeps the fastest, and later plans with EFFT_FLAG_AUTOTUNE
+    reuse it."""
+    import paper_1409_5757_gb300 as efft
+    plan = efft.Plan(n, _code(name), -1)
+    scratch = torch.empty(n, dtype=torch.complex128 if name == "c128" else torch.complex64, device="cuda")
+    res = plan.autotune_candidates(scratch.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    outer = [c["radices"][0] for c in res]
+    assert len(outer) == len(set(outer)) >= 3
+    for c in res:
+        A, B = c["radices"][0], c["radices"][1]
+        assert c["radices"][2] == A and A * B * A == n and A <= 2048 and B <= 2048
+    best = min(res, key=lambda c: c["ms"])
+    assert best["ms"] > 0
+    # a plan created with the flag reuses the measured choice
+    tuned = efft.Plan(n, _code(name), -1, efft.EFFT_FLAG_AUTOTUNE)
+    assert tuned.radices() == [int(R & -R).bit_length() - 1 for R in best["radices"]]
+    x = host_input(orc, name, n, seed=57)
+    t = torch.from_numpy(x.astype(_np(name))).cuda()
+    tuned.execute(t.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    check(t.cpu().numpy().astype(np.complex128), orc.dft(x, -1), name, n, "tuned mixed")
 
 
 @pytest.mark.parametrize("name", ["c128", "c64"])

@@ -369,3 +369,43 @@ def test_fused_digit_swap_in_a_batch_is_bit_identical():
     b.destroy()
     p.destroy()
     del want, xs
+
+
+@pytest.mark.parametrize("radices,flags,variant", [
+    ([8, 11, 8], 0, (-1, -1, 1)), ([9, 9, 9], 0, (-1, -1, 1)), ([8, 10, 8], 0, (-1, -1, 1)),
+    ([10, 8, 10], 1, (1, -1, 1)), ([9, 11, 9], 0, (-1, 1, 1)), ([10, 8, 10], 0, (1, 1, 1)),
+    ([10, 8, 10], 0, (0, 0, 0)), ([9, 8, 9], 0, (1, 1, 0))],
+    ids=["8-11-8-pf", "9-9-9-pf", "8-10-8-pf", "10-8-10-wide-pf-digit-reversed", "9-11-9-fused-pf",
+         "10-8-10-all", "10-8-10-none", "9-8-9-wide-fused"])
+def test_parity_persistent_passes(orc, radices, flags, variant):
+    """complex128 from 2^26 on, every kernel variant set through
+    efft_plan_set_variant: the persistent strided passes that copy the next
+    tile's inputs into shared memory while the current tile finishes (every
+    middle-pass radix 2^8..2^11 on 4096-element tiles, the wide first pass,
+    the swapping and the strided last passes), the folded digit swap and the
+    wide first-pass tiles, on and off; against the full oracle, in natural or
+    digit-reversed order."""
+    import paper_1409_5757_gb300 as efft
+    e = sum(radices)
+    N = 1 << e
+    x = host_input(orc, "c128", N, seed=4100 + e + radices[1])
+    t = torch.from_numpy(x).cuda()
+    p = efft.Plan(N, efft.EFFT_C128, -1, flags, radices=radices)
+    got_v = p.set_variant(*variant)
+    for k, want in zip(("wide", "fused_swap", "persistent"), variant):
+        if want == 0:
+            assert got_v[k] == 0, (k, got_v)
+    if variant[2] == 1:
+        assert got_v["persistent"] == 1
+    p.execute(t.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    got = t.cpu().numpy()
+    del t
+    p.destroy()
+    ref = orc.fft_radix2(x, -1)
+    if flags & efft.EFFT_FLAG_DIGIT_REVERSED_OUT:
+        a, b = radices[0], radices[1]
+        P = np.arange(N, dtype=np.int64)
+        q0, q1, q2 = P >> (a + b), (P >> a) & ((1 << b) - 1), P & ((1 << a) - 1)
+        ref = ref[q0 + (q1 << a) + (q2 << (a + b))]
+    check(got, ref, "c128", N)
