@@ -87,7 +87,7 @@ def test_autotune_scans_every_candidate(orc, name, e):
     assert efft.Plan(N, _code(name), 1, efft.EFFT_FLAG_AUTOTUNE).radices() == best
 
 
-@pytest.mark.parametrize("name,e", [("c128", 26), ("c64", 26), ("c128", 16)])
+@pytest.mark.parametrize("name,e", [("c128", 26), ("c64", 26), ("c128", 16), ("c64", 21)])
 def test_autotune_scans_variants(orc, name, e):
     """The tuner's second stage: for the fastest schedule each kernel
     variant switched the other way where it changes the launches (the wide
@@ -104,8 +104,10 @@ def test_autotune_scans_variants(orc, name, e):
     best = min(res, key=lambda c: c["ms"])
     assert plan.radices() == [int(r).bit_length() - 1 for r in best["radices"]]
     assert plan.variant() == {k: best[k] for k in ("wide", "fused_swap", "persistent")}
+    # each variant candidate differs from the others (a knob that changes no
+    # launch of the fastest schedule is not measured)
     keys = [(c["wide"], c["fused_swap"], c["persistent"]) for c in res[ns:]]
-    assert len(set(keys)) == len(keys) and len(keys) >= 1
+    assert len(set(keys)) == len(keys) <= 3
     if name == "c128" and e >= 26 and best["radices"][0] in (512, 1024, 2048) and len(best["radices"]) == 3:
         assert any(c["fused_swap"] != res[0]["fused_swap"] for c in res) or len(keys) >= 2
     x = host_input(orc, name, N, seed=56)
