@@ -320,8 +320,12 @@ void apply_schedule(efft_plan_s* p, const int* r, int np, const Variant& v) {
   // array reaches natural order without a separate swap sweep; the last pass
   // then transforms the columns of the swapped layout, strided like the
   // first pass, on 8192-element tiles.
-  if (fuse_on && p->permute && np == 3 && c128 && r[0] >= 9 && r[0] <= 11 &&
-      (r[1] == 8 || r[1] == 10 || r[1] == 11)) {
+  // The size rule folds only middle radices 2^8 and 2^10 (two CTAs per SM);
+  // the 2^11 swapping pass (one 512-thread CTA per SM) is slower than the
+  // swap sweep it saves at every size measured, and is reached only through
+  // an explicit variant.
+  const bool fuse_mid = (r[1] == 8 || r[1] == 10) || (v.fuse > 0 && r[1] == 11);
+  if (fuse_on && p->permute && np == 3 && c128 && r[0] >= 9 && r[0] <= 11 && fuse_mid) {
     Pass& m = p->pass[1];
     m.swap = (r[1] == 8) ? 2 : 1;
     m.log2C = 2 * m.swap;

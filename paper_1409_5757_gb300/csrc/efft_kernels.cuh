@@ -781,28 +781,17 @@ efft_pass_pf(void* __restrict__ data, const PassArgs a) {
       for (int j = 0; j < 16; ++j) v[j] = sm[sb + pad_off(j * C)];
     }
     __syncthreads();
-    // the next tile's copies are issued one per output row of the epilogue,
-    // spread between its stores rather than in one burst
-    const bool more = tile + stride < a.ntiles;
-    uint64_t nb0 = 0, nsj = 0;
-    if (more) {
-      const Geo gn = strided_geo<KIND, LC, SWLT>(a, tile + stride, rank, c);
-      nb0 = gn.colbase + (uint64_t)t * gn.step;
-      nsj = (uint64_t)TPC * gn.step;
-    }
+    if (tile + stride < a.ntiles) prefetch(tile + stride);
     if (REM == 0) dif_regs<P, 4>(v);
     else dif_groups<P, (REM == 0 ? 4 : REM)>(v);
 
     if (SWAP) cluster_wait();
-    const uint4* src = reinterpret_cast<const uint4*>(data);
 #pragma unroll
     for (int u = 0; u < 16; ++u) {
-      if (more) cp_async16(&sm[sb0 + pad_off(u * TPC * C)], src + nb0 + (uint64_t)u * nsj);
       const int k = kt | digit_rev_c(last_pos_c(u, REM), LR);
       if (TWID) v[u] = P::pass_tw(v[u], wt, vtw[u * C + c]);
       Mem<P, KIND>::store(data, g.outbase + ((uint64_t)k << a.log2s), v[u], Dout, a.conj_out, nonfinite);
     }
-    if (more) cp_async_commit();
   }
   cp_async_wait_all();  // nothing is left in flight when the CTA exits
 }
