@@ -217,9 +217,8 @@ int efft_plan_create_with_radices(efft_plan_t* out, uint64_t n, int dtype, int s
  *    switched the other way where it changes the passes (kept when faster):
  *    the tile width of the strided first pass (complex64: also of the 2^11
  *    middle pass) doubled or not, the digit swap folded into the middle pass
- *    or not, the persistent prefetching pass kernels or not, radix-8
- *    register stages (8 values per thread, twice the resident warps) or
- *    radix-16 (the last three complex128 only);
+ *    or not, the persistent prefetching pass kernels or not (the last two
+ *    complex128 only);
  *  - n = M * 2^e, M > 1: every outer radix 2^a of the (2^a, M * 2^b, 2^a)
  *    schedule that efft_plan_create accepts, and one pass when n <= 2048.
  * Each candidate is run on `scratch` (n*S bytes of the caller's device
@@ -245,7 +244,6 @@ typedef struct efft_candidate {
   int wide;             /* 1: the wide strided tiles (see efft_plan_autotune)   */
   int fused_swap;       /* 1: digit swap folded into the middle pass            */
   int persistent;       /* 1: persistent prefetching pass kernels               */
-  int radix8;           /* 1: complex128 passes with radix-8 register stages    */
   double ms;            /* median time of one execute (milliseconds)            */
 } efft_candidate;
 
@@ -259,7 +257,7 @@ int efft_plan_autotune_candidates(efft_plan_t plan, void* scratch, void* stream,
 
 /* The kernel variant a plan runs (each 0 or 1; see efft_candidate).  Any
  * pointer may be NULL.  Errors: INVALID_PLAN. */
-int efft_plan_variant(efft_plan_t plan, int* wide, int* fused_swap, int* persistent, int* radix8);
+int efft_plan_variant(efft_plan_t plan, int* wide, int* fused_swap, int* persistent);
 
 /* Switch a plan's kernel variant, keeping its schedule (e.g. to pin a choice
  * an earlier efft_plan_autotune_candidates measured).  Each knob: -1 the
@@ -269,7 +267,7 @@ int efft_plan_variant(efft_plan_t plan, int* wide, int* fused_swap, int* persist
  * A real-data plan switches its complex plan.
  * Errors: INVALID_PLAN; INVALID_FLAGS for a knob outside -1..1;
  * UNSUPPORTED for a plan of N = M * 2^e (M > 1) with a knob other than -1. */
-int efft_plan_set_variant(efft_plan_t plan, int wide, int fused_swap, int persistent, int radix8);
+int efft_plan_set_variant(efft_plan_t plan, int wide, int fused_swap, int persistent);
 
 /* Destroy a plan and free its device tables, after waiting for the
  * executes still using its state words.  The paper's ~EFFT_Transform()

@@ -4,8 +4,7 @@
                        efft_tune.cu autotuner, efft_batch.cu batches,
                        efft_real.cu real-data transforms,
                        efft_mix.cu N = M * 2^e passes,
-                       efft_fx_df2.cu / efft_fx_df2_r8.cu / efft_fx_f32.cu
-                       pass kernels,
+                       efft_fx_df2.cu / efft_fx_f32.cu pass kernels,
                        efft_noalloc.cu; C ABI in include/efft.h)
     libefft_inputs.so  seeded device inputs and norms (csrc/inputs.cu;
                        include/efft_inputs.h), test/benchmark harness only
@@ -34,7 +33,7 @@ COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INC]
 # library -> (translation units, headers they depend on)
 LIBS = {
     "libefft.so": (["efft.cu", "efft_tune.cu", "efft_batch.cu", "efft_real.cu", "efft_mix.cu", "efft_fx_df2.cu",
-                    "efft_fx_df2_r8.cu", "efft_fx_f32.cu", "efft_noalloc.cu"],
+                    "efft_fx_f32.cu", "efft_noalloc.cu"],
                    ["efft_kernels.cuh", "efft_arith.cuh", "efft_mix.cuh", "efft_fx32.cuh", "efft_host.h"], ["efft.h"]),
     "libefft_inputs.so": (["inputs.cu"], [], ["efft_inputs.h"]),
 }

@@ -346,23 +346,6 @@ void apply_schedule(efft_plan_s* p, const int* r, int np, const Variant& v) {
     l.smem = (le + le / 16 + 1) * eb;
     p->permute = false;
   }
-  // radix-8 register stages (8 values per thread) for the complex128 passes
-  // whose tile shape has such a kernel
-  if (c128 && on(v.v8, false)) {
-    for (int j = 0; j < np; ++j) {
-      Pass& ps = p->pass[j];
-      const int lr = ps.log2R, lc = ps.log2C, cta = lr + lc;
-      bool shape = false;
-      if (ps.swap) shape = (lr == 11 && lc == 2) || (lr == 10 && lc == 2) || (lr == 8 && lc == 4);
-      else if (ps.kind == FIRST) shape = (cta == kLog2CtaC128 && lr >= 8) || (ps.wide && (lr == 10 || lr == 11));
-      else if (ps.kind == MID || ps.kind == LAST) shape = (cta == kLog2CtaC128 && lr >= 8 && lr <= 11);
-      else if (ps.kind == LASTS) shape = (cta == kLog2CtaWide && lr >= 9 && lr <= 11);
-      if (shape) {
-        ps.lv = 3;
-        ps.threads = 1 << (cta - 3);
-      }
-    }
-  }
   // persistent prefetching kernels for the complex128 strided passes with a
   // tile shape they are built for.  The rule (measured, 2^28..2^33): they
   // pay for the one-CTA-per-SM passes -- the strided last pass at every
@@ -385,19 +368,18 @@ void apply_schedule(efft_plan_s* p, const int* r, int np, const Variant& v) {
         shape = (lr >= 9 && lr <= 11 && lr + lc == kLog2CtaWide);
         rule = true;
       }
-      ps.pf = shape && (pf > 0 || rule) && ps.lv != 3;
+      ps.pf = shape && (pf > 0 || rule);
     }
   }
 }
 
 Variant realised_variant(const efft_plan_s* p) {
   Variant v;
-  v.wide = v.fuse = v.pf = v.v8 = 0;
+  v.wide = v.fuse = v.pf = 0;
   for (int j = 0; j < p->npasses; ++j) {
     if (p->pass[j].wide) v.wide = 1;
     if (p->pass[j].swap) v.fuse = 1;
     if (p->pass[j].pf) v.pf = 1;
-    if (p->pass[j].lv == 3) v.v8 = 1;
   }
   return v;
 }
@@ -474,8 +456,6 @@ int init_kernels() {
     cudaError_t e0 = mix_set_attrs();
     cudaError_t e1 = fx_set_attrs_df2();
     cudaError_t e2 = fx_set_attrs_f32();
-    const cudaError_t e3 = fx_set_attrs_df2_r8();
-    if (e2 == cudaSuccess) e2 = e3;
     cudaError_t err = cudaGetLastError();
     if (err == cudaSuccess) err = (e0 != cudaSuccess) ? e0 : (e1 != cudaSuccess) ? e1 : e2;
     if (err != cudaSuccess) return EFFT_ERR_CUDA;
@@ -593,10 +573,6 @@ cudaError_t launch_pass(const efft_plan_s* p, const Pass& ps, void* data, const 
   a.s_odd = (ps.kind == FIRST && p->odd > 1) ? p->odd : 1u;
   dim3 grid((unsigned)ps.grid, bt.count), block(ps.threads);
   constexpr int LOG2CTA = (P::kElemBytes == 16) ? kLog2CtaC128 : kLog2CtaC64;
-  if (P::kElemBytes == 16 && ps.lv == 3) {
-    const bool ok = fx_launch_df2_r8(ps.kind, ps.log2R, ps.log2C, ps.swap, grid, block, ps.smem, st, data, a);
-    return ok ? cudaGetLastError() : cudaErrorInvalidConfiguration;
-  }
   if (P::kElemBytes == 16 && ps.pf) {
     // persistent: at most as many CTAs (CTA pairs) as can be resident
     const int minb = (ps.log2R + ps.log2C == kLog2CtaWide) ? 1 : 2;

@@ -41,8 +41,6 @@ struct Pass {
   int swap;   // middle pass that also swaps the outer digits: log2 of its
               // T x T column tile side (0: no swap)
   bool pf;    // complex128 strided pass run by the persistent prefetching kernel
-  int lv;     // complex128: log2 of the values per thread (0: 4, radix-16 stages;
-              // 3: radix-8 stages, twice the threads)
   uint64_t grid;
   int threads;
   size_t smem;
@@ -90,10 +88,8 @@ struct StateRing {
 //        last pass is strided (no separate swap sweep);
 //  pf    complex128 strided passes as persistent kernels that prefetch the
 //        next tile.
-//  v8    complex128 passes with radix-8 register stages (8 values per
-//        thread, twice the threads and resident warps).
 struct Variant {
-  int wide = -1, fuse = -1, pf = -1, v8 = -1;
+  int wide = -1, fuse = -1, pf = -1;
 };
 
 // A tuned schedule: log2 R_0 .. log2 R_{np-1} and the variant for a power of

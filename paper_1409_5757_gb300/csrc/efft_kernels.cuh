@@ -385,28 +385,27 @@ __host__ __device__ constexpr int bitrev_c(int v, int bits) {
   for (int b = 0; b < bits; ++b) r |= ((v >> b) & 1) << (bits - 1 - b);
   return r;
 }
-// output index k of column position p (see col_digit_reverse) for stages of
-// radix 2^LV (the last one 2^(LR mod LV))
-__host__ __device__ constexpr int digit_rev_c(int p, int LR, int LV = 4) {
-  int nfull = LR / LV, rem = LR % LV, k = 0, shift = LR;
+// output index k of column position p (see col_digit_reverse)
+__host__ __device__ constexpr int digit_rev_c(int p, int LR) {
+  int nfull = LR / 4, rem = LR % 4, k = 0, shift = LR;
   for (int st = 0; st < nfull; ++st) {
-    shift -= LV;
-    k |= ((p >> shift) & ((1 << LV) - 1)) << (LV * st);
+    shift -= 4;
+    k |= ((p >> shift) & 15) << (4 * st);
   }
-  if (rem) k |= (p & ((1 << rem) - 1)) << (LV * nfull);
+  if (rem) k |= (p & ((1 << rem) - 1)) << (4 * nfull);
   return k;
 }
-__host__ __device__ constexpr int last_pos_c(int u, int rem, int LV = 4) {
-  return rem == 0 ? bitrev_c(u, LV) : ((u & ~((1 << rem) - 1)) | bitrev_c(u & ((1 << rem) - 1), rem));
+__host__ __device__ constexpr int last_pos_c(int u, int rem) {
+  return rem == 0 ? bitrev_c(u, 4) : ((u & ~((1 << rem) - 1)) | bitrev_c(u & ((1 << rem) - 1), rem));
 }
 // padded slot offset of a raw offset that is a multiple of C (C a power of two)
 __host__ __device__ constexpr int pad_off(int raw) { return raw + (raw >> 4); }
 
-template <class P, int LOG, int NV = 16>
+template <class P, int LOG>
 __device__ __forceinline__ void dif_groups(typename P::V* v) {
-  // NV registers as NV / 2^LOG independent radix-2^LOG DIF groups
+  // 16 registers as 16 / 2^LOG independent radix-2^LOG DIF groups
 #pragma unroll
-  for (int g = 0; g < NV; g += (1 << LOG)) dif_regs<P, LOG>(v + g);
+  for (int g = 0; g < 16; g += (1 << LOG)) dif_regs<P, LOG>(v + g);
 }
 
 // Cluster-wide split barrier (all threads of both CTAs of a pair arrive,
@@ -443,21 +442,15 @@ __device__ __forceinline__ void swap_tile(uint32_t z, uint32_t rank, uint32_t nt
 // digit-reversal sweep is needed.  The two CTAs of a cluster hold each
 // other's destination tiles; a cluster barrier between their loads and their
 // stores keeps the exchange in place.
-// LV: log2 of the values a thread holds, the radix of the register stages
-// (4: radix 16, 16 values; 3: radix 8, 8 values and twice the threads, so
-// twice the resident warps at the same register file).
-template <class P, int KIND, int LR, int LC, int MINB = 2, int SWLT = 0, int LV = 4>
-__global__ void __launch_bounds__(1 << (LR + LC - LV), MINB)
+template <class P, int KIND, int LR, int LC, int MINB = 2, int SWLT = 0>
+__global__ void __launch_bounds__(1 << (LR + LC - 4), MINB)
 efft_pass_fx(void* __restrict__ data, const PassArgs a) {
   typedef typename P::V V;
   if (a.ptrs) data = a.ptrs[blockIdx.y];
   const uint32_t* state = a.state + (a.ptrs ? 4u * blockIdx.y : 0u);
-  constexpr int NV = 1 << LV;  // values per thread
-  constexpr int R = 1 << LR, C = 1 << LC, TPC = R >> LV, NT = (R * C) >> LV;
-  constexpr int NFULL = LR / LV, REM = LR % LV, NST = NFULL + (REM ? 1 : 0);
-  constexpr int NMID = NST - 2;  // register stages between the first and the last
-  static_assert(LV == 3 || LV == 4, "radix 8 or 16 register stages");
-  static_assert(NST >= 2, "at least two register stages");
+  constexpr int R = 1 << LR, C = 1 << LC, TPC = R >> 4, NT = (R * C) / 16;
+  constexpr int NFULL = LR / 4, REM = LR % 4, NST = NFULL + (REM ? 1 : 0);
+  constexpr int NMID = NST - 2;  // radix-16 stages between the first and the last
   constexpr bool SWAP = SWLT > 0;
   static_assert(!SWAP || (KIND == MID && LC == 2 * SWLT), "a swapping pass is a middle pass of T x T columns");
   constexpr bool STRIDED = (KIND == FIRST || KIND == MID || KIND == LASTS);
@@ -474,7 +467,7 @@ efft_pass_fx(void* __restrict__ data, const PassArgs a) {
   static_assert(LR >= 5 && LR <= 12, "radix range");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V* sm = reinterpret_cast<V*>(smem_raw);
-  __shared__ typename P::TW vtw[TWID ? NV * C : 1];
+  __shared__ typename P::TW vtw[TWID ? 16 * C : 1];
   // column-major last pass: lanes hold different t, so the stage-0 twiddles
   // exp(-2*pi*i*t*q/R) come from a shared copy of the R-th roots of unity
   // (root k at k + k/8: lanes reading k = 8t or 4t stay on different banks)
@@ -485,7 +478,7 @@ efft_pass_fx(void* __restrict__ data, const PassArgs a) {
   };
 
   const int tid = threadIdx.x;
-  const int c = CM ? (tid >> (LR - LV)) : (tid & (C - 1));
+  const int c = CM ? (tid >> (LR - 4)) : (tid & (C - 1));
   const int t = CM ? (tid & (TPC - 1)) : (tid >> LC);
   const uint64_t jcol = (uint64_t)blockIdx.x * C + c;
   uint64_t m = 0, colbase, step, outbase = 0;
@@ -522,74 +515,74 @@ efft_pass_fx(void* __restrict__ data, const PassArgs a) {
     nonfinite = (emax >= 0x7FFu);
   }
 
-  const int kt = digit_rev_c(t << LV, LR, LV);
+  const int kt = digit_rev_c(t << 4, LR);
   typename P::TW wt;
   if (TWID) {
     const int sh = (KIND == FIRST) ? 0 : a.log2N - a.log2L;
     // V_c[u] stored as [u][c]: the columns of one warp read consecutive entries
-    if (tid < NV * C) {
-      const int cc = tid >> LV, u = tid & (NV - 1);
+    if (tid < 16 * C) {
+      const int cc = tid >> 4, u = tid & 15;
       const uint64_t mc = SWAP ? (uint64_t)tJ * (1u << SWLT) + (cc & ((1 << SWLT) - 1))
                                : ((uint64_t)blockIdx.x * C + cc) & (KIND == FIRST ? ~0ull : step - 1);
-      const int kc = digit_rev_c(last_pos_c(u, REM, LV), LR, LV);
+      const int kc = digit_rev_c(last_pos_c(u, REM), LR);
       vtw[u * C + cc] = P::expand(twiddle_N(a, (mc * (uint64_t)kc) << sh));
     }
     wt = P::expand(twiddle_N(a, (m * (uint64_t)kt) << sh));
   }
 
-  V v[NV];
+  V v[16];
   // ---- stage 0: rows t + TPC*j straight from global memory ----
   {
     const uint64_t b0 = colbase + (uint64_t)t * step, sj = (uint64_t)TPC * step;
 #pragma unroll
-    for (int j = 0; j < NV; ++j) v[j] = Mem<P, KIND>::load(data, b0 + (uint64_t)j * sj, D, a.conj_in);
+    for (int j = 0; j < 16; ++j) v[j] = Mem<P, KIND>::load(data, b0 + (uint64_t)j * sj, D, a.conj_in);
   }
   if (CM) {
     for (int k = tid; k < R; k += NT) wroot[k + (k >> 3)] = __ldg(a.w2048 + (k << (11 - LR)));
     __syncthreads();
   }
-  dif_regs<P, LV>(v);
+  dif_regs<P, 4>(v);
   // the stage-0 loads are consumed: the partner CTA may overwrite this tile
   if (SWAP) cluster_arrive();
   {
-    // exp(-2*pi*i * t*q / R), q = bitrev(u), to positions t + TPC*q
+    // exp(-2*pi*i * t*q / R), q = bitrev4(u), to positions t + TPC*q
 #pragma unroll
-    for (int u = 1; u < NV; ++u)
-      v[u] = P::mul_tw(v[u], CM ? P::expand(wroot[t * bitrev_c(u, LV) + ((t * bitrev_c(u, LV)) >> 3)])
-                                : P::int_tw(a.w2048, nullptr, (uint32_t)(t * bitrev_c(u, LV)) << (11 - LR)));
+    for (int u = 1; u < 16; ++u)
+      v[u] = P::mul_tw(v[u], CM ? P::expand(wroot[t * bitrev_c(u, 4) + ((t * bitrev_c(u, 4)) >> 3)])
+                                : P::int_tw(a.w2048, nullptr, (uint32_t)(t * bitrev_c(u, 4)) << (11 - LR)));
     const int sb = slot(t, c);
 #pragma unroll
-    for (int u = 0; u < NV; ++u) sm[sb + pad_off(bitrev_c(u, LV) * TPC * PS)] = v[u];
+    for (int u = 0; u < 16; ++u) sm[sb + pad_off(bitrev_c(u, 4) * TPC * PS)] = v[u];
   }
   __syncthreads();
 
-  // ---- middle register stages ----
+  // ---- middle radix-16 stages ----
 #pragma unroll
   for (int st = 1; st <= NMID; ++st) {
-    const int log2l = LR - LV * st;     // sub-block length
-    const int log2g = log2l - LV;       // groups per sub-block
+    const int log2l = LR - 4 * st;      // sub-block length
+    const int log2g = log2l - 4;        // groups per sub-block
     const int b = t >> log2g, i = t & ((1 << log2g) - 1);
     const int sb = slot((b << log2l) + i, c);
     const int gstep = (1 << log2g) * PS;  // raw step between group members
 #pragma unroll
-    for (int j = 0; j < NV; ++j) v[j] = sm[sb + pad_off(j * gstep)];
-    dif_regs<P, LV>(v);
+    for (int j = 0; j < 16; ++j) v[j] = sm[sb + pad_off(j * gstep)];
+    dif_regs<P, 4>(v);
 #pragma unroll
-    for (int u = 1; u < NV; ++u)
-      v[u] = P::mul_tw(v[u], P::int_tw(a.w2048, nullptr, (uint32_t)(i * bitrev_c(u, LV)) << (11 - log2l)));
+    for (int u = 1; u < 16; ++u)
+      v[u] = P::mul_tw(v[u], P::int_tw(a.w2048, nullptr, (uint32_t)(i * bitrev_c(u, 4)) << (11 - log2l)));
     // in place: the thread writes exactly the slots it read
 #pragma unroll
-    for (int u = 0; u < NV; ++u) sm[sb + pad_off(bitrev_c(u, LV) * gstep)] = v[u];
+    for (int u = 0; u < 16; ++u) sm[sb + pad_off(bitrev_c(u, 4) * gstep)] = v[u];
     __syncthreads();
   }
 
-  // ---- last stage: the thread's NV contiguous positions NV*t .. NV*t+NV-1 ----
+  // ---- last stage: the thread's 16 contiguous positions 16t .. 16t+15 ----
   {
-    const int sb = slot(t << LV, c);
+    const int sb = slot(t << 4, c);
 #pragma unroll
-    for (int j = 0; j < NV; ++j) v[j] = sm[sb + pad_off(j * PS)];
-    if (REM == 0) dif_regs<P, LV>(v);
-    else dif_groups<P, (REM == 0 ? LV : REM), NV>(v);
+    for (int j = 0; j < 16; ++j) v[j] = sm[sb + pad_off(j * PS)];
+    if (REM == 0) dif_regs<P, 4>(v);
+    else dif_groups<P, (REM == 0 ? 4 : REM)>(v);
   }
 
   if (STRIDED && (KIND != FIRST || a.s_odd == 1)) {
@@ -598,16 +591,16 @@ efft_pass_fx(void* __restrict__ data, const PassArgs a) {
     if (SWAP) cluster_wait();
     const uint64_t ob = SWAP ? outbase : colbase;
 #pragma unroll
-    for (int u = 0; u < NV; ++u) {
-      const int k = kt | digit_rev_c(last_pos_c(u, REM, LV), LR, LV);
+    for (int u = 0; u < 16; ++u) {
+      const int k = kt | digit_rev_c(last_pos_c(u, REM), LR);
       if (TWID) v[u] = P::pass_tw(v[u], wt, vtw[u * C + c]);
       Mem<P, KIND>::store(data, ob + ((uint64_t)k << a.log2s), v[u], Dout, a.conj_out, nonfinite);
     }
   } else if (STRIDED) {
     // first pass of N = M * 2^e: output k at k * M * 2^log2s
 #pragma unroll
-    for (int u = 0; u < NV; ++u) {
-      const int k = kt | digit_rev_c(last_pos_c(u, REM, LV), LR, LV);
+    for (int u = 0; u < 16; ++u) {
+      const int k = kt | digit_rev_c(last_pos_c(u, REM), LR);
       v[u] = P::pass_tw(v[u], wt, vtw[u * C + c]);
       Mem<P, KIND>::store(data, colbase + ((uint64_t)(k * a.s_odd) << a.log2s), v[u], Dout, a.conj_out,
                           nonfinite);
@@ -615,8 +608,8 @@ efft_pass_fx(void* __restrict__ data, const PassArgs a) {
   } else {
     __syncthreads();  // last-stage reads are complete before the slots are reused
 #pragma unroll
-    for (int u = 0; u < NV; ++u) {
-      const int k = kt | digit_rev_c(last_pos_c(u, REM, LV), LR, LV);
+    for (int u = 0; u < 16; ++u) {
+      const int k = kt | digit_rev_c(last_pos_c(u, REM), LR);
       sm[slot(k, c)] = v[u];
     }
     __syncthreads();
@@ -893,12 +886,6 @@ bool fx_launch_df2_swap(int log2R, int log2C, dim3 grid, dim3 block, size_t smem
                         const PassArgs& a);
 bool fx_launch_df2_lasts(int log2R, dim3 grid, dim3 block, size_t smem, cudaStream_t st, void* data,
                          const PassArgs& a);
-// complex128 passes with radix-8 register stages (efft_fx_df2_r8.cu): the
-// 4096-element tiles of every kind, the wide first and strided last passes,
-// the swapping middle passes; threads = tile / 8.
-cudaError_t fx_set_attrs_df2_r8();
-bool fx_launch_df2_r8(int kind, int log2R, int log2C, int swap, dim3 grid, dim3 block, size_t smem, cudaStream_t st,
-                      void* data, const PassArgs& a);
 // complex128 strided passes as persistent kernels (efft_pass_pf): `grid`
 // CTAs walk a.ntiles tiles (tile pairs for a swapping pass, swap > 0).
 cudaError_t fx_set_attrs_df2_pf();

@@ -372,25 +372,19 @@ def test_fused_digit_swap_in_a_batch_is_bit_identical():
 
 
 @pytest.mark.parametrize("radices,flags,variant", [
-    ([8, 11, 8], 0, (-1, -1, 1, 0)), ([9, 9, 9], 0, (-1, -1, 1, 0)), ([8, 10, 8], 0, (-1, -1, 1, 0)),
-    ([10, 8, 10], 1, (1, -1, 1, 0)), ([9, 11, 9], 0, (-1, 1, 1, 0)), ([10, 8, 10], 0, (1, 1, 1, 0)),
-    ([10, 8, 10], 0, (0, 0, 0, 0)), ([9, 8, 9], 0, (1, 1, 0, 0)),
-    ([8, 11, 8], 0, (-1, -1, 0, 1)), ([9, 9, 9], 0, (-1, -1, 0, 1)), ([8, 10, 8], 0, (-1, 0, 0, 1)),
-    ([10, 8, 10], 1, (1, -1, 0, 1)), ([9, 11, 9], 0, (-1, 1, 0, 1)), ([10, 8, 10], 0, (1, 1, 0, 1)),
-    ([11, 4, 11], 0, (1, 0, 0, 1)), ([10, 10, 10], 0, (1, 0, 0, 1))],
+    ([8, 11, 8], 0, (-1, -1, 1)), ([9, 9, 9], 0, (-1, -1, 1)), ([8, 10, 8], 0, (-1, -1, 1)),
+    ([10, 8, 10], 1, (1, -1, 1)), ([9, 11, 9], 0, (-1, 1, 1)), ([10, 8, 10], 0, (1, 1, 1)),
+    ([10, 8, 10], 0, (0, 0, 0)), ([9, 8, 9], 0, (1, 1, 0))],
     ids=["8-11-8-pf", "9-9-9-pf", "8-10-8-pf", "10-8-10-wide-pf-digit-reversed", "9-11-9-fused-pf",
-         "10-8-10-all", "10-8-10-none", "9-8-9-wide-fused", "8-11-8-r8", "9-9-9-r8", "8-10-8-r8",
-         "10-8-10-wide-r8-digit-reversed", "9-11-9-fused-r8", "10-8-10-wide-fused-r8", "11-4-11-wide-r8",
-         "10-10-10-wide-r8"])
+         "10-8-10-all", "10-8-10-none", "9-8-9-wide-fused"])
 def test_parity_persistent_passes(orc, radices, flags, variant):
     """complex128 from 2^26 on, every kernel variant set through
     efft_plan_set_variant: the persistent strided passes that copy the next
     tile's inputs into shared memory while the current tile finishes (every
     middle-pass radix 2^8..2^11 on 4096-element tiles, the wide first pass,
-    the swapping and the strided last passes), the folded digit swap, the
-    wide first-pass tiles, and the radix-8 register stages (8 values per
-    thread) of every pass kind, on and off; against the full oracle, in
-    natural or digit-reversed order."""
+    the swapping and the strided last passes), the folded digit swap and the
+    wide first-pass tiles, on and off; against the full oracle, in natural or
+    digit-reversed order."""
     import paper_1409_5757_gb300 as efft
     e = sum(radices)
     N = 1 << e
@@ -398,13 +392,11 @@ def test_parity_persistent_passes(orc, radices, flags, variant):
     t = torch.from_numpy(x).cuda()
     p = efft.Plan(N, efft.EFFT_C128, -1, flags, radices=radices)
     got_v = p.set_variant(*variant)
-    for k, want in zip(("wide", "fused_swap", "persistent", "radix8"), variant):
+    for k, want in zip(("wide", "fused_swap", "persistent"), variant):
         if want == 0:
             assert got_v[k] == 0, (k, got_v)
     if variant[2] == 1:
         assert got_v["persistent"] == 1
-    if variant[3] == 1:
-        assert got_v["radix8"] == 1
     p.execute(t.data_ptr(), torch.cuda.current_stream().cuda_stream)
     torch.cuda.synchronize()
     got = t.cpu().numpy()
