@@ -489,6 +489,10 @@ def run_ours(args, wl):
         rad = [int(v) for v in args.radices.split(",")] if args.radices else None
         fwd = efft.Plan(N, code, -1, 0 if rad else tune, radices=rad)
         inv = efft.Plan(N, code, +1, norm_flag | (0 if rad else tune), radices=rad)
+        if args.variant:
+            knobs = [int(v) for v in args.variant.split(",")]
+            fwd.set_variant(*knobs)
+            inv.set_variant(*knobs)
     fpt = flops_real(2 * N) if real else flops(N)  # flop per transform
     stream = torch.cuda.current_stream(dev)
     sp = stream.cuda_stream
@@ -611,6 +615,7 @@ def run_ours(args, wl):
                 "peak_kind": "152 SMs x 128 FP32 lanes x 2070 MHz (maximum SM clock)"}
     launches = sum(v[1] for v in prof.values())
     radices_now = fwd.radices()
+    variant_now = fwd.variant()
     floor_gbs = world * tps * 2 * N * S / (ms_per_step * 1e-3) / 1e9
 
     # the FP32 form against the FP64 form at the same N (complex64 workloads)
@@ -728,7 +733,7 @@ def run_ours(args, wl):
             "dtype": (DTYPE_NAME_REAL if real else DTYPE_NAME)[wl["dtype"]], "data": "synthetic",
             "config": config_of(wl),
             "hbm_gbs": hbm_gbs, "hbm_passes_per_transform": hbm_passes, "floor_equivalent_gbs": floor_gbs,
-            "radices_log2": radices_now,
+            "radices_log2": radices_now, "variant": variant_now,
             "fp64_form_same_n": same_n_c128, "fp32_form": fp32,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "clocks": clocks, "accuracy": accuracy, "impl": "ours",
@@ -995,6 +1000,9 @@ def main():
                     help="plans with EFFT_FLAG_AUTOTUNE (measured radix schedules; c5 always tunes)")
     ap.add_argument("--radices", default=None,
                     help="explicit schedule, log2 radices comma-separated (profiling of one kernel variant)")
+    ap.add_argument("--variant", default=None,
+                    help="kernel variant knobs wide,fused_swap,persistent (each -1 rule, 0 off, 1 on; "
+                         "efft_plan_set_variant) for measuring one variant")
     ap.add_argument("--no-compare", action="store_true",
                     help="complex64 workloads: skip the complex128 run at the same N")
     ap.add_argument("--no-fp32-form", action="store_true",
