@@ -328,9 +328,15 @@ __device__ __forceinline__ void mixm_odd_stage(const typename P::V* in, typename
   }
 }
 
+// Three CTAs per SM where shared memory allows (a 1536-element complex128
+// tile takes 62 KiB with its tables): the register budget then holds every
+// variant at 80 registers without spills, and 24 warps per SM hide more of
+// the latency and barrier stalls than 16.
+constexpr int kMixmMinBlocks = 3;
+
 // Dynamic shared memory: two padded buffers of C*R values, then R roots.
 template <class P, int M>
-__global__ void __launch_bounds__(kMixThreads, 2) efft_pass_mixm(void* __restrict__ data, const MixArgs a) {
+__global__ void __launch_bounds__(kMixThreads, kMixmMinBlocks) efft_pass_mixm(void* __restrict__ data, const MixArgs a) {
   typedef typename P::V V;
   constexpr int KIND = MID;
   if (a.ptrs) data = a.ptrs[blockIdx.y];
