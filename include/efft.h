@@ -217,8 +217,8 @@ int efft_plan_create_with_radices(efft_plan_t* out, uint64_t n, int dtype, int s
  *    switched the other way where it changes the passes (kept when faster):
  *    the tile width of the strided first pass (complex64: also of the 2^11
  *    middle pass) doubled or not, the digit swap folded into the middle pass
- *    or not, the persistent prefetching pass kernels or not (the last two
- *    complex128 only);
+ *    or not, the persistent prefetching pass kernels or not (these two
+ *    complex128 only), the TMA-fed first pass or not (complex64 only);
  *  - n = M * 2^e, M > 1: every outer radix 2^a of the (2^a, M * 2^b, 2^a)
  *    schedule that efft_plan_create accepts, and one pass when n <= 2048.
  * Each candidate is run on `scratch` (n*S bytes of the caller's device
@@ -244,6 +244,7 @@ typedef struct efft_candidate {
   int wide;             /* 1: the wide strided tiles (see efft_plan_autotune)   */
   int fused_swap;       /* 1: digit swap folded into the middle pass            */
   int persistent;       /* 1: persistent prefetching pass kernels               */
+  int tma;              /* 1: complex64 wide first pass fed by TMA copies       */
   double ms;            /* median time of one execute (milliseconds)            */
 } efft_candidate;
 
@@ -257,7 +258,7 @@ int efft_plan_autotune_candidates(efft_plan_t plan, void* scratch, void* stream,
 
 /* The kernel variant a plan runs (each 0 or 1; see efft_candidate).  Any
  * pointer may be NULL.  Errors: INVALID_PLAN. */
-int efft_plan_variant(efft_plan_t plan, int* wide, int* fused_swap, int* persistent);
+int efft_plan_variant(efft_plan_t plan, int* wide, int* fused_swap, int* persistent, int* tma);
 
 /* Switch a plan's kernel variant, keeping its schedule (e.g. to pin a choice
  * an earlier efft_plan_autotune_candidates measured).  Each knob: -1 the
@@ -267,7 +268,19 @@ int efft_plan_variant(efft_plan_t plan, int* wide, int* fused_swap, int* persist
  * A real-data plan switches its complex plan.
  * Errors: INVALID_PLAN; INVALID_FLAGS for a knob outside -1..1;
  * UNSUPPORTED for a plan of N = M * 2^e (M > 1) with a knob other than -1. */
-int efft_plan_set_variant(efft_plan_t plan, int wide, int fused_swap, int persistent);
+int efft_plan_set_variant(efft_plan_t plan, int wide, int fused_swap, int persistent, int tma);
+
+/*
+ * Synchronise `stream`, then report whether a kernel of one of the plan's
+ * earlier executes gave up a bounded device wait: EFFT_ERR_TIMEOUT if so
+ * (that execute's output is incomplete; the record is cleared), else EFFT_OK.
+ * The only device waits in the library are those of the complex64 first
+ * pass fed by TMA copies (the `tma` variant), which waits on an mbarrier in
+ * shared memory for its copies and, when they do not complete within about
+ * 2^24 polls, records the timeout in the execute's state word and returns.
+ * Errors: INVALID_PLAN, CUDA.
+ */
+int efft_execute_check(efft_plan_t plan, void* stream);
 
 /* Destroy a plan and free its device tables, after waiting for the
  * executes still using its state words.  The paper's ~EFFT_Transform()

@@ -45,7 +45,8 @@ _vp = ctypes.c_void_p
 class EfftCandidate(ctypes.Structure):
     """efft_candidate of include/efft.h."""
     _fields_ = [("npasses", ctypes.c_int), ("radices", ctypes.c_uint64 * 4), ("wide", ctypes.c_int),
-                ("fused_swap", ctypes.c_int), ("persistent", ctypes.c_int), ("ms", ctypes.c_double)]
+                ("fused_swap", ctypes.c_int), ("persistent", ctypes.c_int), ("tma", ctypes.c_int),
+                ("ms", ctypes.c_double)]
 
 
 
@@ -74,8 +75,9 @@ _SIGNATURES = {
     "efft_plan_autotune_candidates": (ctypes.c_int, [_vp, _vp, _vp, ctypes.POINTER(EfftCandidate), ctypes.c_int,
                                                      ctypes.POINTER(ctypes.c_int)]),
     "efft_plan_variant": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
-                                         ctypes.POINTER(ctypes.c_int)]),
-    "efft_plan_set_variant": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+                                         ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+    "efft_plan_set_variant": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    "efft_execute_check": (ctypes.c_int, [_vp, _vp]),
     "efft_batch_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.POINTER(ctypes.c_uint64), ctypes.c_int,
                                          ctypes.c_int, ctypes.c_int, ctypes.c_uint32]),
     "efft_batch_execute": (ctypes.c_int, [_vp, ctypes.POINTER(_vp), _vp]),
@@ -203,21 +205,27 @@ class Plan:
         _check(_lib().efft_plan_autotune_candidates(self._h, _vp(scratch_ptr), _vp(stream), arr, cap,
                                                     ctypes.byref(nc)), "efft_plan_autotune_candidates")
         return [{"radices": [int(arr[c].radices[j]) for j in range(arr[c].npasses)], "wide": arr[c].wide,
-                 "fused_swap": arr[c].fused_swap, "persistent": arr[c].persistent, "ms": arr[c].ms}
+                 "fused_swap": arr[c].fused_swap, "persistent": arr[c].persistent, "tma": arr[c].tma,
+                 "ms": arr[c].ms}
                 for c in range(min(nc.value, cap))]
 
     def variant(self) -> dict:
         """efft_plan_variant: the kernel variant the plan runs."""
-        w, f, pp = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
-        _check(_lib().efft_plan_variant(self._h, ctypes.byref(w), ctypes.byref(f), ctypes.byref(pp)),
-               "efft_plan_variant")
-        return {"wide": w.value, "fused_swap": f.value, "persistent": pp.value}
+        w, f, pp, tm = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(_lib().efft_plan_variant(self._h, ctypes.byref(w), ctypes.byref(f), ctypes.byref(pp),
+                                        ctypes.byref(tm)), "efft_plan_variant")
+        return {"wide": w.value, "fused_swap": f.value, "persistent": pp.value, "tma": tm.value}
 
-    def set_variant(self, wide: int = -1, fused_swap: int = -1, persistent: int = -1) -> dict:
+    def set_variant(self, wide: int = -1, fused_swap: int = -1, persistent: int = -1, tma: int = -1) -> dict:
         """efft_plan_set_variant (-1 rule, 0 off, 1 on); returns variant()."""
-        _check(_lib().efft_plan_set_variant(self._h, int(wide), int(fused_swap), int(persistent)),
+        _check(_lib().efft_plan_set_variant(self._h, int(wide), int(fused_swap), int(persistent), int(tma)),
                "efft_plan_set_variant")
         return self.variant()
+
+    def check(self, stream: int = 0) -> int:
+        """efft_execute_check: synchronise `stream` and return the status of
+        the plan's earlier executes' device waits (0 or EFFT_ERR_TIMEOUT)."""
+        return _lib().efft_execute_check(self._h, _vp(stream))
 
     def profile(self, enable: bool = True) -> None:
         """Start (clearing old records) or stop per-launch CUDA-event timing."""

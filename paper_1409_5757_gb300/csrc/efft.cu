@@ -5,6 +5,7 @@
 // mixed-radix passes), owns the O(sqrt N) twiddle tables that the paper's
 // constructor precomputes once (Sec. 3.1, Listing 3) and a 16-byte state
 // word; an execute enqueues the pass kernels on the caller's stream.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -346,6 +347,11 @@ void apply_schedule(efft_plan_s* p, const int* r, int np, const Variant& v) {
     l.smem = (le + le / 16 + 1) * eb;
     p->permute = false;
   }
+  // complex64: the wide first pass (2^10 rows, 16 columns) fed by TMA copies
+  if (!c128 && on(v.tma, kTmaRule)) {
+    Pass& f = p->pass[0];
+    f.tma = np >= 2 && f.kind == FIRST && f.wide && f.log2R == 10 && f.log2C == kLog2CtaWideC64 - 10;
+  }
   // persistent prefetching kernels for the complex128 strided passes with a
   // tile shape they are built for.  The rule (measured, 2^28..2^33): they
   // pay for the one-CTA-per-SM passes -- the strided last pass at every
@@ -375,13 +381,48 @@ void apply_schedule(efft_plan_s* p, const int* r, int np, const Variant& v) {
 
 Variant realised_variant(const efft_plan_s* p) {
   Variant v;
-  v.wide = v.fuse = v.pf = 0;
+  v.wide = v.fuse = v.pf = v.tma = 0;
   for (int j = 0; j < p->npasses; ++j) {
     if (p->pass[j].wide) v.wide = 1;
     if (p->pass[j].swap) v.fuse = 1;
     if (p->pass[j].pf) v.pf = 1;
+    if (p->pass[j].tma) v.tma = 1;
   }
   return v;
+}
+
+// cuTensorMapEncodeTiled through the runtime's driver entry-point query (no
+// link-time libcuda); NULL when the driver does not offer it.
+typedef CUresult (*EncodeTiled)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+static EncodeTiled encode_tiled() {
+  static std::once_flag once;
+  static EncodeTiled fn = nullptr;
+  std::call_once(once, [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiled>(f);
+    cudaGetLastError();
+  });
+  return fn;
+}
+
+// The tensor map of a complex64 first pass of 2^10 rows: the array as
+// [1024][s] 8-byte elements (s = N / 1024), 16 x 256 boxes, no swizzle.
+static bool first_pass_map(CUtensorMap* map, void* data, int log2s) {
+  EncodeTiled fn = encode_tiled();
+  if (!fn || (reinterpret_cast<uintptr_t>(data) & 15u)) return false;
+  const cuuint64_t dims[2] = {1ull << log2s, 1024};
+  const cuuint64_t strides[1] = {(1ull << log2s) * 8};
+  const cuuint32_t box[2] = {16, 256};
+  const cuuint32_t estr[2] = {1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, data, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+         CUDA_SUCCESS;
 }
 
 template <class P, int KIND, int CTA>
@@ -591,6 +632,20 @@ cudaError_t launch_pass(const efft_plan_s* p, const Pass& ps, void* data, const 
   if (P::kElemBytes == 16 && ps.kind == LASTS) {
     const bool ok = fx_launch_df2_lasts(ps.log2R, grid, block, ps.smem, st, data, a);
     return ok ? cudaGetLastError() : cudaErrorInvalidConfiguration;
+  }
+  if (P::kElemBytes == 8 && ps.tma && !bt.ptrs) {
+    CUtensorMap map;
+    if (first_pass_map(&map, data, ps.log2s)) {
+      // word 3 of the state: this execute's record of an expired device wait
+      if (cudaMemsetAsync(bt.state + 3, 0, 4, st) != cudaSuccess) return cudaErrorInvalidValue;
+      a.ntiles = ps.grid;
+      a.inject_timeout = fault_injected("tma_wait") ? 1u : 0u;
+      const uint64_t g = std::min<uint64_t>(ps.grid, (uint64_t)(p->sms > 0 ? p->sms : 152));
+      const bool ok = fx_launch_f32_tma(dim3((unsigned)g, 1), st, data, a, &map);
+      return ok ? cudaGetLastError() : cudaErrorInvalidConfiguration;
+    }
+    // no tensor map (no driver entry point, or a buffer not 16-byte
+    // aligned): the same pass on the kernel that loads its own tiles
   }
   if (ps.wide) {
     const bool ok = (P::kElemBytes == 16) ? fx_launch_df2_wide(ps.log2R, grid, block, ps.smem, st, data, a)
@@ -1112,6 +1167,32 @@ int efft_execute_host_stream(const efft_plan_t* plans, int nplans, void* const* 
   if (sin) cudaStreamDestroy(sin);
   if (sout) cudaStreamDestroy(sout);
   if (rc != EFFT_OK) cudaGetLastError();
+  return rc;
+}
+
+int efft_execute_check(efft_plan_t plan, void* stream) {
+  if (!plan_is_live(plan)) return EFFT_ERR_INVALID_PLAN;
+  if (plan->real) plan = plan->inner;
+  DeviceGuard g(plan->device);
+  if (!g.ok) return EFFT_ERR_CUDA;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (cudaStreamSynchronize(st) != cudaSuccess) {
+    cudaGetLastError();
+    return EFFT_ERR_CUDA;
+  }
+  if (plan->dtype != EFFT_C64) return EFFT_OK;  // complex128 kernels have no device waits
+  uint32_t words[4 * kStateRing];
+  if (cudaMemcpy(words, plan->state, sizeof(words), cudaMemcpyDeviceToHost) != cudaSuccess) {
+    cudaGetLastError();
+    return EFFT_ERR_CUDA;
+  }
+  int rc = EFFT_OK;
+  for (int k = 0; k < kStateRing; ++k)
+    if (words[4 * k + 3] == (uint32_t)EFFT_ERR_TIMEOUT) rc = EFFT_ERR_TIMEOUT;
+  if (rc != EFFT_OK && cudaMemset(plan->state, 0, sizeof(words)) != cudaSuccess) {
+    cudaGetLastError();
+    return EFFT_ERR_CUDA;
+  }
   return rc;
 }
 

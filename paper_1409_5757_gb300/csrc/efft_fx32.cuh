@@ -1,9 +1,11 @@
 // efft_fx32.cuh -- the complex64 pass kernel for radix R = 2^10 as two
 // radix-32 stages (32 values per thread).  Included by efft_fx_f32.cu only.
 #pragma once
+#include <cuda.h>  // CUtensorMap (the struct only; no driver call is made here)
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "../../include/efft.h"
 #include "efft_kernels.cuh"
 
 namespace efft {
@@ -169,5 +171,162 @@ __global__ void __launch_bounds__(32 << LC, MINB) efft_pass_fx32(void* __restric
 // Dynamic shared memory of efft_pass_fx32 with 2^LC columns: 1024 * 2^LC
 // values plus one pad slot per 32.
 constexpr int fx32_smem_bytes(int LC) { return ((1024 << LC) + (1024 << LC) / 32) * 8; }
+
+// ----------------------------------------------------------------------------
+// The wide complex64 first pass of 2^10 rows (the kernel above with C = 16,
+// 512 threads, one CTA per SM), its tiles brought into shared memory by the
+// tensor-memory accelerator.  The pass's columns j < s (s = N / 1024) with
+// rows r < 1024 at element j + r s are the 2-D tensor [1024][s] of 8-byte
+// elements; a tile is its 16 x 1024 box, four TMA copies of 16 x 256 (128
+// bytes per row, so the column coordinate, a multiple of 16, is 128-byte
+// aligned), completed on one mbarrier in shared memory.  The CTA is
+// persistent: as soon as every thread has read the stage-1 inputs the
+// buffer is free, and one thread issues the copies of its next tile, which
+// land while stage 1, the pass twiddle and the stores of this tile run.
+// Stage 0 reads the dense box (bank-conflict free: a warp's 32 lanes read
+// two 128-byte rows), the exchange uses the padded layout of the kernel
+// above.  Same arithmetic, same results as efft_pass_fx32<FIRST, 4>.
+//
+// The mbarrier wait is bounded (kTmaSpinLimit polls of try_wait): on expiry
+// the CTA records EFFT_ERR_TIMEOUT in word 3 of the execute's state (read by
+// efft_execute_check), waits once more, bounded, for the copies it issued,
+// and returns.  a.inject_timeout (host-side fault injection) arms the
+// barrier without issuing copies and polls only 1024 times.
+// ----------------------------------------------------------------------------
+constexpr uint32_t kTmaSpinLimit = 1u << 24;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// bounded wait for the phase `parity` of `bar`; true when it completed
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint32_t limit) {
+  for (uint32_t n = 0; n < limit; ++n)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+// generic-proxy accesses of shared memory before async-proxy (TMA) writes
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+      ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+template <int LC>
+__global__ void __launch_bounds__(32 << LC, 1)
+efft_pass_fx32_tma(void* __restrict__ data, const PassArgs a, const __grid_constant__ CUtensorMap tmap) {
+  typedef PolicyF32 P;
+  typedef float2 V;
+  constexpr int R = 1024, C = 1 << LC, TILE_BYTES = R * C * 8, BOX_ROWS = 256;
+  static_assert(C * 8 == 128, "a tile row is one 128-byte box row");
+  // the copies' destination is aligned up to 1024 bytes (the dynamic
+  // allocation carries that much slack)
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  unsigned char* const tile_base =
+      smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+  V* sm = reinterpret_cast<V*>(tile_base);
+  __shared__ float4 vtw[32 * C];
+  __shared__ __align__(8) uint64_t bar;
+  auto slot = [](int p, int col) {
+    const int raw = (p << LC) + col;
+    return raw + ((raw >> 8) << 3);
+  };
+  const int tid = threadIdx.x;
+  const int c = tid & (C - 1);
+  const int t = tid >> LC;
+  const uint32_t limit = a.inject_timeout ? 1024u : kTmaSpinLimit;
+  if (tid == 0) {
+    mbar_init(&bar, 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+
+  // thread 0: arm the barrier with the tile's bytes and issue its copies
+  auto issue = [&](uint64_t tl) {
+    fence_proxy_async_smem();
+    mbar_expect_tx(&bar, TILE_BYTES);
+    if (!a.inject_timeout)
+#pragma unroll
+      for (int q = 0; q < R / BOX_ROWS; ++q)
+        tma_load_2d(tile_base + q * BOX_ROWS * C * 8, &tmap, (int)(tl * C), q * BOX_ROWS, &bar);
+  };
+  uint64_t tile = blockIdx.x;
+  uint32_t phase = 0;
+  bool failed = false;
+  if (tid == 0 && tile < a.ntiles) issue(tile);
+
+  for (; tile < a.ntiles; tile += gridDim.x) {
+    __syncthreads();  // the previous tile's epilogue no longer reads vtw
+    const uint64_t jcol = tile * C + c, m = jcol;
+    {
+      const int cc = tid & (C - 1), k2 = tid >> LC;
+      vtw[k2 * C + cc] = twiddle_N(a, (tile * C + cc) * (uint64_t)(32 * k2));
+    }
+    const float4 wt = twiddle_N(a, m * (uint64_t)t);
+
+    failed = !mbar_wait_bounded(&bar, phase, limit);
+    if (__syncthreads_or(failed)) {
+      failed = true;
+      break;
+    }
+    phase ^= 1u;
+
+    V v[32];
+    // ---- stage 0: rows t + 32 j of the dense box ----
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      v[j] = sm[((t + 32 * j) << LC) + c];
+      if (a.conj_in) v[j].y = -v[j].y;
+    }
+    __syncthreads();  // the dense box is read before the exchange overwrites it
+    dif32_regs<P>(v);
+#pragma unroll
+    for (int u = 1; u < 32; ++u) {
+      const int e = t * bitrev_c(u, 5);
+      v[u] = P::mul_tw(v[u], __ldg(a.w2048 + 2 * e));
+    }
+#pragma unroll
+    for (int u = 0; u < 32; ++u) sm[slot(32 * bitrev_c(u, 5) + t, c)] = v[u];
+    __syncthreads();
+
+    // ---- stage 1: thread q = t reads positions 32 q + j ----
+#pragma unroll
+    for (int j = 0; j < 32; ++j) v[j] = sm[slot(32 * t + j, c)];
+    __syncthreads();  // every stage-1 read is done: the buffer takes the next tile
+    if (tid == 0 && tile + gridDim.x < a.ntiles) issue(tile + gridDim.x);
+    dif32_regs<P>(v);
+
+    // ---- epilogue: register u holds X[q + 32 k2], k2 = bitrev5(u) ----
+#pragma unroll
+    for (int u = 0; u < 32; ++u) {
+      const int k2 = bitrev_c(u, 5);
+      const int k = t + 32 * k2;
+      v[u] = P::pass_tw(v[u], wt, vtw[k2 * C + c]);
+      Mem<P, FIRST>::store(data, jcol + ((uint64_t)k << a.log2s), v[u], 0, a.conj_out, false);
+    }
+  }
+  if (failed) {
+    if (tid == 0 && a.state) atomicOr(const_cast<uint32_t*>(a.state) + 3, (uint32_t)EFFT_ERR_TIMEOUT);
+    // the copies this CTA issued must land before its shared memory is reused
+    mbar_wait_bounded(&bar, phase, limit);
+  }
+}
+
+constexpr int fx32_tma_smem_bytes() { return fx32_smem_bytes(4) + 1024; }
 
 }  // namespace efft

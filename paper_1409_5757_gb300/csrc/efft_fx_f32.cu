@@ -57,7 +57,17 @@ cudaError_t fx_set_attrs_f32() {
   const cudaError_t m = cudaFuncSetAttribute(efft_pass_fx<PolicyF32, MID, 11, kLog2CtaWideC64 - 11, 1>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (elems + elems / 16 + 1) * 8);
   if (m != cudaSuccess && err == cudaSuccess) err = m;
+  const cudaError_t tm = cudaFuncSetAttribute(efft_pass_fx32_tma<kLog2CtaWideC64 - 10>,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize, fx32_tma_smem_bytes());
+  if (tm != cudaSuccess && err == cudaSuccess) err = tm;
   return err;
+}
+
+bool fx_launch_f32_tma(dim3 grid, cudaStream_t st, void* data, const PassArgs& a, const void* tensor_map) {
+  constexpr int LC = kLog2CtaWideC64 - 10;
+  const CUtensorMap& map = *static_cast<const CUtensorMap*>(tensor_map);
+  efft_pass_fx32_tma<LC><<<grid, 32 << LC, fx32_tma_smem_bytes(), st>>>(data, a, map);
+  return true;
 }
 
 bool fx_launch_f32_wide(int kind, int log2R, dim3 grid, cudaStream_t st, void* data, const PassArgs& a) {

@@ -33,6 +33,9 @@ constexpr int kFuseMaxLog2N = 30;
 // this size on (the wide first pass up to kPersistFirstMaxLog2N)
 constexpr int kPersistMinLog2N = 26;
 constexpr int kPersistFirstMaxLog2N = 31;
+// complex64 wide first pass fed by TMA copies: the size rule (on wherever
+// the pass shape allows it)
+constexpr bool kTmaRule = false;
 
 // One pass of the schedule and its launch shape.
 struct Pass {
@@ -41,6 +44,7 @@ struct Pass {
   int swap;   // middle pass that also swaps the outer digits: log2 of its
               // T x T column tile side (0: no swap)
   bool pf;    // complex128 strided pass run by the persistent prefetching kernel
+  bool tma;   // complex64 wide first pass fed by TMA copies (persistent)
   uint64_t grid;
   int threads;
   size_t smem;
@@ -88,8 +92,9 @@ struct StateRing {
 //        last pass is strided (no separate swap sweep);
 //  pf    complex128 strided passes as persistent kernels that prefetch the
 //        next tile.
+//  tma   complex64 wide first pass as a persistent kernel fed by TMA copies.
 struct Variant {
-  int wide = -1, fuse = -1, pf = -1;
+  int wide = -1, fuse = -1, pf = -1, tma = -1;
 };
 
 // A tuned schedule: log2 R_0 .. log2 R_{np-1} and the variant for a power of

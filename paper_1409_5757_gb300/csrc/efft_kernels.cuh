@@ -49,6 +49,8 @@ struct PassArgs {
                          // (s_odd = M); 1 for power-of-two N
   uint64_t ntiles;       // persistent kernels: tiles per transform (a swapping
                          // pass: tile pairs)
+  uint32_t inject_timeout;  // host-side fault injection: a TMA pass arms its
+                            // barrier without copies (its bounded wait expires)
 };
 
 // Shared-memory slot of (position p, column c): one pad slot per 16 keeps the
@@ -899,5 +901,9 @@ bool fx_launch_f32(int kind, int log2R, dim3 grid, dim3 block, size_t smem, cuda
 // the middle pass of R = 2^11 rows (8 columns, 64 bytes per row segment).
 constexpr int kLog2CtaWideC64 = 14;
 bool fx_launch_f32_wide(int kind, int log2R, dim3 grid, cudaStream_t st, void* data, const PassArgs& a);
+// the wide complex64 first pass (R = 2^10, 16 columns) as a persistent kernel
+// fed by TMA copies; tensor_map: a CUtensorMap of the array as [1024][N/1024]
+// 8-byte elements with 16 x 256 boxes.  `grid` CTAs walk a.ntiles tiles.
+bool fx_launch_f32_tma(dim3 grid, cudaStream_t st, void* data, const PassArgs& a, const void* tensor_map);
 
 }  // namespace efft

@@ -49,6 +49,7 @@ efft_candidate describe(const efft_plan_s* p, double ms) {
   c.wide = v.wide;
   c.fused_swap = v.fuse;
   c.persistent = v.pf;
+  c.tma = v.tma;
   c.ms = ms;
   return c;
 }
@@ -59,7 +60,7 @@ std::vector<int> signature(const efft_plan_s* p) {
   std::vector<int> s = {p->npasses, p->permute ? 1 : 0};
   for (int j = 0; j < p->npasses; ++j) {
     const Pass& q = p->pass[j];
-    s.insert(s.end(), {q.kind, q.log2R, q.log2C, q.wide ? 1 : 0, q.swap, q.pf ? 1 : 0, (int)q.R_int});
+    s.insert(s.end(), {q.kind, q.log2R, q.log2C, q.wide ? 1 : 0, q.swap, q.pf ? 1 : 0, q.tma ? 1 : 0, (int)q.R_int});
   }
   return s;
 }
@@ -194,9 +195,9 @@ int autotune_impl(efft_plan_s* p, void* scratch, cudaStream_t st, efft_candidate
   }
   // 2. power of two: each variant knob of the fastest schedule switched the
   // other way, where that changes the launches; kept when faster
-  for (int knob = 0; rc == EFFT_OK && p->odd == 1 && best_ms >= 0 && knob < 3; ++knob) {
+  for (int knob = 0; rc == EFFT_OK && p->odd == 1 && best_ms >= 0 && knob < 4; ++knob) {
     Tuned c = best;
-    int* k = (knob == 0) ? &c.v.wide : (knob == 1) ? &c.v.fuse : &c.v.pf;
+    int* k = (knob == 0) ? &c.v.wide : (knob == 1) ? &c.v.fuse : (knob == 2) ? &c.v.pf : &c.v.tma;
     apply(p, best);
     const std::vector<int> s0 = signature(p);
     *k = 1 - *k;
@@ -258,16 +259,18 @@ int efft_plan_autotune(efft_plan_t plan, void* scratch, void* stream, int* cand_
   return rc;
 }
 
-int efft_plan_set_variant(efft_plan_t plan, int wide, int fused_swap, int persistent) {
+int efft_plan_set_variant(efft_plan_t plan, int wide, int fused_swap, int persistent, int tma) {
   if (!plan_is_live(plan)) return EFFT_ERR_INVALID_PLAN;
   if (plan->real) plan = plan->inner;
-  for (int k : {wide, fused_swap, persistent})
+  for (int k : {wide, fused_swap, persistent, tma})
     if (k < -1 || k > 1) return EFFT_ERR_INVALID_FLAGS;
-  if (plan->odd > 1) return (wide == -1 && fused_swap == -1 && persistent == -1) ? EFFT_OK : EFFT_ERR_UNSUPPORTED;
+  if (plan->odd > 1)
+    return (wide == -1 && fused_swap == -1 && persistent == -1 && tma == -1) ? EFFT_OK : EFFT_ERR_UNSUPPORTED;
   Variant v;
   v.wide = wide;
   v.fuse = fused_swap;
   v.pf = persistent;
+  v.tma = tma;
   int r[kMaxPasses] = {0, 0, 0, 0};
   const int np = plan->npasses;
   for (int j = 0; j < np; ++j) r[j] = plan->pass[j].log2R;
@@ -275,13 +278,14 @@ int efft_plan_set_variant(efft_plan_t plan, int wide, int fused_swap, int persis
   return EFFT_OK;
 }
 
-int efft_plan_variant(efft_plan_t plan, int* wide, int* fused_swap, int* persistent) {
+int efft_plan_variant(efft_plan_t plan, int* wide, int* fused_swap, int* persistent, int* tma) {
   if (!plan_is_live(plan)) return EFFT_ERR_INVALID_PLAN;
   if (plan->real) plan = plan->inner;
   const Variant v = realised_variant(plan);
   if (wide) *wide = v.wide;
   if (fused_swap) *fused_swap = v.fuse;
   if (persistent) *persistent = v.pf;
+  if (tma) *tma = v.tma;
   return EFFT_OK;
 }
 

@@ -103,11 +103,11 @@ def test_autotune_scans_variants(orc, name, e):
     assert [[int(r).bit_length() - 1 for r in c["radices"]] for c in res[:ns]] == schedule_candidates(e)
     best = min(res, key=lambda c: c["ms"])
     assert plan.radices() == [int(r).bit_length() - 1 for r in best["radices"]]
-    assert plan.variant() == {k: best[k] for k in ("wide", "fused_swap", "persistent")}
+    assert plan.variant() == {k: best[k] for k in ("wide", "fused_swap", "persistent", "tma")}
     # each variant candidate differs from the others (a knob that changes no
     # launch of the fastest schedule is not measured)
-    keys = [(c["wide"], c["fused_swap"], c["persistent"]) for c in res[ns:]]
-    assert len(set(keys)) == len(keys) <= 3
+    keys = [(c["wide"], c["fused_swap"], c["persistent"], c["tma"]) for c in res[ns:]]
+    assert len(set(keys)) == len(keys) <= 4
     if name == "c128" and e >= 26 and best["radices"][0] in (512, 1024, 2048) and len(best["radices"]) == 3:
         assert any(c["fused_swap"] != res[0]["fused_swap"] for c in res) or len(keys) >= 2
     x = host_input(orc, name, N, seed=56)

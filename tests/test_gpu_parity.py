@@ -409,3 +409,54 @@ def test_parity_persistent_passes(orc, radices, flags, variant):
         q0, q1, q2 = P >> (a + b), (P >> a) & ((1 << b) - 1), P & ((1 << a) - 1)
         ref = ref[q0 + (q1 << a) + (q2 << (a + b))]
     check(got, ref, "c128", N)
+
+
+@pytest.mark.parametrize("e,sign", [(28, -1), (28, 1), (20, -1), (24, 1)])
+def test_parity_c64_tma_first_pass(orc, e, sign):
+    """complex64: the wide first pass of 2^10 rows (16 columns) as the
+    persistent kernel fed by TMA copies (efft_plan_set_variant, tma = 1; at
+    2^20 and 2^24 with the wide tiles forced, fewer tiles than SMs at 2^20):
+    against the full oracle, bit for bit against the kernel that loads its
+    own tiles (the same arithmetic), and no expired device wait."""
+    import paper_1409_5757_gb300 as efft
+    N = 1 << e
+    x = host_input(orc, "c64", N, seed=5100 + e)
+    runs = {}
+    for tma in (0, 1):
+        p = efft.Plan(N, efft.EFFT_C64, sign)
+        v = p.set_variant(1, -1, -1, tma)
+        assert v["tma"] == tma and v["wide"] == 1
+        t = torch.from_numpy(x.astype(np.complex64)).cuda()
+        p.execute(t.data_ptr(), torch.cuda.current_stream().cuda_stream)
+        assert p.check(torch.cuda.current_stream().cuda_stream) == 0
+        runs[tma] = t
+        p.destroy()
+    assert torch.equal(runs[0], runs[1])
+    got = runs[1].cpu().numpy().astype(np.complex128)
+    del runs
+    check(got, orc.fft_radix2(x, sign), "c64", N)
+
+
+def test_tma_wait_expiry_is_reported(orc, monkeypatch):
+    """The bounded device wait of the TMA-fed first pass, made to run out on
+    purpose: with EFFT_FAULT_INJECT=tma_wait the kernel arms its barrier
+    without issuing copies, gives up after 1024 polls, records the timeout
+    and returns; efft_execute_check reports EFFT_ERR_TIMEOUT once, and the
+    context stays usable (the next execute is correct)."""
+    import paper_1409_5757_gb300 as efft
+    N = 1 << 22
+    x = host_input(orc, "c64", N, seed=52)
+    p = efft.Plan(N, efft.EFFT_C64, -1)
+    assert p.set_variant(1, -1, -1, 1)["tma"] == 1
+    sp = torch.cuda.current_stream().cuda_stream
+    t = torch.from_numpy(x.astype(np.complex64)).cuda()
+    monkeypatch.setenv("EFFT_FAULT_INJECT", "tma_wait")
+    p.execute(t.data_ptr(), sp)
+    monkeypatch.delenv("EFFT_FAULT_INJECT")
+    assert p.check(sp) == 8  # EFFT_ERR_TIMEOUT
+    assert p.check(sp) == 0  # the record was cleared
+    t = torch.from_numpy(x.astype(np.complex64)).cuda()
+    p.execute(t.data_ptr(), sp)
+    assert p.check(sp) == 0
+    check(t.cpu().numpy().astype(np.complex128), orc.fft_radix2(x, -1), "c64", N)
+    p.destroy()
