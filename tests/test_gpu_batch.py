@@ -298,10 +298,12 @@ def test_batch_host_stream_chain(orc, name):
     hout.free()
 
 
-def test_batch_of_256_uneven_c64(orc):
-    """256 complex64 transforms, N = 2^e with e uniform in {12..24} (seed 5):
-    bit-identical to single plans for all, the oracle for the smallest and
-    largest of each size class sampled."""
+@pytest.mark.parametrize("flags", [0, 0x4], ids=["table", "autotuned"])
+def test_batch_of_256_uneven_c64(orc, flags):
+    """256 complex64 transforms, N = 2^e with e uniform in {12..24} (seed 5),
+    with the table's schedules and with EFFT_FLAG_AUTOTUNE (the benchmark's
+    setting): bit-identical to single plans of the same flags for all, the
+    oracle for the smallest and largest sampled."""
     import paper_1409_5757_gb300 as efft
     from paper_1409_5757_gb300 import inputs
     es = np.random.default_rng(5).integers(12, 25, 256)
@@ -309,9 +311,9 @@ def test_batch_of_256_uneven_c64(orc):
     for i, t in enumerate(ts):
         inputs.fill_uniform(t, 5000 + i)
     refs = [t.clone() for t in ts]
-    efft.fft_batch_(ts)
+    efft.fft_batch_(ts, -1, flags)
     for r in refs:
-        efft.fft_(r)
+        efft.fft_(r, -1, flags)
     torch.cuda.synchronize()
     for e, t, r in zip(es, ts, refs):
         assert torch.equal(t, r), f"N=2^{e}"

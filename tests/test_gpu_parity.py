@@ -423,7 +423,9 @@ def test_parity_c64_tma_first_pass(orc, e, sign):
     x = host_input(orc, "c64", N, seed=5100 + e)
     runs = {}
     for tma in (0, 1):
-        p = efft.Plan(N, efft.EFFT_C64, sign)
+        # a first pass of 2^10 rows: the table's schedule at 2^20 and 2^28,
+        # 2^10 * 2^4 * 2^10 at 2^24
+        p = efft.Plan(N, efft.EFFT_C64, sign, radices=[10, 4, 10] if e == 24 else None)
         v = p.set_variant(1, -1, -1, tma)
         assert v["tma"] == tma and v["wide"] == 1
         t = torch.from_numpy(x.astype(np.complex64)).cuda()
