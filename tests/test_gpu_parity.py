@@ -446,7 +446,7 @@ def test_tma_wait_expiry_is_reported(orc, monkeypatch):
     and returns; efft_execute_check reports EFFT_ERR_TIMEOUT once, and the
     context stays usable (the next execute is correct)."""
     import paper_1409_5757_gb300 as efft
-    N = 1 << 22
+    N = 1 << 20  # schedule 2^10 * 2^10: a first pass of 2^10 rows
     x = host_input(orc, "c64", N, seed=52)
     p = efft.Plan(N, efft.EFFT_C64, -1)
     assert p.set_variant(1, -1, -1, 1)["tma"] == 1
