@@ -347,12 +347,10 @@ void apply_schedule(efft_plan_s* p, const int* r, int np, const Variant& v) {
     l.smem = (le + le / 16 + 1) * eb;
     p->permute = false;
   }
-  // the wide first pass fed by TMA copies: complex64 2^10 rows x 16
-  // columns; complex128 2^10 x 8 or 2^11 x 4
-  if (np >= 2 && p->pass[0].kind == FIRST && p->pass[0].wide && on(v.tma, c128 ? kTmaRuleC128 : kTmaRule)) {
+  // complex64: the wide first pass (2^10 rows, 16 columns) fed by TMA copies
+  if (!c128 && on(v.tma, kTmaRule)) {
     Pass& f = p->pass[0];
-    f.tma = c128 ? (f.log2R == 10 || f.log2R == 11) && f.log2R + f.log2C == kLog2CtaWide
-                 : f.log2R == 10 && f.log2C == kLog2CtaWideC64 - 10;
+    f.tma = np >= 2 && f.kind == FIRST && f.wide && f.log2R == 10 && f.log2C == kLog2CtaWideC64 - 10;
   }
   // persistent prefetching kernels for the complex128 strided passes with a
   // tile shape they are built for.  The rule (measured, 2^28..2^33): they
@@ -376,7 +374,7 @@ void apply_schedule(efft_plan_s* p, const int* r, int np, const Variant& v) {
         shape = (lr >= 9 && lr <= 11 && lr + lc == kLog2CtaWide);
         rule = true;
       }
-      ps.pf = shape && (pf > 0 || rule) && !ps.tma;
+      ps.pf = shape && (pf > 0 || rule);
     }
   }
 }
@@ -413,15 +411,14 @@ static EncodeTiled encode_tiled() {
   return fn;
 }
 
-// The tensor map of a first pass of R rows and C columns per tile: the
-// array as [R][w s] 8-byte words (s = N / R columns of w words: w = 1 for
-// complex64, 2 for complex128), boxes of (w C) x 256, no swizzle.
-static bool first_pass_map(CUtensorMap* map, void* data, int log2R, int log2s, int words, int C) {
+// The tensor map of a complex64 first pass of 2^10 rows: the array as
+// [1024][s] 8-byte elements (s = N / 1024), 16 x 256 boxes, no swizzle.
+static bool first_pass_map(CUtensorMap* map, void* data, int log2s) {
   EncodeTiled fn = encode_tiled();
   if (!fn || (reinterpret_cast<uintptr_t>(data) & 15u)) return false;
-  const cuuint64_t dims[2] = {(uint64_t)words << log2s, 1ull << log2R};
-  const cuuint64_t strides[1] = {((uint64_t)words << log2s) * 8};
-  const cuuint32_t box[2] = {(cuuint32_t)(words * C), 256};
+  const cuuint64_t dims[2] = {1ull << log2s, 1024};
+  const cuuint64_t strides[1] = {(1ull << log2s) * 8};
+  const cuuint32_t box[2] = {16, 256};
   const cuuint32_t estr[2] = {1, 1};
   return fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, data, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
@@ -617,24 +614,6 @@ cudaError_t launch_pass(const efft_plan_s* p, const Pass& ps, void* data, const 
   a.s_odd = (ps.kind == FIRST && p->odd > 1) ? p->odd : 1u;
   dim3 grid((unsigned)ps.grid, bt.count), block(ps.threads);
   constexpr int LOG2CTA = (P::kElemBytes == 16) ? kLog2CtaC128 : kLog2CtaC64;
-  if (ps.tma && !bt.ptrs) {
-    CUtensorMap map;
-    const int words = P::kElemBytes / 8;
-    if (first_pass_map(&map, data, ps.log2R, ps.log2s, words, 1 << ps.log2C)) {
-      // word 3 of the state: this execute's record of an expired device wait
-      // (complex128: the range scan has just cleared the whole state)
-      if (P::kElemBytes == 8 && cudaMemsetAsync(bt.state + 3, 0, 4, st) != cudaSuccess)
-        return cudaErrorInvalidValue;
-      a.ntiles = ps.grid;
-      a.inject_timeout = fault_injected("tma_wait") ? 1u : 0u;
-      const uint64_t g = std::min<uint64_t>(ps.grid, (uint64_t)(p->sms > 0 ? p->sms : 152));
-      const bool ok = (P::kElemBytes == 8) ? fx_launch_f32_tma(dim3((unsigned)g, 1), st, data, a, &map)
-                                           : fx_launch_df2_tma(ps.log2R, dim3((unsigned)g, 1), st, data, a, &map);
-      return ok ? cudaGetLastError() : cudaErrorInvalidConfiguration;
-    }
-    // no tensor map (no driver entry point, or a buffer not 16-byte
-    // aligned): the same pass on the kernel that loads its own tiles
-  }
   if (P::kElemBytes == 16 && ps.pf) {
     // persistent: at most as many CTAs (CTA pairs) as can be resident
     const int minb = (ps.log2R + ps.log2C == kLog2CtaWide) ? 1 : 2;
@@ -653,6 +632,20 @@ cudaError_t launch_pass(const efft_plan_s* p, const Pass& ps, void* data, const 
   if (P::kElemBytes == 16 && ps.kind == LASTS) {
     const bool ok = fx_launch_df2_lasts(ps.log2R, grid, block, ps.smem, st, data, a);
     return ok ? cudaGetLastError() : cudaErrorInvalidConfiguration;
+  }
+  if (P::kElemBytes == 8 && ps.tma && !bt.ptrs) {
+    CUtensorMap map;
+    if (first_pass_map(&map, data, ps.log2s)) {
+      // word 3 of the state: this execute's record of an expired device wait
+      if (cudaMemsetAsync(bt.state + 3, 0, 4, st) != cudaSuccess) return cudaErrorInvalidValue;
+      a.ntiles = ps.grid;
+      a.inject_timeout = fault_injected("tma_wait") ? 1u : 0u;
+      const uint64_t g = std::min<uint64_t>(ps.grid, (uint64_t)(p->sms > 0 ? p->sms : 152));
+      const bool ok = fx_launch_f32_tma(dim3((unsigned)g, 1), st, data, a, &map);
+      return ok ? cudaGetLastError() : cudaErrorInvalidConfiguration;
+    }
+    // no tensor map (no driver entry point, or a buffer not 16-byte
+    // aligned): the same pass on the kernel that loads its own tiles
   }
   if (ps.wide) {
     const bool ok = (P::kElemBytes == 16) ? fx_launch_df2_wide(ps.log2R, grid, block, ps.smem, st, data, a)
@@ -1187,6 +1180,7 @@ int efft_execute_check(efft_plan_t plan, void* stream) {
     cudaGetLastError();
     return EFFT_ERR_CUDA;
   }
+  if (plan->dtype != EFFT_C64) return EFFT_OK;  // complex128 kernels have no device waits
   uint32_t words[4 * kStateRing];
   if (cudaMemcpy(words, plan->state, sizeof(words), cudaMemcpyDeviceToHost) != cudaSuccess) {
     cudaGetLastError();

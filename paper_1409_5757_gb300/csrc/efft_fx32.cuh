@@ -1,6 +1,7 @@
 // efft_fx32.cuh -- the complex64 pass kernel for radix R = 2^10 as two
 // radix-32 stages (32 values per thread).  Included by efft_fx_f32.cu only.
 #pragma once
+#include <cuda.h>  // CUtensorMap (the struct only; no driver call is made here)
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -192,6 +193,40 @@ constexpr int fx32_smem_bytes(int LC) { return ((1024 << LC) + (1024 << LC) / 32
 // and returns.  a.inject_timeout (host-side fault injection) arms the
 // barrier without issuing copies and polls only 1024 times.
 // ----------------------------------------------------------------------------
+constexpr uint32_t kTmaSpinLimit = 1u << 24;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// bounded wait for the phase `parity` of `bar`; true when it completed
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint32_t limit) {
+  for (uint32_t n = 0; n < limit; ++n)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+// generic-proxy accesses of shared memory before async-proxy (TMA) writes
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+      ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
 template <int LC>
 __global__ void __launch_bounds__(32 << LC, 1)
 efft_pass_fx32_tma(void* __restrict__ data, const PassArgs a, const __grid_constant__ CUtensorMap tmap) {

@@ -136,28 +136,6 @@ bool fx_launch_df2_pf(int kind, int log2R, int log2C, int swap, dim3 grid, dim3 
   return e == cudaSuccess;
 }
 
-// TMA-fed wide first pass: the padded tile plus 1024 bytes of alignment slack
-constexpr int kTmaSmem = ((1 << kLog2CtaWide) + (1 << kLog2CtaWide) / 16 + 1) * 16 + 1024;
-
-bool fx_launch_df2_tma(int log2R, dim3 grid, cudaStream_t st, void* data, const PassArgs& a, const void* tensor_map) {
-  const CUtensorMap& map = *static_cast<const CUtensorMap*>(tensor_map);
-  if (log2R == 10) efft_pass_tma_df2<10, kLog2CtaWide - 10><<<grid, 512, kTmaSmem, st>>>(data, a, map);
-  else if (log2R == 11) efft_pass_tma_df2<11, kLog2CtaWide - 11><<<grid, 512, kTmaSmem, st>>>(data, a, map);
-  else return false;
-  return true;
-}
-
-namespace {
-void attrs_tma(cudaError_t& err) {
-  const cudaError_t x = cudaFuncSetAttribute(efft_pass_tma_df2<10, kLog2CtaWide - 10>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, kTmaSmem);
-  const cudaError_t y = cudaFuncSetAttribute(efft_pass_tma_df2<11, kLog2CtaWide - 11>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, kTmaSmem);
-  if (x != cudaSuccess && err == cudaSuccess) err = x;
-  if (y != cudaSuccess && err == cudaSuccess) err = y;
-}
-}  // namespace
-
 cudaError_t fx_set_attrs_df2() {
   cudaError_t err = cudaSuccess;
   attrs<FIRST>(err);
@@ -172,7 +150,6 @@ cudaError_t fx_set_attrs_df2() {
   set_smem(lasts_kernel<11>(), 8192, err);
   const cudaError_t e2 = fx_set_attrs_df2_pf();
   if (e2 != cudaSuccess && err == cudaSuccess) err = e2;
-  attrs_tma(err);
   return err;
 }
 

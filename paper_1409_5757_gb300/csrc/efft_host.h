@@ -37,8 +37,6 @@ constexpr int kPersistFirstMaxLog2N = 31;
 // allows it (measured: 2^31 first pass 8.30 ms against 9.16, c4 30.85 ms
 // against 31.7; 2^28 1.12 against 1.11)
 constexpr bool kTmaRule = true;
-// complex128 wide first pass fed by TMA copies (2^10 or 2^11 rows)
-constexpr bool kTmaRuleC128 = false;
 
 // One pass of the schedule and its launch shape.
 struct Pass {
@@ -47,7 +45,7 @@ struct Pass {
   int swap;   // middle pass that also swaps the outer digits: log2 of its
               // T x T column tile side (0: no swap)
   bool pf;    // complex128 strided pass run by the persistent prefetching kernel
-  bool tma;   // wide first pass fed by TMA copies (persistent)
+  bool tma;   // complex64 wide first pass fed by TMA copies (persistent)
   uint64_t grid;
   int threads;
   size_t smem;
@@ -95,7 +93,7 @@ struct StateRing {
 //        last pass is strided (no separate swap sweep);
 //  pf    complex128 strided passes as persistent kernels that prefetch the
 //        next tile.
-//  tma   the wide first pass as a persistent kernel fed by TMA copies.
+//  tma   complex64 wide first pass as a persistent kernel fed by TMA copies.
 struct Variant {
   int wide = -1, fuse = -1, pf = -1, tma = -1;
 };

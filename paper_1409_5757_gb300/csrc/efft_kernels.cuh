@@ -14,11 +14,9 @@
 //   efft_twiddles   FP64 twiddle tables exp(-2*pi*i*t*stride/N) split into
 //                   FP32 (hi, lo) pairs (plan time only).
 #pragma once
-#include <cuda.h>  // CUtensorMap (the struct only; no driver call is made here)
 #include <cstdint>
 #include <cuda_runtime.h>
 
-#include "../../include/efft.h"
 #include "efft_arith.cuh"
 
 namespace efft {
@@ -627,44 +625,6 @@ efft_pass_fx(void* __restrict__ data, const PassArgs a) {
 }
 
 // ----------------------------------------------------------------------------
-// Tensor-memory-accelerator (TMA) copies completed on an mbarrier, and the
-// bounded wait on it: at most kTmaSpinLimit polls of try_wait.
-// ----------------------------------------------------------------------------
-constexpr uint32_t kTmaSpinLimit = 1u << 24;
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// bounded wait for the phase `parity` of `bar`; true when it completed
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint32_t limit) {
-  for (uint32_t n = 0; n < limit; ++n)
-    if (mbar_try_wait(bar, parity)) return true;
-  return false;
-}
-// generic-proxy accesses of shared memory before async-proxy (TMA) writes
-__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
-      ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
-      : "memory");
-}
-
-// ----------------------------------------------------------------------------
 // Persistent complex128 strided pass with the next tile's loads in flight
 // during the current tile's last stage and epilogue.
 //
@@ -839,142 +799,6 @@ efft_pass_pf(void* __restrict__ data, const PassArgs a) {
 }
 
 // ----------------------------------------------------------------------------
-// The wide complex128 first pass (R = 2^10 or 2^11 rows, 8192-element tiles,
-// one CTA of 512 threads per SM) as a persistent kernel fed by TMA copies:
-// the pass's columns j < s (element j + r s) are the 2-D tensor [R][2 s] of
-// 8-byte words, a tile its (2 C) x R box, taken as R / 256 copies of
-// (2 C) x 256 (C * 16 = 64 or 128 bytes per row; the column coordinate
-// 2 C * tile is a multiple of 8 words, 16-byte aligned) that complete on an
-// mbarrier.  As in the complex64 kernel, stage 0 reads the dense box and
-// converts each binary64 pair to double-float, a barrier separates those
-// reads from the padded exchange layout, and one thread issues the next
-// tile's copies as soon as the last stage has read its inputs.  The wait is
-// bounded; on expiry the CTA records EFFT_ERR_TIMEOUT in word 3 of the
-// execute's state, waits once more, bounded, for its copies, and returns.
-// Same arithmetic, same results as efft_pass_fx<PolicyDF2, FIRST, LR, LC, 1>.
-// ----------------------------------------------------------------------------
-template <int LR, int LC>
-__global__ void __launch_bounds__(1 << (LR + LC - 4), 1)
-efft_pass_tma_df2(void* __restrict__ data, const PassArgs a, const __grid_constant__ CUtensorMap tmap) {
-  typedef PolicyDF2 P;
-  typedef P::V V;
-  constexpr int R = 1 << LR, C = 1 << LC, TPC = R >> 4, NT = (R * C) / 16;
-  constexpr int NFULL = LR / 4, REM = LR % 4, NST = NFULL + (REM ? 1 : 0);
-  constexpr int NMID = NST - 2;
-  constexpr int BOX_ROWS = 256, TILE_BYTES = R * C * 16;
-  static_assert(R % BOX_ROWS == 0 && C * 16 >= 16, "box shape");
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  unsigned char* const tile_base = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
-  V* sm = reinterpret_cast<V*>(tile_base);
-  const uint4* dense = reinterpret_cast<const uint4*>(tile_base);
-  __shared__ P::TW vtw[16 * C];
-  __shared__ __align__(8) uint64_t bar;
-  auto slot = [](int p, int col) {
-    const int raw = (p << LC) + col;
-    return raw + (raw >> 4);
-  };
-  const int tid = threadIdx.x;
-  const int c = tid & (C - 1);
-  const int t = tid >> LC;
-  const uint32_t emax = __ldg(a.state);
-  const int D = (int)emax - 127;
-  const int Dout = D - a.out_shift;
-  const bool nonfinite = (emax >= 0x7FFu);
-  const int kt = digit_rev_c(t << 4, LR);
-  const int sb0 = slot(t, c);
-  const uint32_t limit = a.inject_timeout ? 1024u : kTmaSpinLimit;
-  if (tid == 0) {
-    mbar_init(&bar, 1);
-    mbar_fence_init();
-  }
-  __syncthreads();
-  auto issue = [&](uint64_t tl) {
-    fence_proxy_async_smem();
-    mbar_expect_tx(&bar, TILE_BYTES);
-    if (!a.inject_timeout)
-#pragma unroll
-      for (int q = 0; q < R / BOX_ROWS; ++q)
-        tma_load_2d(tile_base + q * BOX_ROWS * C * 16, &tmap, (int)(tl * 2 * C), q * BOX_ROWS, &bar);
-  };
-  uint64_t tile = blockIdx.x;
-  uint32_t phase = 0;
-  bool failed = false;
-  if (tid == 0 && tile < a.ntiles) issue(tile);
-
-  for (; tile < a.ntiles; tile += gridDim.x) {
-    const uint64_t jcol = (tile << LC) + c;
-    __syncthreads();  // the previous tile's epilogue no longer reads vtw
-    if (tid < 16 * C) {
-      const int cc = tid >> 4, u = tid & 15;
-      const int kc = digit_rev_c(last_pos_c(u, REM), LR);
-      vtw[u * C + cc] = P::expand(twiddle_N(a, ((tile << LC) + cc) * (uint64_t)kc));
-    }
-    const P::TW wt = P::expand(twiddle_N(a, jcol * (uint64_t)kt));
-
-    failed = !mbar_wait_bounded(&bar, phase, limit);
-    if (__syncthreads_or(failed)) {
-      failed = true;
-      break;
-    }
-    phase ^= 1u;
-
-    V v[16];
-    // ---- stage 0: rows t + TPC*j of the dense box, binary64 -> double-float ----
-#pragma unroll
-    for (int j = 0; j < 16; ++j) v[j] = Mem<P, FIRST>::convert(dense[((t + TPC * j) << LC) + c], D, a.conj_in);
-    __syncthreads();  // the dense box is read before the exchange overwrites it
-    dif_regs<P, 4>(v);
-#pragma unroll
-    for (int u = 1; u < 16; ++u)
-      v[u] = P::mul_tw(v[u], P::int_tw(a.w2048, nullptr, (uint32_t)(t * bitrev_c(u, 4)) << (11 - LR)));
-#pragma unroll
-    for (int u = 0; u < 16; ++u) sm[sb0 + pad_off(bitrev_c(u, 4) * TPC * C)] = v[u];
-    __syncthreads();
-
-    // ---- middle radix-16 stages ----
-#pragma unroll
-    for (int st = 1; st <= NMID; ++st) {
-      const int log2l = LR - 4 * st;
-      const int log2g = log2l - 4;
-      const int b = t >> log2g, i = t & ((1 << log2g) - 1);
-      const int sb = slot((b << log2l) + i, c);
-      const int gstep = (1 << log2g) * C;
-#pragma unroll
-      for (int j = 0; j < 16; ++j) v[j] = sm[sb + pad_off(j * gstep)];
-      dif_regs<P, 4>(v);
-#pragma unroll
-      for (int u = 1; u < 16; ++u)
-        v[u] = P::mul_tw(v[u], P::int_tw(a.w2048, nullptr, (uint32_t)(i * bitrev_c(u, 4)) << (11 - log2l)));
-#pragma unroll
-      for (int u = 0; u < 16; ++u) sm[sb + pad_off(bitrev_c(u, 4) * gstep)] = v[u];
-      __syncthreads();
-    }
-
-    // ---- last stage; then the buffer takes the next tile ----
-    {
-      const int sb = slot(t << 4, c);
-#pragma unroll
-      for (int j = 0; j < 16; ++j) v[j] = sm[sb + pad_off(j * C)];
-    }
-    __syncthreads();
-    if (tid == 0 && tile + gridDim.x < a.ntiles) issue(tile + gridDim.x);
-    if (REM == 0) dif_regs<P, 4>(v);
-    else dif_groups<P, (REM == 0 ? 4 : REM)>(v);
-#pragma unroll
-    for (int u = 0; u < 16; ++u) {
-      const int k = kt | digit_rev_c(last_pos_c(u, REM), LR);
-      v[u] = P::pass_tw(v[u], wt, vtw[u * C + c]);
-      Mem<P, FIRST>::store(data, jcol + ((uint64_t)k << a.log2s), v[u], Dout, a.conj_out, nonfinite);
-    }
-  }
-  if (failed) {
-    if (tid == 0) atomicOr(const_cast<uint32_t*>(a.state) + 3, (uint32_t)EFFT_ERR_TIMEOUT);
-    mbar_wait_bounded(&bar, phase, limit);
-  }
-  (void)NT;
-}
-
-// ----------------------------------------------------------------------------
 // N <= 8: one thread, Eq. 1 evaluated directly with table twiddles.
 // ----------------------------------------------------------------------------
 template <class P>
@@ -1081,9 +905,5 @@ bool fx_launch_f32_wide(int kind, int log2R, dim3 grid, cudaStream_t st, void* d
 // fed by TMA copies; tensor_map: a CUtensorMap of the array as [1024][N/1024]
 // 8-byte elements with 16 x 256 boxes.  `grid` CTAs walk a.ntiles tiles.
 bool fx_launch_f32_tma(dim3 grid, cudaStream_t st, void* data, const PassArgs& a, const void* tensor_map);
-// the wide complex128 first pass (R = 2^10 or 2^11, 8192-element tiles) as a
-// persistent kernel fed by TMA copies; tensor_map: the array as [R][2 N/R]
-// 8-byte words with (2 C) x 256 boxes.
-bool fx_launch_df2_tma(int log2R, dim3 grid, cudaStream_t st, void* data, const PassArgs& a, const void* tensor_map);
 
 }  // namespace efft

@@ -462,52 +462,3 @@ def test_tma_wait_expiry_is_reported(orc, monkeypatch):
     assert p.check(sp) == 0
     check(t.cpu().numpy().astype(np.complex128), orc.fft_radix2(x, -1), "c64", N)
     p.destroy()
-
-
-@pytest.mark.parametrize("e,radices,sign", [(28, [10, 8, 10], -1), (28, [11, 6, 11], 1), (20, [10, 10], -1),
-                                            (24, [10, 4, 10], 1)])
-def test_parity_c128_tma_first_pass(orc, e, radices, sign):
-    """complex128: the wide first pass (2^10 x 8 or 2^11 x 4 columns per
-    tile) as the persistent kernel fed by TMA copies (tma = 1; the wide tiles
-    forced below 2^28): against the full oracle, bit for bit against the
-    first pass that loads its own tiles, and no expired device wait."""
-    import paper_1409_5757_gb300 as efft
-    N = 1 << e
-    x = host_input(orc, "c128", N, seed=5200 + e + radices[0])
-    runs = {}
-    for tma in (0, 1):
-        p = efft.Plan(N, efft.EFFT_C128, sign, radices=radices)
-        v = p.set_variant(1, 0, 0, tma)
-        assert v["tma"] == tma and v["wide"] == 1, v
-        t = torch.from_numpy(x).cuda()
-        p.execute(t.data_ptr(), torch.cuda.current_stream().cuda_stream)
-        assert p.check(torch.cuda.current_stream().cuda_stream) == 0
-        runs[tma] = t
-        p.destroy()
-    assert torch.equal(runs[0], runs[1])
-    got = runs[1].cpu().numpy()
-    del runs
-    check(got, orc.fft_radix2(x, sign), "c128", N)
-
-
-def test_tma_wait_expiry_is_reported_c128(orc, monkeypatch):
-    """The complex128 TMA-fed first pass with its wait made to run out
-    (EFFT_FAULT_INJECT=tma_wait): EFFT_ERR_TIMEOUT once, then a correct
-    execute on the same plan."""
-    import paper_1409_5757_gb300 as efft
-    N = 1 << 20
-    x = host_input(orc, "c128", N, seed=53)
-    p = efft.Plan(N, efft.EFFT_C128, -1, radices=[10, 10])
-    assert p.set_variant(1, -1, -1, 1)["tma"] == 1
-    sp = torch.cuda.current_stream().cuda_stream
-    t = torch.from_numpy(x.copy()).cuda()
-    monkeypatch.setenv("EFFT_FAULT_INJECT", "tma_wait")
-    p.execute(t.data_ptr(), sp)
-    monkeypatch.delenv("EFFT_FAULT_INJECT")
-    assert p.check(sp) == 8
-    assert p.check(sp) == 0
-    t = torch.from_numpy(x.copy()).cuda()
-    p.execute(t.data_ptr(), sp)
-    assert p.check(sp) == 0
-    check(t.cpu().numpy(), orc.fft_radix2(x, -1), "c128", N)
-    p.destroy()
