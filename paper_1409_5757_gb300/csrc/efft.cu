@@ -347,10 +347,14 @@ void apply_schedule(efft_plan_s* p, const int* r, int np, const Variant& v) {
     l.smem = (le + le / 16 + 1) * eb;
     p->permute = false;
   }
-  // complex64: the wide first pass (2^10 rows, 16 columns) fed by TMA copies
+  // complex64: the wide first pass (2^10 rows, 16 columns) and the wide
+  // middle pass (2^11 rows, 8 columns) fed by TMA copies
   if (!c128 && on(v.tma, kTmaRule)) {
-    Pass& f = p->pass[0];
-    f.tma = np >= 2 && f.kind == FIRST && f.wide && f.log2R == 10 && f.log2C == kLog2CtaWideC64 - 10;
+    for (int j = 0; j < np; ++j) {
+      Pass& f = p->pass[j];
+      if (f.kind == FIRST) f.tma = f.wide && f.log2R == 10 && f.log2C == kLog2CtaWideC64 - 10;
+      if (f.kind == MID) f.tma = f.wide && f.log2R == 11 && f.log2C == kLog2CtaWideC64 - 11 && f.log2s >= 3;
+    }
   }
   // persistent prefetching kernels for the complex128 strided passes with a
   // tile shape they are built for.  The rule (measured, 2^28..2^33): they
@@ -409,6 +413,21 @@ static EncodeTiled encode_tiled() {
     cudaGetLastError();
   });
   return fn;
+}
+
+// The tensor map of a complex64 middle pass of R = 2^log2R rows at stride
+// s = 2^log2s: the array as [N / (R s)][R][s] 8-byte elements, boxes of
+// C x 256 x 1, no swizzle.
+static bool mid_pass_map(CUtensorMap* map, void* data, int log2N, int log2R, int log2s, int C) {
+  EncodeTiled fn = encode_tiled();
+  if (!fn || (reinterpret_cast<uintptr_t>(data) & 15u)) return false;
+  const cuuint64_t dims[3] = {1ull << log2s, 1ull << log2R, 1ull << (log2N - log2R - log2s)};
+  const cuuint64_t strides[2] = {(1ull << log2s) * 8, (1ull << (log2R + log2s)) * 8};
+  const cuuint32_t box[3] = {(cuuint32_t)C, 256, 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, data, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+         CUDA_SUCCESS;
 }
 
 // The tensor map of a complex64 first pass of 2^10 rows: the array as
@@ -635,13 +654,16 @@ cudaError_t launch_pass(const efft_plan_s* p, const Pass& ps, void* data, const 
   }
   if (P::kElemBytes == 8 && ps.tma && !bt.ptrs) {
     CUtensorMap map;
-    if (first_pass_map(&map, data, ps.log2s)) {
-      // word 3 of the state: this execute's record of an expired device wait
-      if (cudaMemsetAsync(bt.state + 3, 0, 4, st) != cudaSuccess) return cudaErrorInvalidValue;
+    const bool first = (ps.kind == FIRST);
+    if (first ? first_pass_map(&map, data, ps.log2s)
+              : mid_pass_map(&map, data, p->log2n, ps.log2R, ps.log2s, 1 << ps.log2C)) {
+      // (word 3 of the state, this execute's record of an expired device
+      // wait, was cleared by enqueue_batch)
       a.ntiles = ps.grid;
       a.inject_timeout = fault_injected("tma_wait") ? 1u : 0u;
       const uint64_t g = std::min<uint64_t>(ps.grid, (uint64_t)(p->sms > 0 ? p->sms : 152));
-      const bool ok = fx_launch_f32_tma(dim3((unsigned)g, 1), st, data, a, &map);
+      const bool ok = first ? fx_launch_f32_tma(dim3((unsigned)g, 1), st, data, a, &map)
+                            : fx_launch_f32_mid_tma(dim3((unsigned)g, 1), st, data, a, &map);
       return ok ? cudaGetLastError() : cudaErrorInvalidConfiguration;
     }
     // no tensor map (no driver entry point, or a buffer not 16-byte
@@ -963,6 +985,14 @@ int enqueue_batch(efft_plan_s* p, void* data, const Batch& bt, cudaStream_t st) 
     else efft_small<PolicyF32><<<dim3(1, bt.count), 32, 0, st>>>(data, a);
     prof_end(p, rec, st);
     return cudaGetLastError() == cudaSuccess ? EFFT_OK : EFFT_ERR_LAUNCH;
+  }
+  // complex64 passes fed by TMA record an expired wait in word 3 of the
+  // execute's state: cleared once per execute (complex128 executes clear
+  // the whole word in the range scan)
+  if (!c128 && !bt.ptrs) {
+    bool tma = false;
+    for (int j = 0; j < p->npasses; ++j) tma = tma || p->pass[j].tma;
+    if (tma && cudaMemsetAsync(bt.state + 3, 0, 4, st) != cudaSuccess) return EFFT_ERR_LAUNCH;
   }
   for (int j = 0; j < p->npasses; ++j) {
     int rec = prof_begin(p, 1 + j, st);

@@ -329,4 +329,151 @@ efft_pass_fx32_tma(void* __restrict__ data, const PassArgs a, const __grid_const
 
 constexpr int fx32_tma_smem_bytes() { return fx32_smem_bytes(4) + 1024; }
 
+// ----------------------------------------------------------------------------
+// The wide complex64 middle pass of 2^11 rows (radix-16 stages, 8 columns,
+// 1024 threads, one CTA per SM; efft_pass_fx<PolicyF32, MID, 11, 3, 1>) as a
+// persistent kernel fed by TMA copies.  The pass works on blocks of L = R s
+// elements (s = 2^log2s, the column stride); block b's columns m < s with
+// rows r < R at element b L + m + r s are the 3-D tensor [N/L][R][s] of
+// 8-byte elements, and a tile (8 adjacent columns of one block) is R / 256
+// boxes of 8 x 256 x 1 (64 bytes per row; the column coordinate, a multiple
+// of 8, is 64-byte aligned).  Everything else as in efft_pass_fx32_tma:
+// the next tile's copies are issued once the last stage has read its
+// inputs, stage 0 reads the dense box, a barrier separates those reads from
+// the padded exchange layout, and the mbarrier wait is bounded, its expiry
+// recorded in word 3 of the execute's state.  Same arithmetic, same results
+// as the kernel that loads its own tiles.
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+      "[%5];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+      : "memory");
+}
+
+template <int LR, int LC>
+__global__ void __launch_bounds__(1 << (LR + LC - 4), 1)
+efft_pass_mid_tma_f32(void* __restrict__ data, const PassArgs a, const __grid_constant__ CUtensorMap tmap) {
+  typedef PolicyF32 P;
+  typedef P::V V;
+  constexpr int R = 1 << LR, C = 1 << LC, TPC = R >> 4;
+  constexpr int NFULL = LR / 4, REM = LR % 4, NST = NFULL + (REM ? 1 : 0);
+  constexpr int NMID = NST - 2;
+  constexpr int BOX_ROWS = 256, TILE_BYTES = R * C * 8;
+  static_assert(R % BOX_ROWS == 0 && (C * 8) % 16 == 0, "box shape");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  unsigned char* const tile_base = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+  V* sm = reinterpret_cast<V*>(tile_base);
+  __shared__ P::TW vtw[16 * C];
+  __shared__ __align__(8) uint64_t bar;
+  auto slot = [](int p, int col) {
+    const int raw = (p << LC) + col;
+    return raw + (raw >> 4);
+  };
+  const int tid = threadIdx.x;
+  const int c = tid & (C - 1);
+  const int t = tid >> LC;
+  const int kt = digit_rev_c(t << 4, LR);
+  const int sb0 = slot(t, c);
+  const int sh = a.log2N - a.log2L;
+  const uint64_t smask = (1ull << a.log2s) - 1ull;
+  const uint32_t limit = a.inject_timeout ? 1024u : kTmaSpinLimit;
+  if (tid == 0) {
+    mbar_init(&bar, 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  auto issue = [&](uint64_t tl) {
+    const uint64_t j0 = tl << LC;
+    const int blk = (int)(j0 >> a.log2s), m0 = (int)(j0 & smask);
+    fence_proxy_async_smem();
+    mbar_expect_tx(&bar, TILE_BYTES);
+    if (!a.inject_timeout)
+#pragma unroll
+      for (int q = 0; q < R / BOX_ROWS; ++q) tma_load_3d(tile_base + q * BOX_ROWS * C * 8, &tmap, m0, q * BOX_ROWS, blk, &bar);
+  };
+  uint64_t tile = blockIdx.x;
+  uint32_t phase = 0;
+  bool failed = false;
+  if (tid == 0 && tile < a.ntiles) issue(tile);
+
+  for (; tile < a.ntiles; tile += gridDim.x) {
+    const uint64_t jcol = (tile << LC) + c;
+    const uint64_t m = jcol & smask;
+    const uint64_t colbase = ((jcol >> a.log2s) << a.log2L) + m;
+    __syncthreads();  // the previous tile's epilogue no longer reads vtw
+    if (tid < 16 * C) {
+      const int cc = tid >> 4, u = tid & 15;
+      const uint64_t mc = ((tile << LC) + cc) & smask;
+      const int kc = digit_rev_c(last_pos_c(u, REM), LR);
+      vtw[u * C + cc] = P::expand(twiddle_N(a, (mc * (uint64_t)kc) << sh));
+    }
+    const P::TW wt = P::expand(twiddle_N(a, (m * (uint64_t)kt) << sh));
+
+    failed = !mbar_wait_bounded(&bar, phase, limit);
+    if (__syncthreads_or(failed)) {
+      failed = true;
+      break;
+    }
+    phase ^= 1u;
+
+    V v[16];
+    // ---- stage 0: rows t + TPC*j of the dense box ----
+#pragma unroll
+    for (int j = 0; j < 16; ++j) v[j] = sm[((t + TPC * j) << LC) + c];
+    __syncthreads();  // the dense box is read before the exchange overwrites it
+    dif_regs<P, 4>(v);
+#pragma unroll
+    for (int u = 1; u < 16; ++u)
+      v[u] = P::mul_tw(v[u], P::int_tw(a.w2048, nullptr, (uint32_t)(t * bitrev_c(u, 4)) << (11 - LR)));
+#pragma unroll
+    for (int u = 0; u < 16; ++u) sm[sb0 + pad_off(bitrev_c(u, 4) * TPC * C)] = v[u];
+    __syncthreads();
+
+    // ---- middle radix-16 stages ----
+#pragma unroll
+    for (int st = 1; st <= NMID; ++st) {
+      const int log2l = LR - 4 * st;
+      const int log2g = log2l - 4;
+      const int b = t >> log2g, i = t & ((1 << log2g) - 1);
+      const int sb = slot((b << log2l) + i, c);
+      const int gstep = (1 << log2g) * C;
+#pragma unroll
+      for (int j = 0; j < 16; ++j) v[j] = sm[sb + pad_off(j * gstep)];
+      dif_regs<P, 4>(v);
+#pragma unroll
+      for (int u = 1; u < 16; ++u)
+        v[u] = P::mul_tw(v[u], P::int_tw(a.w2048, nullptr, (uint32_t)(i * bitrev_c(u, 4)) << (11 - log2l)));
+#pragma unroll
+      for (int u = 0; u < 16; ++u) sm[sb + pad_off(bitrev_c(u, 4) * gstep)] = v[u];
+      __syncthreads();
+    }
+
+    // ---- last stage; then the buffer takes the next tile ----
+    {
+      const int sb = slot(t << 4, c);
+#pragma unroll
+      for (int j = 0; j < 16; ++j) v[j] = sm[sb + pad_off(j * C)];
+    }
+    __syncthreads();
+    if (tid == 0 && tile + gridDim.x < a.ntiles) issue(tile + gridDim.x);
+    if (REM == 0) dif_regs<P, 4>(v);
+    else dif_groups<P, (REM == 0 ? 4 : REM)>(v);
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+      const int k = kt | digit_rev_c(last_pos_c(u, REM), LR);
+      v[u] = P::pass_tw(v[u], wt, vtw[u * C + c]);
+      Mem<P, MID>::store(data, colbase + ((uint64_t)k << a.log2s), v[u], 0, 0u, false);
+    }
+  }
+  if (failed) {
+    if (tid == 0 && a.state) atomicOr(const_cast<uint32_t*>(a.state) + 3, (uint32_t)EFFT_ERR_TIMEOUT);
+    mbar_wait_bounded(&bar, phase, limit);
+  }
+}
+
+// padded 16384-element tile of 8-byte elements plus alignment slack
+constexpr int mid_tma_smem_bytes() { return ((1 << 14) + (1 << 14) / 16 + 1) * 8 + 1024; }
+
 }  // namespace efft

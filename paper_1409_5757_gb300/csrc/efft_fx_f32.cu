@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include "efft_fx32.cuh"
+#include "efft_host.h"
 #include "efft_kernels.cuh"
 
 namespace efft {
@@ -60,7 +61,17 @@ cudaError_t fx_set_attrs_f32() {
   const cudaError_t tm = cudaFuncSetAttribute(efft_pass_fx32_tma<kLog2CtaWideC64 - 10>,
                                               cudaFuncAttributeMaxDynamicSharedMemorySize, fx32_tma_smem_bytes());
   if (tm != cudaSuccess && err == cudaSuccess) err = tm;
+  const cudaError_t tm2 = cudaFuncSetAttribute(efft_pass_mid_tma_f32<11, kLog2CtaWideC64 - 11>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, mid_tma_smem_bytes());
+  if (tm2 != cudaSuccess && err == cudaSuccess) err = tm2;
   return err;
+}
+
+bool fx_launch_f32_mid_tma(dim3 grid, cudaStream_t st, void* data, const PassArgs& a, const void* tensor_map) {
+  constexpr int LC = kLog2CtaWideC64 - 11;
+  const CUtensorMap& map = *static_cast<const CUtensorMap*>(tensor_map);
+  efft_pass_mid_tma_f32<11, LC><<<grid, 1 << (11 + LC - 4), mid_tma_smem_bytes(), st>>>(data, a, map);
+  return true;
 }
 
 bool fx_launch_f32_tma(dim3 grid, cudaStream_t st, void* data, const PassArgs& a, const void* tensor_map) {

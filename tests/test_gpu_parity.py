@@ -462,3 +462,53 @@ def test_tma_wait_expiry_is_reported(orc, monkeypatch):
     assert p.check(sp) == 0
     check(t.cpu().numpy().astype(np.complex128), orc.fft_radix2(x, -1), "c64", N)
     p.destroy()
+
+
+@pytest.mark.parametrize("radices,sign", [([9, 11, 9], -1), ([4, 11, 4], 1), ([6, 11, 6], -1)])
+def test_parity_c64_tma_middle_pass(orc, radices, sign):
+    """complex64: the wide middle pass of 2^11 rows (8 columns, 1024 threads)
+    as the persistent kernel fed by TMA copies (3-D boxes: column, row,
+    block), at the 2^29 default schedule and with the wide tiles forced at
+    2^19 and 2^23 (16 and 64 columns per block): against the full oracle,
+    bit for bit against the middle pass that loads its own tiles, and no
+    expired device wait."""
+    import paper_1409_5757_gb300 as efft
+    e = sum(radices)
+    N = 1 << e
+    x = host_input(orc, "c64", N, seed=5300 + e)
+    runs = {}
+    for tma in (0, 1):
+        p = efft.Plan(N, efft.EFFT_C64, sign, radices=radices)
+        v = p.set_variant(1, -1, -1, tma)
+        assert v["tma"] == tma and v["wide"] == 1, v
+        t = torch.from_numpy(x.astype(np.complex64)).cuda()
+        p.execute(t.data_ptr(), torch.cuda.current_stream().cuda_stream)
+        assert p.check(torch.cuda.current_stream().cuda_stream) == 0
+        runs[tma] = t
+        p.destroy()
+    assert torch.equal(runs[0], runs[1])
+    got = runs[1].cpu().numpy().astype(np.complex128)
+    del runs
+    check(got, orc.fft_radix2(x, sign), "c64", N)
+
+
+def test_tma_wait_expiry_is_reported_middle_pass(orc, monkeypatch):
+    """The TMA-fed complex64 middle pass with its wait made to run out
+    (EFFT_FAULT_INJECT=tma_wait): EFFT_ERR_TIMEOUT, then a correct execute."""
+    import paper_1409_5757_gb300 as efft
+    N = 1 << 19
+    x = host_input(orc, "c64", N, seed=54)
+    p = efft.Plan(N, efft.EFFT_C64, -1, radices=[4, 11, 4])
+    assert p.set_variant(1, -1, -1, 1)["tma"] == 1
+    sp = torch.cuda.current_stream().cuda_stream
+    t = torch.from_numpy(x.astype(np.complex64)).cuda()
+    monkeypatch.setenv("EFFT_FAULT_INJECT", "tma_wait")
+    p.execute(t.data_ptr(), sp)
+    monkeypatch.delenv("EFFT_FAULT_INJECT")
+    assert p.check(sp) == 8
+    assert p.check(sp) == 0
+    t = torch.from_numpy(x.astype(np.complex64)).cuda()
+    p.execute(t.data_ptr(), sp)
+    assert p.check(sp) == 0
+    check(t.cpu().numpy().astype(np.complex128), orc.fft_radix2(x, -1), "c64", N)
+    p.destroy()
