@@ -14,6 +14,12 @@
 #include "efft_kernels.cuh"
 
 namespace efft {
+
+// The wide complex64 middle pass (R = 2^11, 8 columns) as a persistent
+// kernel fed by TMA copies (efft_fx_f32.cu); tensor_map: the array as
+// [N / (R s)][R][s] 8-byte elements with 8 x 256 x 1 boxes.
+bool fx_launch_f32_mid_tma(dim3 grid, cudaStream_t st, void* data, const PassArgs& a, const void* tensor_map);
+
 namespace host {
 
 constexpr uint32_t kMagic = 0xEFF71409u;
@@ -217,10 +223,6 @@ int launch_range_scan(const void* data, uint64_t n_complex, uint32_t* state, voi
 void free_plan_memory(efft_plan_s* p);
 int prof_begin(efft_plan_s* p, int slot, cudaStream_t st);
 void prof_end(efft_plan_s* p, int rec, cudaStream_t st);
-// The wide complex64 middle pass (R = 2^11, 8 columns) as a persistent
-// kernel fed by TMA copies (efft_fx_f32.cu); tensor_map: the array as
-// [N / (R s)][R][s] 8-byte elements with 8 x 256 x 1 boxes.
-bool fx_launch_f32_mid_tma(dim3 grid, cudaStream_t st, void* data, const PassArgs& a, const void* tensor_map);
 // Mixed-radix passes (efft_mix.cu): kernel attributes and one pass launch.
 cudaError_t mix_set_attrs();
 cudaError_t launch_mix(const efft_plan_s* p, const Pass& ps, void* data, const Batch& bt, cudaStream_t st);
