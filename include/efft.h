@@ -218,7 +218,8 @@ int efft_plan_create_with_radices(efft_plan_t* out, uint64_t n, int dtype, int s
  *    the tile width of the strided first pass (complex64: also of the 2^11
  *    middle pass) doubled or not, the digit swap folded into the middle pass
  *    or not, the persistent prefetching pass kernels or not (these two
- *    complex128 only), the TMA-fed first pass or not (complex64 only);
+ *    complex128 only), the TMA-fed first and 2^11 middle passes or not
+ *    (complex64 only);
  *  - n = M * 2^e, M > 1: every outer radix 2^a of the (2^a, M * 2^b, 2^a)
  *    schedule that efft_plan_create accepts, and one pass when n <= 2048.
  * Each candidate is run on `scratch` (n*S bytes of the caller's device
@@ -244,7 +245,8 @@ typedef struct efft_candidate {
   int wide;             /* 1: the wide strided tiles (see efft_plan_autotune)   */
   int fused_swap;       /* 1: digit swap folded into the middle pass            */
   int persistent;       /* 1: persistent prefetching pass kernels               */
-  int tma;              /* 1: complex64 wide first pass fed by TMA copies       */
+  int tma;              /* 1: complex64 wide first and 2^11 middle passes fed   */
+                        /*    by TMA copies                                     */
   double ms;            /* median time of one execute (milliseconds)            */
 } efft_candidate;
 
@@ -274,10 +276,11 @@ int efft_plan_set_variant(efft_plan_t plan, int wide, int fused_swap, int persis
  * Synchronise `stream`, then report whether a kernel of one of the plan's
  * earlier executes gave up a bounded device wait: EFFT_ERR_TIMEOUT if so
  * (that execute's output is incomplete; the record is cleared), else EFFT_OK.
- * The only device waits in the library are those of the complex64 first
- * pass fed by TMA copies (the `tma` variant), which waits on an mbarrier in
- * shared memory for its copies and, when they do not complete within about
- * 2^24 polls, records the timeout in the execute's state word and returns.
+ * The only device waits in the library are those of the complex64 passes
+ * fed by TMA copies (the `tma` variant: the wide first pass and the wide
+ * 2^11 middle pass), which wait on an mbarrier in shared memory for their
+ * copies and, when those do not complete within about 2^24 polls, record the
+ * timeout in the execute's state word and return.
  * Errors: INVALID_PLAN, CUDA.
  */
 int efft_execute_check(efft_plan_t plan, void* stream);
