@@ -53,9 +53,11 @@ __device__ __forceinline__ float4 w_of(const RealArgs& a, uint64_t m) {
 // The pair kernels work on kPairBatch pairs per thread and loop trip: the
 // loads of all of them are issued before any is used, so that each thread
 // keeps 2 kPairBatch loads in flight (one pair per trip left the loop at
-// about 0.6 of the memory bandwidth, short of loads in flight).  The pairs
-// (k, N/2 - k), k <= N/4, are disjoint, so the batch's loads and stores do
-// not overlap.
+// about 0.6 of the memory bandwidth, short of loads in flight).  A block's
+// trip covers kPairBatch consecutive chunks of blockDim.x pairs, so the
+// accesses stay in two contiguous runs (k ascending, N/2 - k descending).
+// The pairs (k, N/2 - k), k <= N/4, are disjoint, so the batch's loads and
+// stores do not overlap.
 constexpr int kPairBatch = 4;
 
 // complex64: FP32 with the compensated twiddle product of the pass kernels.
@@ -98,12 +100,12 @@ __device__ __forceinline__ void pair_f32(float2* __restrict__ z, const RealArgs&
 __global__ void __launch_bounds__(256, 4) efft_real_pairs_f32(float2* __restrict__ z, const RealArgs a) {
   const uint64_t half = a.nh >> 1;
   const float sc = __uint_as_float((uint32_t)(127 - a.out_shift) << 23);
-  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  for (uint64_t k0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k0 <= half; k0 += kPairBatch * stride) {
+  const uint64_t trip = (uint64_t)kPairBatch * blockDim.x;
+  for (uint64_t k0 = (uint64_t)blockIdx.x * trip + threadIdx.x; k0 <= half; k0 += trip * gridDim.x) {
     float2 zk[kPairBatch], zm[kPairBatch];
 #pragma unroll
     for (int u = 0; u < kPairBatch; ++u) {
-      const uint64_t k = k0 + u * stride;
+      const uint64_t k = k0 + (uint64_t)u * blockDim.x;
       if (k <= half) {
         zk[u] = __ldcg(z + k);
         zm[u] = (k == 0) ? zk[u] : __ldcg(z + (a.nh - k));
@@ -111,7 +113,7 @@ __global__ void __launch_bounds__(256, 4) efft_real_pairs_f32(float2* __restrict
     }
 #pragma unroll
     for (int u = 0; u < kPairBatch; ++u) {
-      const uint64_t k = k0 + u * stride;
+      const uint64_t k = k0 + (uint64_t)u * blockDim.x;
       if (k <= half) pair_f32(z, a, k, zk[u], zm[u], sc);
     }
   }
@@ -125,12 +127,12 @@ __global__ void __launch_bounds__(256, 3) efft_real_pairs_df(uint4* __restrict__
   const bool nonfinite = (emax >= 0x7FFu);
   const int D = (int)emax + a.grow - 127;
   const int Dout = D - a.out_shift;
-  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  for (uint64_t k0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k0 <= half; k0 += kPairBatch * stride) {
+  const uint64_t trip = (uint64_t)kPairBatch * blockDim.x;
+  for (uint64_t k0 = (uint64_t)blockIdx.x * trip + threadIdx.x; k0 <= half; k0 += trip * gridDim.x) {
     uint4 ukb[kPairBatch], umb[kPairBatch];
 #pragma unroll
     for (int u = 0; u < kPairBatch; ++u) {
-      const uint64_t k = k0 + u * stride;
+      const uint64_t k = k0 + (uint64_t)u * blockDim.x;
       if (k <= half) {
         ukb[u] = __ldcg(z + k);
         umb[u] = (k == 0) ? ukb[u] : __ldcg(z + (a.nh - k));
@@ -138,7 +140,7 @@ __global__ void __launch_bounds__(256, 3) efft_real_pairs_df(uint4* __restrict__
     }
 #pragma unroll
     for (int u = 0; u < kPairBatch; ++u) {
-    const uint64_t k = k0 + u * stride;
+    const uint64_t k = k0 + (uint64_t)u * blockDim.x;
     if (k > half) break;
     const uint64_t km = (k == 0) ? 0 : a.nh - k;
     const uint4 uk = ukb[u];
