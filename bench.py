@@ -675,7 +675,8 @@ def run_ours(args, wl):
                "api": "efft_execute_host_stream (one cudaHostAlloc host array as input and output, the one "
                       "device buffer; copy in, transform, copy out in sequence: a second 128 GiB device "
                       "buffer does not fit)"}
-    elif N * S <= (32 << 30) and not args.no_e2e:
+    elif (N * S <= (32 << 30) and not args.no_e2e
+          and (world == 1 or (host_room is not None and host_room >= world * 2 * N * S + (24 << 30)))):
         src = keep if keep is not None else x
         hin = inputs.PinnedHost(N, tdt)
         hout = inputs.PinnedHost(N, tdt)
