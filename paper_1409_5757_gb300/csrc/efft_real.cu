@@ -50,100 +50,61 @@ __device__ __forceinline__ float4 w_of(const RealArgs& a, uint64_t m) {
   return w;
 }
 
-// The pair kernels work on kPairBatch pairs per thread and loop trip: the
-// loads of all of them are issued before any is used, so that each thread
-// keeps 2 kPairBatch loads in flight (one pair per trip left the loop at
-// about 0.6 of the memory bandwidth, short of loads in flight).  A block's
-// trip covers kPairBatch consecutive chunks of blockDim.x pairs, so the
-// accesses stay in two contiguous runs (k ascending, N/2 - k descending).
-// The pairs (k, N/2 - k), k <= N/4, are disjoint, so the batch's loads and
-// stores do not overlap.
-constexpr int kPairBatch = 4;
-
 // complex64: FP32 with the compensated twiddle product of the pass kernels.
-__device__ __forceinline__ void pair_f32(float2* __restrict__ z, const RealArgs& a, uint64_t k, float2 zk,
-                                         float2 zm, float sc) {
-  const uint64_t km = (k == 0) ? 0 : a.nh - k;
-  float2 p, q;
-  if (k == 0) {
-    // forward: Z_0 and its conjugate; inverse: F_0 and F_{N/2}, both real
-    p = a.inverse ? make_float2(zk.x, 0.f) : zk;
-    q = a.inverse ? make_float2(zk.y, 0.f) : make_float2(zk.x, -zk.y);
-  } else {
-    p = zk;
-    q = make_float2(zm.x, -zm.y);
-  }
-  const float2 A = PolicyF32::add(p, q), B = PolicyF32::sub(p, q);
-  // D = -i W^k B (inverse +i conj(W)^k B): exactly -i B at k = 0, -B at
-  // k = N/4 (N/2 even), else with W^k from the table
-  float2 D;
-  if (k == 0) {
-    D = a.inverse ? make_float2(-B.y, B.x) : make_float2(B.y, -B.x);
-  } else if (2 * k == a.nh) {
-    D = make_float2(-B.x, -B.y);
-  } else {
-    const float2 wb = PolicyF32::mul_tw(B, w_of(a, k));
-    D = a.inverse ? make_float2(-wb.y, wb.x) : make_float2(wb.y, -wb.x);
-  }
-  float2 x = PolicyF32::add(A, D), y = PolicyF32::sub(A, D);
-  x = make_float2(__fmul_rn(x.x, sc), __fmul_rn(x.y, sc));
-  y = make_float2(__fmul_rn(y.x, sc), __fmul_rn(-y.y, sc));  // conj
-  if (k == 0) {
-    // forward: (F_0, F_{N/2}) = (x.re, y.re); inverse: Z_0 = x
-    z[0] = a.inverse ? x : make_float2(x.x, y.x);
-  } else {
-    z[k] = x;
-    if (km != k) z[km] = y;
-  }
-}
-
-__global__ void __launch_bounds__(256, 4) efft_real_pairs_f32(float2* __restrict__ z, const RealArgs a) {
+__global__ void __launch_bounds__(256) efft_real_pairs_f32(float2* __restrict__ z, const RealArgs a) {
   const uint64_t half = a.nh >> 1;
   const float sc = __uint_as_float((uint32_t)(127 - a.out_shift) << 23);
-  const uint64_t trip = (uint64_t)kPairBatch * blockDim.x;
-  for (uint64_t k0 = (uint64_t)blockIdx.x * trip + threadIdx.x; k0 <= half; k0 += trip * gridDim.x) {
-    float2 zk[kPairBatch], zm[kPairBatch];
-#pragma unroll
-    for (int u = 0; u < kPairBatch; ++u) {
-      const uint64_t k = k0 + (uint64_t)u * blockDim.x;
-      if (k <= half) {
-        zk[u] = __ldcg(z + k);
-        zm[u] = (k == 0) ? zk[u] : __ldcg(z + (a.nh - k));
-      }
+  for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k <= half;
+       k += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t km = (k == 0) ? 0 : a.nh - k;
+    const float2 zk = __ldcg(z + k);
+    float2 p, q;
+    if (k == 0) {
+      // forward: Z_0 and its conjugate; inverse: F_0 and F_{N/2}, both real
+      p = a.inverse ? make_float2(zk.x, 0.f) : zk;
+      q = a.inverse ? make_float2(zk.y, 0.f) : make_float2(zk.x, -zk.y);
+    } else {
+      const float2 zm = __ldcg(z + km);
+      p = zk;
+      q = make_float2(zm.x, -zm.y);
     }
-#pragma unroll
-    for (int u = 0; u < kPairBatch; ++u) {
-      const uint64_t k = k0 + (uint64_t)u * blockDim.x;
-      if (k <= half) pair_f32(z, a, k, zk[u], zm[u], sc);
+    const float2 A = PolicyF32::add(p, q), B = PolicyF32::sub(p, q);
+    // D = -i W^k B (inverse +i conj(W)^k B): exactly -i B at k = 0, -B at
+    // k = N/4 (N/2 even), else with W^k from the table
+    float2 D;
+    if (k == 0) {
+      D = a.inverse ? make_float2(-B.y, B.x) : make_float2(B.y, -B.x);
+    } else if (2 * k == a.nh) {
+      D = make_float2(-B.x, -B.y);
+    } else {
+      const float2 wb = PolicyF32::mul_tw(B, w_of(a, k));
+      D = a.inverse ? make_float2(-wb.y, wb.x) : make_float2(wb.y, -wb.x);
+    }
+    float2 x = PolicyF32::add(A, D), y = PolicyF32::sub(A, D);
+    x = make_float2(__fmul_rn(x.x, sc), __fmul_rn(x.y, sc));
+    y = make_float2(__fmul_rn(y.x, sc), __fmul_rn(-y.y, sc));  // conj
+    if (k == 0) {
+      // forward: (F_0, F_{N/2}) = (x.re, y.re); inverse: Z_0 = x
+      z[0] = a.inverse ? x : make_float2(x.x, y.x);
+    } else {
+      z[k] = x;
+      if (km != k) z[km] = y;
     }
   }
 }
 
 // complex128: double-float, the binary64 values converted with an exact
 // power-of-two scale (the bound on |values| comes from the range scan).
-__global__ void __launch_bounds__(256, 3) efft_real_pairs_df(uint4* __restrict__ z, const RealArgs a) {
+__global__ void __launch_bounds__(256) efft_real_pairs_df(uint4* __restrict__ z, const RealArgs a) {
   const uint64_t half = a.nh >> 1;
   const uint32_t emax = __ldg(a.state);
   const bool nonfinite = (emax >= 0x7FFu);
   const int D = (int)emax + a.grow - 127;
   const int Dout = D - a.out_shift;
-  const uint64_t trip = (uint64_t)kPairBatch * blockDim.x;
-  for (uint64_t k0 = (uint64_t)blockIdx.x * trip + threadIdx.x; k0 <= half; k0 += trip * gridDim.x) {
-    uint4 ukb[kPairBatch], umb[kPairBatch];
-#pragma unroll
-    for (int u = 0; u < kPairBatch; ++u) {
-      const uint64_t k = k0 + (uint64_t)u * blockDim.x;
-      if (k <= half) {
-        ukb[u] = __ldcg(z + k);
-        umb[u] = (k == 0) ? ukb[u] : __ldcg(z + (a.nh - k));
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < kPairBatch; ++u) {
-    const uint64_t k = k0 + (uint64_t)u * blockDim.x;
-    if (k > half) break;
+  for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k <= half;
+       k += (uint64_t)gridDim.x * blockDim.x) {
     const uint64_t km = (k == 0) ? 0 : a.nh - k;
-    const uint4 uk = ukb[u];
+    const uint4 uk = __ldcg(z + k);
     cdf2 p, q;
     {
       const df re = f64bits_to_df(uk.x, uk.y, D, 0u), im = f64bits_to_df(uk.z, uk.w, D, 0u);
@@ -156,7 +117,7 @@ __global__ void __launch_bounds__(256, 3) efft_real_pairs_df(uint4* __restrict__
           q = cdf2{make_float2(re.h, -im.h), make_float2(re.l, -im.l)};
         }
       } else {
-        const uint4 um = umb[u];
+        const uint4 um = __ldcg(z + km);
         const df mre = f64bits_to_df(um.x, um.y, D, 0u);
         const df mim = f64bits_to_df(um.z, um.w, D, 0x80000000u);  // conj
         p = cdf2{make_float2(re.h, im.h), make_float2(re.l, im.l)};
@@ -187,7 +148,6 @@ __global__ void __launch_bounds__(256, 3) efft_real_pairs_df(uint4* __restrict__
     } else {
       z[k] = ox;
       if (km != k) z[km] = oy;
-    }
     }
   }
 }
