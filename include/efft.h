@@ -200,6 +200,10 @@ int efft_execute_host_stream(const efft_plan_t* plans, int nplans, void* const* 
  *  p = 1 with log2 R_0 = log2 n in [4, 11];
  *  p = 2 or 3 with every log2 R_j in [4, 11], sum log2 n, and R_0 = R_{p-1}
  *    (symmetric: the digit reversal is then an involution, done in place).
+ * For n = M * 2^e with M > 1 odd (Sec. 2.1's size set):
+ *  p = 1 with log2 R_0 = e and n <= 2048 (one CTA tile);
+ *  p = 3 given as (a, b, a), a >= 1, 2a + b = e: the passes 2^a, M * 2^b,
+ *    2^a, each at most 2048 points.
  * Any other schedule: EFFT_ERR_UNSUPPORTED (before any CUDA call).
  * EFFT_FLAG_AUTOTUNE is rejected here (EFFT_ERR_INVALID_FLAGS).
  */

@@ -135,6 +135,19 @@ static bool mixed_ok(const efft_plan_s* p, int a) {
   return A <= (uint64_t)tile && B <= (uint64_t)tile;
 }
 
+// An explicit schedule for N = M * 2^e, M > 1: one pass (log2 R_0 = e, N
+// within a CTA tile) or (2^a, M * 2^b, 2^a) given as (a, b, a).
+static bool valid_mixed_schedule(uint64_t n, int dtype, const int* r, int np) {
+  efft_plan_s q;
+  std::memset(&q, 0, sizeof(q));
+  q.n = n;
+  q.dtype = dtype;
+  const int e = __builtin_ctzll(n);
+  if (!r) return false;
+  if (np == 1) return r[0] == e && mixed_ok(&q, 0);
+  return np == 3 && r[0] >= 1 && r[0] == r[2] && r[1] >= 0 && 2 * r[0] + r[1] == e && mixed_ok(&q, r[0]);
+}
+
 int mixed_candidates(const efft_plan_s* p, int* a, int cap) {
   int k = 0;
   for (int c = 0; 2 * c <= __builtin_ctzll(p->n); ++c)
@@ -755,7 +768,8 @@ int plan_create_impl(efft_plan_t* out, uint64_t n, int dtype, int sign, uint32_t
   const bool cached = (flags & EFFT_FLAG_AUTOTUNE) && !r_explicit && tuned_lookup(dev, n, dtype, &t);
   if (p->odd > 1) {
     // N = M * 2^e: the mixed-radix schedule (the tuned outer radix if cached)
-    const int rc0 = apply_mixed_schedule(p, cached ? t.mixed_a : -1);
+    const int force = r_explicit ? (np_explicit == 3 ? r_explicit[0] : 0) : (cached ? t.mixed_a : -1);
+    const int rc0 = apply_mixed_schedule(p, force);
     if (rc0 != EFFT_OK) {
       delete p;
       return rc0;
@@ -846,8 +860,11 @@ int efft_plan_create_with_radices(efft_plan_t* out, uint64_t n, int dtype, int s
   int rc = check_create_args(out, n, dtype, sign);
   if (rc != EFFT_OK) return rc;
   if (flags & ~(EFFT_FLAG_ALL & ~EFFT_FLAG_AUTOTUNE)) return EFFT_ERR_INVALID_FLAGS;
-  if ((n & (n - 1)) != 0) return EFFT_ERR_UNSUPPORTED;  // explicit schedules: powers of two
-  if (!valid_schedule(ilog2_u64(n), log2_radices, npasses)) return EFFT_ERR_UNSUPPORTED;
+  if ((n & (n - 1)) != 0) {
+    if (!valid_mixed_schedule(n, dtype, log2_radices, npasses)) return EFFT_ERR_UNSUPPORTED;
+  } else if (!valid_schedule(ilog2_u64(n), log2_radices, npasses)) {
+    return EFFT_ERR_UNSUPPORTED;
+  }
   static const int kNone[1] = {0};
   return plan_create_impl(out, n, dtype, sign, flags, log2_radices ? log2_radices : kNone, npasses);
 }

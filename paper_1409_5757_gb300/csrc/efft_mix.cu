@@ -45,6 +45,24 @@ bool launch_mixm_odd(int odd, const MixArgs& m, const Pass& ps, void* data, unsi
   }
 }
 
+// The middle pass of N = 3 * 2^e with R = 3 * 2^b, b = 4..6, in two register
+// stages (efft_pass_m3): 16 columns per CTA.
+template <class P, int P1>
+void launch_m3(const MixArgs& m, const efft_plan_s* p, void* data, unsigned count, cudaStream_t st) {
+  const uint64_t tiles = p->n / (uint64_t)(P1 * 16) / (uint64_t)kM3Cols;
+  efft_pass_m3<P, P1><<<dim3((unsigned)tiles, count), kMixThreads, m3_smem_bytes(P1 * 16, P::kElemBytes), st>>>(data, m);
+}
+
+template <class P>
+bool launch_m3_b(int b, const MixArgs& m, const efft_plan_s* p, void* data, unsigned count, cudaStream_t st) {
+  switch (b) {
+    case 4: launch_m3<P, 3>(m, p, data, count, st); return true;
+    case 5: launch_m3<P, 6>(m, p, data, count, st); return true;
+    case 6: launch_m3<P, 12>(m, p, data, count, st); return true;
+    default: return false;
+  }
+}
+
 template <class P>
 cudaError_t launch_mix_p(const efft_plan_s* p, const Pass& ps, void* data, const Batch& bt, cudaStream_t st) {
   MixArgs m;
@@ -71,6 +89,10 @@ cudaError_t launch_mix_p(const efft_plan_s* p, const Pass& ps, void* data, const
   const uint64_t odd = ps.R_int / (ps.R_int & (~ps.R_int + 1));
   m.log2b = __builtin_ctzll(ps.R_int);
   m.log2s = __builtin_ctzll(ps.s_int);
+  if (ps.kind == MID && odd == 3 && m.log2b >= 4 && m.log2b <= 6 && m.log2s >= 4 &&
+      (ps.s_int & (ps.s_int - 1)) == 0 &&
+      launch_m3_b<P>(m.log2b, m, p, data, bt.count, st))
+    return cudaGetLastError();
   if (ps.kind == MID && odd > 1 && m.log2b >= 4 && (ps.s_int & (ps.s_int - 1)) == 0 && ps.C_int <= 32 &&
       launch_mixm_odd<P>((int)odd, m, ps, data, bt.count, st))
     return cudaGetLastError();
@@ -120,6 +142,15 @@ cudaError_t mix_set_attrs() {
       cudaFuncSetAttribute(efft_pass_mixm<PolicyF32, 13>, attr, mix64),
       cudaFuncSetAttribute(efft_pass_mixm<PolicyF32, 15>, attr, mix64)};
   for (cudaError_t x : f)
+    if (x != cudaSuccess) return x;
+  const cudaError_t g[6] = {
+      cudaFuncSetAttribute(efft_pass_m3<PolicyDF2, 3>, attr, m3_smem_bytes(48, PolicyDF2::kElemBytes)),
+      cudaFuncSetAttribute(efft_pass_m3<PolicyDF2, 6>, attr, m3_smem_bytes(96, PolicyDF2::kElemBytes)),
+      cudaFuncSetAttribute(efft_pass_m3<PolicyDF2, 12>, attr, m3_smem_bytes(192, PolicyDF2::kElemBytes)),
+      cudaFuncSetAttribute(efft_pass_m3<PolicyF32, 3>, attr, m3_smem_bytes(48, PolicyF32::kElemBytes)),
+      cudaFuncSetAttribute(efft_pass_m3<PolicyF32, 6>, attr, m3_smem_bytes(96, PolicyF32::kElemBytes)),
+      cudaFuncSetAttribute(efft_pass_m3<PolicyF32, 12>, attr, m3_smem_bytes(192, PolicyF32::kElemBytes))};
+  for (cudaError_t x : g)
     if (x != cudaSuccess) return x;
   return cudaSuccess;
 }

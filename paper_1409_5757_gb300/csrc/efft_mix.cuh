@@ -430,4 +430,114 @@ __global__ void __launch_bounds__(kMixThreads, kMixmMinBlocks) efft_pass_mixm(vo
   }
 }
 
+// ----------------------------------------------------------------------------
+// Middle pass of N = 3 * 2^e with R = 3 * 2^b, b = 4..6 (R = 48, 96, 192),
+// in two register stages and one shared-memory exchange (the Stockham kernel
+// above exchanges every stage through shared memory):
+//   R = P1 * 16, P1 = 3 * 2^(b-4); n = n2 + 16 n1, k = k1 + P1 k2;
+//   stage A, thread n2 < 16 of its column: the P1-point DFT over
+//     x[n2 + 16 n1] (a radix-3 butterfly over n1 = j, j + Q, j + 2Q,
+//     Q = P1 / 3, times exp(-2*pi*i*j*q/P1), then radix-Q DIF in registers:
+//     output q + 3 r in the register of bitrev(r)), times
+//     exp(-2*pi*i*n2*k1/R), to shared memory at (k1, n2);
+//   stage B, thread k1 < P1: the 16-point DIF over n2, output k1 + P1 k2,
+//     the pass twiddle exp(-2*pi*i*m*k/L) = W(m k1) W(m P1 k2) (the first
+//     per thread, the second per column from a table), stored.
+// C = 16 columns per CTA, 256 threads (stage B uses 16 P1 of them); the R-th
+// roots of unity come from the two-level table once per CTA.
+// ----------------------------------------------------------------------------
+constexpr int kM3Cols = 16;
+
+template <class P, int P1>
+__global__ void __launch_bounds__(kMixThreads, 3) efft_pass_m3(void* __restrict__ data, const MixArgs a) {
+  typedef typename P::V V;
+  constexpr int KIND = MID, C = kM3Cols, R = P1 * 16, Q = P1 / 3, LQ = (Q == 1) ? 0 : (Q == 2) ? 1 : 2;
+  static_assert(P1 == 3 || P1 == 6 || P1 == 12, "R = 48, 96 or 192");
+  if (a.ptrs) data = a.ptrs[blockIdx.y];
+  const uint32_t* state = a.state + (a.ptrs ? 4u * blockIdx.y : 0u);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  V* sm = reinterpret_cast<V*>(smem_raw);                     // [k1][n2][c], one pad slot per 16
+  __shared__ float4 roots[R];                                 // exp(-2*pi*i*j/R)
+  __shared__ float4 vtab[16 * C];                             // W(m_c P1 k2), [k2][c]
+  auto slot = [](int k1, int n2, int c) {
+    const int raw = ((k1 << 4) + n2) * C + c;
+    return raw + (raw >> 4);
+  };
+  int D = 0;
+  if (P::kElemBytes == 16) D = (int)__ldg(state) - 127;
+  const uint64_t runit = a.N / (uint64_t)R, tw_unit = a.N / a.L;
+  for (int j = threadIdx.x; j < R; j += kMixThreads) roots[j] = twiddle_mix(a, (uint64_t)j * runit);
+
+  // columns jcol0 .. jcol0 + C - 1, all in block jcol0 / s (C divides s)
+  const uint64_t jcol0 = (uint64_t)blockIdx.x * C;
+  const uint64_t m0 = jcol0 & ((1ull << a.log2s) - 1ull);
+  const uint64_t base0 = (jcol0 >> a.log2s) * a.L + m0;
+  const int c = threadIdx.x & (C - 1), t = threadIdx.x >> 4;  // t: n2 in stage A, k1 in stage B
+  {
+    const int k2 = threadIdx.x >> 4, cc = threadIdx.x & (C - 1);
+    vtab[k2 * C + cc] = twiddle_mix(a, (m0 + cc) * (uint64_t)(P1 * k2) * tw_unit);
+  }
+  __syncthreads();  // roots
+
+  // ---- stage A: thread n2 = t, the P1 rows n2 + 16 n1 of column c ----
+  {
+    V v[P1];
+#pragma unroll
+    for (int n1 = 0; n1 < P1; ++n1)
+      v[n1] = Mem<P, KIND>::load(data, base0 + c + ((uint64_t)(t + 16 * n1) << a.log2s), D, 0u);
+    // radix 3 over (j, j + Q, j + 2Q), then exp(-2*pi*i*j*q/P1) = roots[16 j q]
+#pragma unroll
+    for (int j = 0; j < Q; ++j) {
+      const V x0 = v[j], x1 = v[j + Q], x2 = v[j + 2 * Q];
+      const V t1 = P::add(x1, x2);
+      const V t2 = P::sub(x0, mix_scale(t1, df{0.5f, 0.f}));
+      const V t3 = P::mul_negi(mix_scale(P::sub(x1, x2), K_SQRT3_2()));
+      v[j] = P::add(x0, t1);
+      v[j + Q] = P::add(t2, t3);
+      v[j + 2 * Q] = P::sub(t2, t3);
+      if (j > 0) {
+        v[j + Q] = P::mul_tw(v[j + Q], P::expand(roots[16 * j]));
+        v[j + 2 * Q] = P::mul_tw(v[j + 2 * Q], P::expand(roots[32 * j]));
+      }
+    }
+    // radix-Q DIF of each third: register q Q + u holds output q + 3 bitrev(u)
+    if constexpr (LQ > 0) {
+#pragma unroll
+      for (int q = 0; q < 3; ++q) dif_regs<P, LQ>(v + q * Q);
+    }
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+#pragma unroll
+      for (int u = 0; u < Q; ++u) {
+        const int k1 = q + 3 * bitrev_c(u, LQ);
+        V y = v[q * Q + u];
+        if (k1 > 0 && t > 0) y = P::mul_tw(y, P::expand(roots[t * k1]));
+        sm[slot(k1, t, c)] = y;
+      }
+    }
+  }
+  __syncthreads();
+
+  // ---- stage B: thread k1 = t < P1, the 16 points n2 of column c ----
+  if (t < P1) {
+    V v[16];
+#pragma unroll
+    for (int n2 = 0; n2 < 16; ++n2) v[n2] = sm[slot(t, n2, c)];
+    dif_regs<P, 4>(v);
+    const typename P::TW wt = P::expand(twiddle_mix(a, (m0 + c) * (uint64_t)t * tw_unit));
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+      const int k2 = bitrev_c(u, 4);
+      const int k = t + P1 * k2;
+      const V y = P::pass_tw(v[u], wt, P::expand(vtab[k2 * C + c]));
+      Mem<P, KIND>::store(data, base0 + c + ((uint64_t)k << a.log2s), y, 0, 0u, false);
+    }
+  }
+}
+
+// dynamic shared memory of efft_pass_m3: the padded C x R tile
+constexpr int m3_smem_bytes(int R, int elem_bytes) {
+  return (kM3Cols * R + kM3Cols * R / 16) * elem_bytes;
+}
+
 }  // namespace efft

@@ -163,7 +163,14 @@ def test_schedule_and_batch_argument_errors_before_cuda(libs):
     assert create(1 << 3, [3]) == 9                 # N <= 8: direct sums only
     assert create(1 << 12, [6, 6], flags=0x4) == 12  # autotune with an explicit schedule
     assert create(34, [6, 6]) == 1
-    assert create(12, [2]) == 9                     # explicit schedules: powers of two
+    # N = M * 2^e: one pass of log2 R_0 = e within 2048 points, or (a, b, a)
+    assert create(12, [3]) == 9                     # log2 R_0 != e
+    assert create(3 << 12, [12]) == 9               # one pass above 2048 points
+    assert create(3 << 12, [4, 5, 3]) == 9          # not symmetric
+    assert create(3 << 12, [0, 12, 0]) == 9         # outer radix 1
+    assert create(3 << 12, [4, 5, 4]) == 9          # 2a + b != e
+    assert create(3 << 26, [5, 16, 5]) == 9         # middle radix 3 * 2^16 above 2048
+    assert create(3 << 12, [3, 6, 3], flags=0x4) == 12
     assert L.efft_plan_create_with_radices(None, 1 << 12, 1, -1, 0, radices(6, 6)[0], 2) == 4
     assert h.value is None
 

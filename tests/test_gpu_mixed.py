@@ -103,6 +103,26 @@ def test_mixed_outer_passes_on_specialised_kernels(orc, name, N, a):
         _check(got, orc.dft(x, sign), name, N, f"sign {sign}")
 
 
+@pytest.mark.parametrize("name", ["c128", "c64"])
+@pytest.mark.parametrize("e,a", [(10, 3), (12, 4), (13, 4), (14, 4), (17, 6), (20, 7), (24, 9)])
+def test_mixed_two_stage_middle_pass(orc, name, e, a):
+    """N = 3 * 2^e on the explicit schedule (2^a, 3 * 2^b, 2^a), b = e - 2a in
+    4..6: the middle radices 48, 96 and 192 at strides 2^a >= 16 run the
+    two-stage register kernel (radix 3 * 2^(b-4), then 16); a = 3 keeps the
+    Stockham kernel.  Both signs, every element against the oracle."""
+    import paper_1409_5757_gb300 as efft
+    N = 3 << e
+    b = e - 2 * a
+    x = host_input(orc, name, N, seed=900 + e)
+    for sign in (-1, 1):
+        t = torch.from_numpy(x.astype(np.complex128 if name == "c128" else np.complex64)).cuda()
+        p = efft.Plan(N, _code(name), sign, 0, radices=[a, b, a])
+        assert p.radices() == [a, b, a]
+        p.execute(t.data_ptr(), torch.cuda.current_stream().cuda_stream)
+        torch.cuda.synchronize()
+        _check(t.cpu().numpy().astype(np.complex128), orc.dft(x, sign), name, N, f"(a={a}, b={b}) sign {sign}")
+
+
 def test_mixed_extreme_magnitudes_and_nan(orc):
     N = 3 << 12
     x = orc.gen_uniform(4, N)
@@ -129,7 +149,7 @@ def test_mixed_round_trip(orc):
 
 def test_mixed_batch_matches_single_plans(orc):
     import paper_1409_5757_gb300 as efft
-    sizes = [3 << 10, 1 << 12, 15 << 7, 5 << 16, 3 << 10, 7, 12]
+    sizes = [3 << 10, 1 << 12, 15 << 7, 5 << 16, 3 << 10, 7, 12, 3 << 14, 3 << 17]
     xs = [host_input(orc, "c64", n, seed=40 + i) for i, n in enumerate(sizes)]
     ts = [torch.from_numpy(x.astype(np.complex64)).cuda() for x in xs]
     refs = [t.clone() for t in ts]
