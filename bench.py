@@ -673,8 +673,8 @@ def run_ours(args, wl):
                "h2d_bytes_per_step": N * S, "d2h_bytes_per_step": N * S,
                "ms_per_step": dt * 1e3, "steps": Ke, "pin_seconds": t_pin,
                "api": "efft_execute_host_stream (one cudaHostAlloc host array as input and output, the one "
-                      "device buffer; copy in, transform, copy out in sequence: a second 128 GiB device "
-                      "buffer does not fit)"}
+                      "device buffer: a second 128 GiB device buffer does not fit; the copy out of a step "
+                      "and the copy in of the next share the link's two directions, 1 GiB piece by piece)"}
     elif (N * S <= (32 << 30) and not args.no_e2e
           and (world == 1 or (host_room is not None and host_room >= world * 2 * N * S + (24 << 30)))):
         src = keep if keep is not None else x

@@ -175,16 +175,21 @@ int efft_execute_host(efft_plan_t plan, void* host_data, void* dev_data, void* s
  * dev_bufs[i % nbufs], the plans[0 .. nplans) are applied to it in order, in
  * place, and the result is copied to host_out[i].  Copies in, transforms and
  * copies out run on three streams (the transforms on `stream`), so array i+1
- * is copied in and array i-1 copied out while array i is transformed; a
- * buffer is reused only after the copy-out of its previous array finished.
- * With nbufs >= 3 the copies in both directions also overlap each other.
+ * is copied in and array i-1 copied out while array i is transformed.  The
+ * copies go in 1 GiB pieces; a piece of a buffer is refilled once the copy
+ * out of the buffer's previous array has read that piece, so even with one
+ * buffer the copy out of array i and the copy in of array i+nbufs overlap
+ * (the link's two directions), and with nbufs >= 3 the copies in both
+ * directions also overlap the transforms.
  * Synchronous: returns when every result is in host memory.
  *  plans      nplans >= 1 live plans with the same n and dtype.
  *  host_in    count host pointers (pinned memory gives the full copy rate).
  *  host_out   count host pointers; host_out[i] may equal host_in[i] but must
- *             not overlap any host_in[j], j != i.  Several host_in entries may
- *             share memory, and so may several host_out entries (the copies
- *             out are issued in order on one stream).
+ *             not overlap any host_in[j], j != i, except that with nbufs = 1
+ *             host_in[j] (j > i) may equal host_out[i] (each piece is then
+ *             copied in after the same piece was copied out).  Several
+ *             host_in entries may share memory, and so may several host_out
+ *             entries (the copies out are issued in order on one stream).
  *  dev_bufs   nbufs >= 1 device buffers of n*S bytes on the plans' device.
  * Errors: INVALID_PLAN, INVALID_PTR, MISALIGNED, INVALID_SIZE (plans of
  * different n or dtype, count < 0, nplans or nbufs < 1), LAUNCH, CUDA.

@@ -1160,7 +1160,12 @@ int efft_execute_host_stream(const efft_plan_t* plans, int nplans, void* const* 
   const size_t bytes = plan_bytes(p0);
   cudaStream_t sc = reinterpret_cast<cudaStream_t>(stream);
   cudaStream_t sin = nullptr, sout = nullptr;
-  std::vector<cudaEvent_t> ev_in(nbufs, nullptr), ev_comp(nbufs, nullptr), ev_out(nbufs, nullptr);
+  // one copy-out event per 1 GiB piece of each buffer: the next array's copy
+  // of a piece into the buffer waits only for that piece's copy out, so with
+  // one buffer the copy out of array i and the copy in of array i+1 share the
+  // link's two directions
+  const size_t npieces = (bytes + kCopyChunk - 1) / kCopyChunk;
+  std::vector<cudaEvent_t> ev_in(nbufs, nullptr), ev_comp(nbufs, nullptr), ev_out(nbufs * npieces, nullptr);
   std::vector<bool> used(nbufs, false);
   int rc = EFFT_OK;
   if (cudaStreamCreateWithFlags(&sin, cudaStreamNonBlocking) != cudaSuccess ||
@@ -1168,21 +1173,23 @@ int efft_execute_host_stream(const efft_plan_t* plans, int nplans, void* const* 
     rc = EFFT_ERR_CUDA;
   for (int b = 0; rc == EFFT_OK && b < nbufs; ++b) {
     if (cudaEventCreateWithFlags(&ev_in[b], cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&ev_comp[b], cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&ev_out[b], cudaEventDisableTiming) != cudaSuccess)
+        cudaEventCreateWithFlags(&ev_comp[b], cudaEventDisableTiming) != cudaSuccess)
       rc = EFFT_ERR_CUDA;
+    for (size_t q = 0; rc == EFFT_OK && q < npieces; ++q)
+      if (cudaEventCreateWithFlags(&ev_out[b * npieces + q], cudaEventDisableTiming) != cudaSuccess)
+        rc = EFFT_ERR_CUDA;
   }
   for (int i = 0; rc == EFFT_OK && i < count; ++i) {
     const int b = i % nbufs;
     void* buf = dev_bufs[b];
-    // copy in once the buffer's previous result has been copied out
-    if (used[b] && cudaStreamWaitEvent(sin, ev_out[b], 0) != cudaSuccess) { rc = EFFT_ERR_CUDA; break; }
     // copies in 1 GiB pieces: the two copy directions then interleave on the
-    // link (measured 16+16 GiB: 118 ms whole, 100 ms in pieces)
-    for (size_t o = 0; rc == EFFT_OK && o < bytes; o += kCopyChunk) {
+    // link (measured 16+16 GiB: 118 ms whole, 100 ms in pieces); each piece
+    // once the buffer's previous result has left that piece
+    for (size_t o = 0, q = 0; rc == EFFT_OK && o < bytes; o += kCopyChunk, ++q) {
       const size_t len = (bytes - o < kCopyChunk) ? bytes - o : kCopyChunk;
-      if (cudaMemcpyAsync(static_cast<char*>(buf) + o, static_cast<const char*>(host_in[i]) + o, len,
-                          cudaMemcpyHostToDevice, sin) != cudaSuccess)
+      if (used[b] && cudaStreamWaitEvent(sin, ev_out[b * npieces + q], 0) != cudaSuccess) rc = EFFT_ERR_CUDA;
+      else if (cudaMemcpyAsync(static_cast<char*>(buf) + o, static_cast<const char*>(host_in[i]) + o, len,
+                               cudaMemcpyHostToDevice, sin) != cudaSuccess)
         rc = EFFT_ERR_CUDA;
     }
     if (rc != EFFT_OK || cudaEventRecord(ev_in[b], sin) != cudaSuccess) { rc = EFFT_ERR_CUDA; break; }
@@ -1193,13 +1200,14 @@ int efft_execute_host_stream(const efft_plan_t* plans, int nplans, void* const* 
     if (cudaEventRecord(ev_comp[b], sc) != cudaSuccess) { rc = EFFT_ERR_CUDA; break; }
     // copy out
     if (cudaStreamWaitEvent(sout, ev_comp[b], 0) != cudaSuccess) { rc = EFFT_ERR_CUDA; break; }
-    for (size_t o = 0; rc == EFFT_OK && o < bytes; o += kCopyChunk) {
+    for (size_t o = 0, q = 0; rc == EFFT_OK && o < bytes; o += kCopyChunk, ++q) {
       const size_t len = (bytes - o < kCopyChunk) ? bytes - o : kCopyChunk;
       if (cudaMemcpyAsync(static_cast<char*>(host_out[i]) + o, static_cast<const char*>(buf) + o, len,
-                          cudaMemcpyDeviceToHost, sout) != cudaSuccess)
+                          cudaMemcpyDeviceToHost, sout) != cudaSuccess ||
+          cudaEventRecord(ev_out[b * npieces + q], sout) != cudaSuccess)
         rc = EFFT_ERR_CUDA;
     }
-    if (rc != EFFT_OK || cudaEventRecord(ev_out[b], sout) != cudaSuccess) { rc = EFFT_ERR_CUDA; break; }
+    if (rc != EFFT_OK) break;
     used[b] = true;
   }
   // drain everything that was enqueued, even after an error
@@ -1209,8 +1217,9 @@ int efft_execute_host_stream(const efft_plan_t* plans, int nplans, void* const* 
   for (int b = 0; b < nbufs; ++b) {
     if (ev_in[b]) cudaEventDestroy(ev_in[b]);
     if (ev_comp[b]) cudaEventDestroy(ev_comp[b]);
-    if (ev_out[b]) cudaEventDestroy(ev_out[b]);
   }
+  for (cudaEvent_t e : ev_out)
+    if (e) cudaEventDestroy(e);
   if (sin) cudaStreamDestroy(sin);
   if (sout) cudaStreamDestroy(sout);
   if (rc != EFFT_OK) cudaGetLastError();

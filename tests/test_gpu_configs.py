@@ -331,3 +331,24 @@ def test_execute_host_stream(orc, nbufs):
         efft.execute_host_stream([fwd, other], [hin[0].data_ptr()], [hout[0].data_ptr()], [bufs[0].data_ptr()])
     assert ei.value.status == 1
     efft.execute_host_stream([fwd], [], [], [bufs[0].data_ptr()])  # count 0 is a no-op
+
+
+def test_execute_host_stream_one_buffer_in_pieces(orc):
+    """One device buffer, one host array as every input and output, N = 5 *
+    2^24 complex128 (1.25 GiB: a 1 GiB piece and a ragged quarter): the copy
+    in of step i+1 overlaps the copy out of step i piece by piece, so each
+    piece must be read back only after the previous step wrote it.  Two
+    forward steps give F(F x) = N x[-n mod N] (Eq. 1 applied twice)."""
+    import paper_1409_5757_gb300 as efft
+    N = 5 << 24
+    fwd = efft.Plan(N, efft.EFFT_C128, -1)
+    x = orc.gen_uniform(77, N)
+    h = torch.from_numpy(x.copy()).pin_memory()
+    buf = torch.empty(N, dtype=torch.complex128, device="cuda")
+    efft.execute_host_stream([fwd], [h.data_ptr()] * 2, [h.data_ptr()] * 2, [buf.data_ptr()],
+                             torch.cuda.current_stream().cuda_stream)
+    want = np.roll(x[::-1], 1)  # x[-n mod N]
+    got = h.numpy() / N
+    assert oracle.rel_l2(got, want) <= 2 * 1e-14 * 27
+    # the second piece alone (elements from 2^26 on) is as accurate as the whole
+    assert oracle.rel_l2(got[1 << 26:], want[1 << 26:]) <= 2 * 1e-14 * 27
