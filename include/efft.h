@@ -230,7 +230,9 @@ int efft_plan_create_with_radices(efft_plan_t* out, uint64_t n, int dtype, int s
  *    complex128 only), the TMA-fed first and 2^11 middle passes or not
  *    (complex64 only);
  *  - n = M * 2^e, M > 1: every outer radix 2^a of the (2^a, M * 2^b, 2^a)
- *    schedule that efft_plan_create accepts, and one pass when n <= 2048.
+ *    schedule that efft_plan_create accepts, and one pass when n <= 2048;
+ *    then, for the fastest, the first pass's tile width switched the other
+ *    way where that changes the passes (kept when faster).
  * Each candidate is run on `scratch` (n*S bytes of the caller's device
  * memory on the plan's device; its contents are overwritten) on `stream`,
  * twice untimed and then a few times between CUDA events; its time is the
@@ -278,7 +280,10 @@ int efft_plan_variant(efft_plan_t plan, int* wide, int* fused_swap, int* persist
  * rounding.  No execute of the plan may be in flight.
  * A real-data plan switches its complex plan.
  * Errors: INVALID_PLAN; INVALID_FLAGS for a knob outside -1..1;
- * UNSUPPORTED for a plan of N = M * 2^e (M > 1) with a knob other than -1. */
+ * UNSUPPORTED for a plan of N = M * 2^e (M > 1) with a knob other than
+ * `wide` set (there `wide` is the tile width of the first pass when it runs
+ * on the power-of-two kernels: 2^10 or 2^11 rows for complex128, 2^10 for
+ * complex64). */
 int efft_plan_set_variant(efft_plan_t plan, int wide, int fused_swap, int persistent, int tma);
 
 /*

@@ -158,7 +158,7 @@ int mixed_candidates(const efft_plan_s* p, int* a, int cap) {
   return k;
 }
 
-int apply_mixed_schedule(efft_plan_s* p, int force_a) {
+int apply_mixed_schedule(efft_plan_s* p, int force_a, const Variant& v) {
   const uint64_t n = p->n;
   const int tile = (p->dtype == EFFT_C128) ? kMixTileC128 : kMixTileC64;
   const size_t eb = (p->dtype == EFFT_C128) ? 16 : 8;
@@ -239,7 +239,9 @@ int apply_mixed_schedule(efft_plan_s* p, int force_a) {
       ps.mixed = false;
       ps.log2s = (j == 0) ? e - a : 0;
       ps.log2L = ps.log2s + a;
-      ps.wide = j == 0 && n >= (1ull << kWideMinLog2N) && (p->dtype == EFFT_C128 ? a >= 10 : a == 10);
+      // the first pass's tile width: the size rule, or the variant's knob
+      const bool wide_on = (v.wide < 0) ? n >= (1ull << kWideMinLog2N) : v.wide != 0;
+      ps.wide = j == 0 && wide_on && (p->dtype == EFFT_C128 ? a >= 10 : a == 10);
       ps.log2C = (ps.wide ? (p->dtype == EFFT_C128 ? kLog2CtaWide : kLog2CtaWideC64) : log2cta) - a;
       ps.grid = ncol >> ps.log2C;
       ps.threads = 1 << (a + ps.log2C - 4);
@@ -769,7 +771,7 @@ int plan_create_impl(efft_plan_t* out, uint64_t n, int dtype, int sign, uint32_t
   if (p->odd > 1) {
     // N = M * 2^e: the mixed-radix schedule (the tuned outer radix if cached)
     const int force = r_explicit ? (np_explicit == 3 ? r_explicit[0] : 0) : (cached ? t.mixed_a : -1);
-    const int rc0 = apply_mixed_schedule(p, force);
+    const int rc0 = apply_mixed_schedule(p, force, (cached && !r_explicit) ? t.v : Variant());
     if (rc0 != EFFT_OK) {
       delete p;
       return rc0;

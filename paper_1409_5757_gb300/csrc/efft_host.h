@@ -105,7 +105,8 @@ struct Variant {
 };
 
 // A tuned schedule: log2 R_0 .. log2 R_{np-1} and the variant for a power of
-// two; for N = M * 2^e the outer radix 2^mixed_a (0: one pass).
+// two; for N = M * 2^e the outer radix 2^mixed_a (0: one pass) and the
+// variant's tile-width knob.
 struct Tuned {
   int np = 0;
   int r[kMaxPasses] = {0, 0, 0, 0};
@@ -187,8 +188,9 @@ int ilog2_u64(uint64_t n);
 // N = M * 2^e with M odd, M <= kMaxOdd, 1 <= N <= 2^EFFT_MAX_LOG2N.
 bool valid_size(uint64_t n);
 // Schedule of a plan with N = M * 2^e, M > 1 (pass table and swap); the
-// outer radix 2^force_a when force_a >= 0 is a valid choice (0: one pass).
-int apply_mixed_schedule(efft_plan_s* p, int force_a = -1);
+// outer radix 2^force_a when force_a >= 0 is a valid choice (0: one pass);
+// v.wide >= 0 sets the first pass's tile width instead of the size rule.
+int apply_mixed_schedule(efft_plan_s* p, int force_a = -1, const Variant& v = Variant());
 // The outer-radix exponents apply_mixed_schedule accepts for p (0: one pass).
 int mixed_candidates(const efft_plan_s* p, int* a, int cap);
 

@@ -4,8 +4,9 @@
 // parameters are the radix schedule (for N = M * 2^e the outer radix of the
 // (2^a, M * 2^b, 2^a) schedule) and the kernel variant of its passes: the
 // tile width of the strided passes (C doubled or not), the digit swap folded
-// into the middle pass or not, and the persistent prefetching pass kernels or
-// not.
+// into the middle pass or not, the persistent prefetching pass kernels or
+// not, and the TMA-fed complex64 passes or not (N = M * 2^e: the tile width
+// of the first pass only).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -34,7 +35,7 @@ struct Cand {
 };
 
 void apply(efft_plan_s* p, const Tuned& t) {
-  if (p->odd > 1) apply_mixed_schedule(p, t.mixed_a);
+  if (p->odd > 1) apply_mixed_schedule(p, t.mixed_a, t.v);
   else apply_schedule(p, t.r, t.np, t.v);
 }
 
@@ -120,8 +121,8 @@ int autotune_impl(efft_plan_s* p, void* scratch, cudaStream_t st, efft_candidate
   } else {
     prev.np = p->npasses;
     for (int j = 0; j < prev.np; ++j) prev.r[j] = p->pass[j].log2R;
-    prev.v = realised_variant(p);
   }
+  prev.v = realised_variant(p);
   const size_t bytes = plan_bytes(p);
   const int reps = (p->n <= (1ull << 20)) ? 21 : (p->n <= (1ull << 26) ? 9 : 5);
   const bool prof = p->profiling;
@@ -189,13 +190,15 @@ int autotune_impl(efft_plan_s* p, void* scratch, cudaStream_t st, efft_candidate
     record(ms);
     if (best_ms < 0 || ms < best_ms) {
       best = cands[i];
-      if (p->odd == 1) best.v = realised_variant(p);
+      best.v = realised_variant(p);
       best_ms = ms;
     }
   }
-  // 2. power of two: each variant knob of the fastest schedule switched the
-  // other way, where that changes the launches; kept when faster
-  for (int knob = 0; rc == EFFT_OK && p->odd == 1 && best_ms >= 0 && knob < 4; ++knob) {
+  // 2. each variant knob of the fastest schedule switched the other way,
+  // where that changes the launches; kept when faster (N = M * 2^e: the
+  // first pass's tile width only)
+  const int nknobs = (p->odd > 1) ? 1 : 4;
+  for (int knob = 0; rc == EFFT_OK && best_ms >= 0 && knob < nknobs; ++knob) {
     Tuned c = best;
     int* k = (knob == 0) ? &c.v.wide : (knob == 1) ? &c.v.fuse : (knob == 2) ? &c.v.pf : &c.v.tma;
     apply(p, best);
@@ -264,8 +267,16 @@ int efft_plan_set_variant(efft_plan_t plan, int wide, int fused_swap, int persis
   if (plan->real) plan = plan->inner;
   for (int k : {wide, fused_swap, persistent, tma})
     if (k < -1 || k > 1) return EFFT_ERR_INVALID_FLAGS;
-  if (plan->odd > 1)
-    return (wide == -1 && fused_swap == -1 && persistent == -1 && tma == -1) ? EFFT_OK : EFFT_ERR_UNSUPPORTED;
+  if (plan->odd > 1) {
+    // N = M * 2^e: the first pass's tile width only
+    if (fused_swap != -1 || persistent != -1 || tma != -1) return EFFT_ERR_UNSUPPORTED;
+    Variant v;
+    v.wide = wide;
+    const int a = (plan->npasses == 3) ? __builtin_ctzll(plan->pass[0].mixed ? plan->pass[0].R_int
+                                                                               : (1ull << plan->pass[0].log2R))
+                                       : 0;
+    return apply_mixed_schedule(plan, a, v);
+  }
   Variant v;
   v.wide = wide;
   v.fuse = fused_swap;

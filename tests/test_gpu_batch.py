@@ -128,19 +128,51 @@ def test_autotune_mixed_sizes_scans_outer_radix(orc, name, n):
     scratch = torch.empty(n, dtype=torch.complex128 if name == "c128" else torch.complex64, device="cuda")
     res = plan.autotune_candidates(scratch.data_ptr(), torch.cuda.current_stream().cuda_stream)
     outer = [c["radices"][0] for c in res]
-    assert len(outer) == len(set(outer)) >= 3
+    # the schedule scan (distinct outer radices), then at most one record of
+    # the fastest schedule with the first pass's tile width switched
+    k = len(set(outer))
+    assert k >= 3 and len(outer[:k]) == len(set(outer[:k])) and len(res) <= k + 1
     for c in res:
         A, B = c["radices"][0], c["radices"][1]
         assert c["radices"][2] == A and A * B * A == n and A <= 2048 and B <= 2048
+    if len(res) == k + 1:
+        first = min(res[:k], key=lambda c: c["ms"])
+        assert res[k]["radices"] == first["radices"] and res[k]["wide"] == 1 - first["wide"]
     best = min(res, key=lambda c: c["ms"])
     assert best["ms"] > 0
     # a plan created with the flag reuses the measured choice
     tuned = efft.Plan(n, _code(name), -1, efft.EFFT_FLAG_AUTOTUNE)
     assert tuned.radices() == [int(R & -R).bit_length() - 1 for R in best["radices"]]
+    assert tuned.variant()["wide"] == best["wide"]
     x = host_input(orc, name, n, seed=57)
     t = torch.from_numpy(x.astype(_np(name))).cuda()
     tuned.execute(t.data_ptr(), torch.cuda.current_stream().cuda_stream)
     check(t.cpu().numpy().astype(np.complex128), orc.dft(x, -1), name, n, "tuned mixed")
+
+
+@pytest.mark.parametrize("name,n", [("c128", 3 << 24), ("c64", 3 << 26)])
+def test_mixed_first_pass_tile_width_knob(orc, name, n):
+    """N = M * 2^e with outer radix 2^10: the `wide` knob switches the first
+    pass (2^10 rows at the odd stride 3 * 2^(e-10)) between its two tile
+    widths; both give the oracle's transform, and the tuner's flip of the
+    knob is a candidate of the same schedule."""
+    import paper_1409_5757_gb300 as efft
+    plan = efft.Plan(n, _code(name), -1)
+    assert plan.radices()[0] == 10
+    x = host_input(orc, name, n, seed=58)
+    ref = orc.dft(x, -1)
+    seen = set()
+    for w in (1, 0):
+        assert plan.set_variant(w, -1, -1)["wide"] == w
+        seen.add(plan.variant()["wide"])
+        t = torch.from_numpy(x.astype(_np(name))).cuda()
+        plan.execute(t.data_ptr(), torch.cuda.current_stream().cuda_stream)
+        torch.cuda.synchronize()
+        check(t.cpu().numpy().astype(np.complex128), ref, name, n, f"wide={w}")
+    assert seen == {0, 1}
+    with pytest.raises(efft.EfftError) as ei:
+        plan.set_variant(-1, 1, -1)
+    assert ei.value.status == 9
 
 
 @pytest.mark.parametrize("name", ["c128", "c64"])

@@ -169,12 +169,15 @@ def test_mixed_plan_rules():
     assert ei.value.status == 9
     p = efft.Plan(3 << 10, efft.EFFT_C128, -1)
     scratch = torch.empty(3 << 10, dtype=torch.complex128, device="cuda")
-    # the tuner scans the outer radix; the variant knobs apply to powers of two
+    # the tuner scans the outer radix; of the variant knobs only the first
+    # pass's tile width applies to N = M * 2^e
     res = p.autotune_candidates(scratch.data_ptr(), 0)
     assert len(res) >= 2 and all(c["radices"][0] * c["radices"][1] * c["radices"][2] == 3 << 10 for c in res)
-    with pytest.raises(efft.EfftError) as ei:
-        p.set_variant(1, -1, -1)
-    assert ei.value.status == 9
+    for knobs in ((-1, 1, -1), (-1, -1, 0), (-1, -1, -1, 1)):
+        with pytest.raises(efft.EfftError) as ei:
+            p.set_variant(*knobs)
+        assert ei.value.status == 9
+    p.set_variant(1, -1, -1)
     p.set_variant(-1, -1, -1)
     # 3 * 2^10 > 2048 points: three passes + the swap + half a sweep of range scan
     assert p.info()["hbm_passes"] == 4.5
