@@ -241,6 +241,7 @@ efft_pass_fx32_tma(void* __restrict__ data, const PassArgs a, const __grid_const
       smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   V* sm = reinterpret_cast<V*>(tile_base);
   __shared__ float4 vtw[32 * C];
+  __shared__ float4 wroot[R + R / 8];  // the 1024-th roots, root k at k + k/8
   __shared__ __align__(8) uint64_t bar;
   auto slot = [](int p, int col) {
     const int raw = (p << LC) + col;
@@ -254,6 +255,7 @@ efft_pass_fx32_tma(void* __restrict__ data, const PassArgs a, const __grid_const
     mbar_init(&bar, 1);
     mbar_fence_init();
   }
+  for (int k = tid; k < R; k += blockDim.x) wroot[k + (k >> 3)] = __ldg(a.w2048 + 2 * k);
   __syncthreads();
 
   // thread 0: arm the barrier with the tile's bytes and issue its copies
@@ -298,7 +300,7 @@ efft_pass_fx32_tma(void* __restrict__ data, const PassArgs a, const __grid_const
 #pragma unroll
     for (int u = 1; u < 32; ++u) {
       const int e = t * bitrev_c(u, 5);
-      v[u] = P::mul_tw(v[u], __ldg(a.w2048 + 2 * e));
+      v[u] = P::mul_tw(v[u], wroot[e + (e >> 3)]);
     }
 #pragma unroll
     for (int u = 0; u < 32; ++u) sm[slot(32 * bitrev_c(u, 5) + t, c)] = v[u];
@@ -366,6 +368,7 @@ efft_pass_mid_tma_f32(void* __restrict__ data, const PassArgs a, const __grid_co
   unsigned char* const tile_base = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   V* sm = reinterpret_cast<V*>(tile_base);
   __shared__ P::TW vtw[16 * C];
+  __shared__ float4 wroot[2048 + 256];  // the 2048-th roots, root k at k + k/8
   __shared__ __align__(8) uint64_t bar;
   auto slot = [](int p, int col) {
     const int raw = (p << LC) + col;
@@ -383,6 +386,7 @@ efft_pass_mid_tma_f32(void* __restrict__ data, const PassArgs a, const __grid_co
     mbar_init(&bar, 1);
     mbar_fence_init();
   }
+  for (int k = tid; k < 2048; k += blockDim.x) wroot[k + (k >> 3)] = __ldg(a.w2048 + k);
   __syncthreads();
   auto issue = [&](uint64_t tl) {
     const uint64_t j0 = tl << LC;
@@ -425,8 +429,10 @@ efft_pass_mid_tma_f32(void* __restrict__ data, const PassArgs a, const __grid_co
     __syncthreads();  // the dense box is read before the exchange overwrites it
     dif_regs<P, 4>(v);
 #pragma unroll
-    for (int u = 1; u < 16; ++u)
-      v[u] = P::mul_tw(v[u], P::int_tw(a.w2048, nullptr, (uint32_t)(t * bitrev_c(u, 4)) << (11 - LR)));
+    for (int u = 1; u < 16; ++u) {
+      const int e = (t * bitrev_c(u, 4)) << (11 - LR);
+      v[u] = P::mul_tw(v[u], wroot[e + (e >> 3)]);
+    }
 #pragma unroll
     for (int u = 0; u < 16; ++u) sm[sb0 + pad_off(bitrev_c(u, 4) * TPC * C)] = v[u];
     __syncthreads();
@@ -443,8 +449,10 @@ efft_pass_mid_tma_f32(void* __restrict__ data, const PassArgs a, const __grid_co
       for (int j = 0; j < 16; ++j) v[j] = sm[sb + pad_off(j * gstep)];
       dif_regs<P, 4>(v);
 #pragma unroll
-      for (int u = 1; u < 16; ++u)
-        v[u] = P::mul_tw(v[u], P::int_tw(a.w2048, nullptr, (uint32_t)(i * bitrev_c(u, 4)) << (11 - log2l)));
+      for (int u = 1; u < 16; ++u) {
+        const int e = (i * bitrev_c(u, 4)) << (11 - log2l);
+        v[u] = P::mul_tw(v[u], wroot[e + (e >> 3)]);
+      }
 #pragma unroll
       for (int u = 0; u < 16; ++u) sm[sb + pad_off(bitrev_c(u, 4) * gstep)] = v[u];
       __syncthreads();
