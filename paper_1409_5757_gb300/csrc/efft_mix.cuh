@@ -469,25 +469,27 @@ __global__ void __launch_bounds__(kMixThreads, 3) efft_pass_m3(void* __restrict_
   int D = 0;
   if (P::kElemBytes == 16) D = (int)__ldg(state) - 127;
   const uint64_t runit = a.N / (uint64_t)R, tw_unit = a.N / a.L;
-  for (int j = threadIdx.x; j < R; j += kMixThreads) roots[j] = twiddle_mix(a, (uint64_t)j * runit);
 
   // columns jcol0 .. jcol0 + C - 1, all in block jcol0 / s (C divides s)
   const uint64_t jcol0 = (uint64_t)blockIdx.x * C;
   const uint64_t m0 = jcol0 & ((1ull << a.log2s) - 1ull);
   const uint64_t base0 = (jcol0 >> a.log2s) * a.L + m0;
   const int c = threadIdx.x & (C - 1), t = threadIdx.x >> 4;  // t: n2 in stage A, k1 in stage B
-  {
-    const int k2 = threadIdx.x >> 4, cc = threadIdx.x & (C - 1);
-    vtab[k2 * C + cc] = twiddle_mix(a, (m0 + cc) * (uint64_t)(P1 * k2) * tw_unit);
-  }
-  __syncthreads();  // roots
 
   // ---- stage A: thread n2 = t, the P1 rows n2 + 16 n1 of column c ----
   {
+    // the tile's loads are issued first: they are in flight while the roots
+    // and the pass twiddles are built and the CTA meets at the barrier
     V v[P1];
 #pragma unroll
     for (int n1 = 0; n1 < P1; ++n1)
       v[n1] = Mem<P, KIND>::load(data, base0 + c + ((uint64_t)(t + 16 * n1) << a.log2s), D, 0u);
+    for (int j = threadIdx.x; j < R; j += kMixThreads) roots[j] = twiddle_mix(a, (uint64_t)j * runit);
+    {
+      const int k2 = threadIdx.x >> 4, cc = threadIdx.x & (C - 1);
+      vtab[k2 * C + cc] = twiddle_mix(a, (m0 + cc) * (uint64_t)(P1 * k2) * tw_unit);
+    }
+    __syncthreads();  // roots
     // radix 3 over (j, j + Q, j + 2Q), then exp(-2*pi*i*j*q/P1) = roots[16 j q]
 #pragma unroll
     for (int j = 0; j < Q; ++j) {
