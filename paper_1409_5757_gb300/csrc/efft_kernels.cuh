@@ -6,13 +6,9 @@
 //                   (Sec. 3.4 "reassembly"); results written back to the
 //                   slots that were read (the in-place principle of Sec. 3.4).
 //   efft_small      N <= 8: one thread evaluates Eq. 1 directly.
-//   efft_range_scan max binary64 exponent of the input (complex128 only):
-//                   fixes the power-of-two scale of the double-float data.
-//   efft_digit_swap in-place tiled transpose that turns the digit-reversed
-//                   pass output into natural order (the scatter of Sec. 3.2,
-//                   Listings 5-6, done as pairwise tile swaps).
-//   efft_twiddles   FP64 twiddle tables exp(-2*pi*i*t*stride/N) split into
-//                   FP32 (hi, lo) pairs (plan time only).
+// The range scan (largest binary64 exponent of the input), the digit swap
+// (digit-reversed pass output to natural order) and the twiddle-table
+// kernel are in efft.cu with their launches.
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -827,45 +823,6 @@ __global__ void efft_small(void* __restrict__ data, const PassArgs a) {
     y[k] = acc;
   }
   for (int k = 0; k < N; ++k) Mem<P, SINGLE>::store(data, k, y[k], Dout, a.conj_out, nonfinite);
-}
-
-// ----------------------------------------------------------------------------
-// In-place digit reversal for radices (a, b, a): position (i0, i1, i2) with
-// i0, i2 < A, i1 < B swaps with (i2, i1, i0).  For fixed i1 this is the
-// transpose of an A x A matrix with row stride B*A; CTA z handles the tile
-// pair (I, J), (J, I) with I <= J (triangular decode of blockIdx.x).
-// T x T tiles, T = min(32, A); 256 threads.
-// ----------------------------------------------------------------------------
-template <typename E>
-__global__ void __launch_bounds__(256) efft_digit_swap(E* __restrict__ data, int log2A, uint32_t B, int log2T,
-                                                       E* const* ptrs) {
-  if (ptrs) data = ptrs[blockIdx.z];  // batched launch: transform blockIdx.z
-  __shared__ E t0[32][33];
-  __shared__ E t1[32][33];
-  const int T = 1 << log2T;
-  const uint64_t A = 1ull << log2A;
-  const uint64_t rowstride = A * B;  // stride of i0 (B = extent of the middle digit)
-  const uint64_t i1 = blockIdx.y;
-  // triangular decode: z -> (I, J), I <= J
-  const uint32_t z = blockIdx.x;
-  uint32_t J = (uint32_t)((sqrtf(8.0f * (float)z + 1.0f) - 1.0f) * 0.5f);
-  while ((J + 1) * (J + 2) / 2 <= z) ++J;
-  while (J * (J + 1) / 2 > z) --J;
-  const uint32_t I = z - J * (J + 1) / 2;
-  const uint64_t base = i1 << log2A;
-  // tile (I, J): rows i0 = I*T + r, cols i2 = J*T + col
-  for (int e = threadIdx.x; e < T * T; e += blockDim.x) {
-    int r = e >> log2T, col = e & (T - 1);
-    t0[r][col] = data[base + ((uint64_t)I * T + r) * rowstride + (uint64_t)J * T + col];
-    if (I != J) t1[r][col] = data[base + ((uint64_t)J * T + r) * rowstride + (uint64_t)I * T + col];
-  }
-  __syncthreads();
-  // position (J*T + r, i1, I*T + col) receives old (I*T + col, i1, J*T + r) = t0[col][r]
-  for (int e = threadIdx.x; e < T * T; e += blockDim.x) {
-    int r = e >> log2T, col = e & (T - 1);
-    data[base + ((uint64_t)J * T + r) * rowstride + (uint64_t)I * T + col] = t0[col][r];
-    if (I != J) data[base + ((uint64_t)I * T + r) * rowstride + (uint64_t)J * T + col] = t1[col][r];
-  }
 }
 
 // Launch interface of the specialised kernels (one translation unit per
